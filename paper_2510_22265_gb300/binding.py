@@ -1,0 +1,292 @@
+"""Thin ctypes binding of the EBCC C ABI (include/ebcc.h).
+
+Argument marshalling only: every step runs in the CUDA library
+``libebcc_gb300.so``; there is no Python or CPU fallback.  Device buffers are
+torch CUDA tensors (their ``data_ptr()``), the stream is torch's current stream
+unless one is given.  Importing works without a GPU; calling a compute entry
+point without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C  # noqa: N812
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libebcc_gb300.so")
+
+EBCC_OK = 0
+EBCC_BOUND_ABS = 0
+EBCC_BOUND_REL = 1
+ERRORS = {-1: "EINVAL", -2: "ENONFINITE", -3: "ECORRUPT", -4: "ENOMEM", -5: "EBUDGET", -6: "ECAPACITY",
+          -7: "ETIMEOUT", -8: "ECUDA"}
+
+# every symbol include/ebcc.h declares
+EXPORTS = [
+    "ebcc_params_default", "ebcc_strerror", "ebcc_free", "ebcc_compress", "ebcc_decompress",
+    "ebcc_stream_info", "ebcc_compress_batch_dev", "ebcc_decompress_batch_dev", "ebcc_max_stream_bytes",
+    "ebcc_server_create", "ebcc_server_submit", "ebcc_server_poll", "ebcc_server_cancel",
+    "ebcc_server_destroy", "ebcc_dwt_fwd_dev", "ebcc_dwt_inv_dev", "ebcc_effective_levels",
+    "ebcc_quantise_dev", "ebcc_band_step", "ebcc_t1_encode_dev", "ebcc_t1_decode_dev", "ebcc_pcrd_dev",
+    "ebcc_spiht_encode_dev", "ebcc_spiht_decode_dev", "ebcc_spiht_prefix_recon_dev",
+    "ebcc_count_within_dev",
+]
+
+
+class EbccError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        super().__init__(f"{what}: {ERRORS.get(code, code)} ({code})")
+        self.code = code
+
+
+class ebcc_params(C.Structure):
+    _fields_ = [("levels", C.c_int), ("cblk_w", C.c_int), ("cblk_h", C.c_int), ("r0", C.c_double),
+                ("q", C.c_double), ("tol", C.c_double), ("spiht_guard_bits", C.c_int)]
+
+
+class ebcc_stats(C.Structure):
+    _fields_ = [("r_base", C.c_double), ("r_base1", C.c_double), ("iters_base", C.c_int),
+                ("iters_base1", C.c_int), ("iters_trunc", C.c_int), ("used_fallback", C.c_int),
+                ("guard_bits", C.c_int), ("n_escape", C.c_int), ("base_bytes", C.c_longlong),
+                ("res_bytes", C.c_longlong), ("total_bytes", C.c_longlong),
+                ("spiht_len_bytes", C.c_longlong), ("len_two", C.c_longlong), ("len_one", C.c_longlong),
+                ("q_base", C.c_double)]
+
+
+class ebcc_field_desc(C.Structure):
+    _fields_ = [("field", C.c_void_p), ("ny", C.c_size_t), ("nx", C.c_size_t), ("bound", C.c_double),
+                ("bound_kind", C.c_int)]
+
+
+class ebcc_out_desc(C.Structure):
+    _fields_ = [("stream", C.c_void_p), ("capacity", C.c_size_t), ("len", C.c_size_t), ("status", C.c_int),
+                ("stats", ebcc_stats)]
+
+
+class ebcc_stream_desc(C.Structure):
+    _fields_ = [("stream", C.c_void_p), ("len", C.c_size_t), ("ny", C.c_size_t), ("nx", C.c_size_t)]
+
+
+class ebcc_request(C.Structure):
+    _fields_ = [("kind", C.c_int), ("field", C.c_void_p), ("stream", C.c_void_p), ("stream_len", C.c_size_t),
+                ("ny", C.c_size_t), ("nx", C.c_size_t), ("bound", C.c_double), ("bound_kind", C.c_int)]
+
+
+class ebcc_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("stream", C.c_void_p), ("stream_len", C.c_size_t),
+                ("field", C.c_void_p), ("latency_s", C.c_double), ("queue_s", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library; raise if it was not built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIBPATH):
+            raise RuntimeError(f"EBCC CUDA library not built: {LIBPATH} (run __graft_entry__.build())")
+        L = C.CDLL(LIBPATH)
+        L.ebcc_strerror.restype = C.c_char_p
+        L.ebcc_max_stream_bytes.restype = C.c_size_t
+        L.ebcc_max_stream_bytes.argtypes = [C.c_size_t, C.c_size_t]
+        L.ebcc_band_step.restype = C.c_double
+        L.ebcc_band_step.argtypes = [C.c_int, C.c_int, C.c_int]
+        L.ebcc_effective_levels.argtypes = [C.c_size_t, C.c_size_t, C.c_int]
+        L.ebcc_compress.argtypes = [C.c_void_p, C.c_size_t, C.c_size_t, C.c_double, C.c_int,
+                                    C.POINTER(ebcc_params), C.POINTER(C.c_void_p), C.POINTER(C.c_size_t),
+                                    C.POINTER(ebcc_stats)]
+        L.ebcc_decompress.argtypes = [C.c_void_p, C.c_size_t, C.c_void_p, C.c_size_t, C.c_size_t]
+        L.ebcc_stream_info.argtypes = [C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t),
+                                       C.POINTER(C.c_double)]
+        L.ebcc_free.argtypes = [C.c_void_p]
+        L.ebcc_compress_batch_dev.argtypes = [C.POINTER(ebcc_field_desc), C.c_int, C.POINTER(ebcc_out_desc),
+                                              C.POINTER(ebcc_params), C.c_void_p]
+        L.ebcc_decompress_batch_dev.argtypes = [C.POINTER(ebcc_stream_desc), C.c_int, C.POINTER(C.c_void_p),
+                                                C.c_void_p]
+        L.ebcc_dwt_fwd_dev.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_size_t, C.c_int, C.c_double,
+                                       C.c_double, C.c_void_p]
+        L.ebcc_dwt_inv_dev.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_size_t, C.c_int, C.c_void_p]
+        L.ebcc_quantise_dev.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_size_t, C.c_int, C.c_int,
+                                        C.c_void_p]
+        L.ebcc_t1_encode_dev.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                         C.c_int] + [C.c_void_p] * 9
+        L.ebcc_t1_decode_dev.argtypes = [C.c_void_p] * 6 + [C.c_int] * 3 + [C.c_void_p] * 4
+        L.ebcc_pcrd_dev.argtypes = [C.c_void_p] * 4 + [C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p]
+        L.ebcc_spiht_encode_dev.argtypes = [C.c_void_p, C.c_size_t, C.c_size_t, C.c_int, C.c_void_p, C.c_size_t] + \
+            [C.c_void_p] * 6
+        L.ebcc_spiht_decode_dev.argtypes = [C.c_void_p, C.c_int64, C.c_size_t, C.c_size_t, C.c_int, C.c_int] + \
+            [C.c_void_p] * 4
+        L.ebcc_spiht_prefix_recon_dev.argtypes = [C.c_void_p] * 4 + [C.c_int64, C.c_size_t, C.c_int, C.c_void_p,
+                                                                     C.c_void_p]
+        L.ebcc_count_within_dev.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_double, C.c_double,
+                                            C.c_double, C.c_double, C.c_void_p, C.c_void_p]
+        L.ebcc_server_create.argtypes = [C.c_size_t, C.c_int, C.POINTER(ebcc_params), C.POINTER(C.c_void_p)]
+        L.ebcc_server_submit.argtypes = [C.c_void_p, C.POINTER(ebcc_request), C.POINTER(C.c_uint64)]
+        L.ebcc_server_poll.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.POINTER(ebcc_result)]
+        L.ebcc_server_cancel.argtypes = [C.c_void_p, C.c_uint64]
+        L.ebcc_server_destroy.argtypes = [C.c_void_p]
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != EBCC_OK:
+        raise EbccError(rc, what)
+
+
+def params(levels=5, cblk=(32, 32), r0=20.0, q=0.999, tol=1e-3, guard_bits=3) -> ebcc_params:
+    return ebcc_params(levels, cblk[0], cblk[1], r0, q, tol, guard_bits)
+
+
+def stats_dict(s: ebcc_stats) -> dict:
+    return {f: getattr(s, f) for f, _ in ebcc_stats._fields_}
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------ host API
+def ebcc_compress(field: np.ndarray, bound: float, kind: int = EBCC_BOUND_REL, p: ebcc_params | None = None):
+    """Compress a host float32 field; returns (bytes, stats dict)."""
+    x = np.ascontiguousarray(field, dtype=np.float32)
+    ny, nx = x.shape
+    out = C.c_void_p()
+    n = C.c_size_t()
+    st = ebcc_stats()
+    rc = lib().ebcc_compress(x.ctypes.data, ny, nx, bound, kind, C.byref(p) if p else None, C.byref(out),
+                             C.byref(n), C.byref(st))
+    _check(rc, "ebcc_compress")
+    data = C.string_at(out, n.value)
+    lib().ebcc_free(out)
+    return data, stats_dict(st)
+
+
+def ebcc_decompress(stream: bytes, ny: int, nx: int) -> np.ndarray:
+    buf = np.frombuffer(stream, np.uint8)
+    out = np.empty((ny, nx), np.float32)
+    _check(lib().ebcc_decompress(buf.ctypes.data, len(stream), out.ctypes.data, ny, nx), "ebcc_decompress")
+    return out
+
+
+def ebcc_stream_info(stream: bytes):
+    buf = np.frombuffer(stream, np.uint8)
+    ny, nx, b = C.c_size_t(), C.c_size_t(), C.c_double()
+    _check(lib().ebcc_stream_info(buf.ctypes.data, len(stream), C.byref(ny), C.byref(nx), C.byref(b)),
+           "ebcc_stream_info")
+    return ny.value, nx.value, b.value
+
+
+def ebcc_max_stream_bytes(ny: int, nx: int) -> int:
+    return lib().ebcc_max_stream_bytes(ny, nx)
+
+
+def ebcc_band_step(P: int, level: int, orient: int) -> float:
+    return lib().ebcc_band_step(P, level, orient)
+
+
+def ebcc_effective_levels(ny: int, nx: int, levels: int) -> int:
+    return lib().ebcc_effective_levels(ny, nx, levels)
+
+
+# ------------------------------------------------------------ device API
+def ebcc_compress_batch_dev(fields, bounds, kinds=None, p: ebcc_params | None = None, stream=None,
+                            outs=None):
+    """fields: list of 2-D float32 CUDA tensors; returns list of (uint8 CUDA
+    tensor holding the stream, length, status, stats dict)."""
+    import torch
+    n = len(fields)
+    kinds = kinds or [EBCC_BOUND_REL] * n
+    fd = (ebcc_field_desc * max(n, 1))()
+    od = (ebcc_out_desc * max(n, 1))()
+    bufs = []
+    for i, f in enumerate(fields):
+        ny, nx = f.shape
+        fd[i] = ebcc_field_desc(f.data_ptr(), ny, nx, float(bounds[i]), int(kinds[i]))
+        b = outs[i] if outs is not None else torch.empty(ebcc_max_stream_bytes(ny, nx), dtype=torch.uint8,
+                                                        device=f.device)
+        bufs.append(b)
+        od[i].stream = b.data_ptr()
+        od[i].capacity = b.numel()
+    rc = lib().ebcc_compress_batch_dev(fd, n, od, C.byref(p) if p else None, C.c_void_p(_stream(stream)))
+    res = [(bufs[i], od[i].len, od[i].status, stats_dict(od[i].stats)) for i in range(n)]
+    return rc, res
+
+
+def ebcc_decompress_batch_dev(streams, lens, shapes, outs, stream=None):
+    n = len(streams)
+    sd = (ebcc_stream_desc * max(n, 1))()
+    op = (C.c_void_p * max(n, 1))()
+    for i in range(n):
+        sd[i] = ebcc_stream_desc(streams[i].data_ptr(), int(lens[i]), shapes[i][0], shapes[i][1])
+        op[i] = outs[i].data_ptr()
+    return lib().ebcc_decompress_batch_dev(sd, n, op, C.c_void_p(_stream(stream)))
+
+
+def ebcc_dwt_fwd_dev(inp, out, levels: int, norm_min: float = 0.0, norm_range: float = 0.0, stream=None):
+    ny, nx = inp.shape
+    _check(lib().ebcc_dwt_fwd_dev(_ptr(inp), _ptr(out), ny, nx, levels, norm_min, norm_range,
+                                  C.c_void_p(_stream(stream))), "ebcc_dwt_fwd_dev")
+
+
+def ebcc_dwt_inv_dev(inp, out, levels: int, stream=None):
+    ny, nx = inp.shape
+    _check(lib().ebcc_dwt_inv_dev(_ptr(inp), _ptr(out), ny, nx, levels, C.c_void_p(_stream(stream))),
+           "ebcc_dwt_inv_dev")
+
+
+def ebcc_quantise_dev(coef, q, levels: int, P: int, stream=None):
+    ny, nx = coef.shape
+    _check(lib().ebcc_quantise_dev(_ptr(coef), _ptr(q), ny, nx, levels, P, C.c_void_p(_stream(stream))),
+           "ebcc_quantise_dev")
+
+
+def ebcc_t1_encode_dev(q, orient, w, h, cap, maxpass, out: dict, stream=None):
+    nblk = orient.numel()
+    return lib().ebcc_t1_encode_dev(_ptr(q), _ptr(orient), nblk, w, h, _ptr(out["bytes"]), cap, maxpass,
+                                    _ptr(out["K"]), _ptr(out["npass"]), _ptr(out["pass_len"]), _ptr(out["tail"]),
+                                    _ptr(out["tail_len"]), _ptr(out["dD"]), _ptr(out["D0"]), _ptr(out["spp"]),
+                                    C.c_void_p(_stream(stream)))
+
+
+def ebcc_t1_decode_dev(data, off, ln, orient, K, npass, w, h, mag, plane, neg, stream=None):
+    _check(lib().ebcc_t1_decode_dev(_ptr(data), _ptr(off), _ptr(ln), _ptr(orient), _ptr(K), _ptr(npass),
+                                    orient.numel(), w, h, _ptr(mag), _ptr(plane), _ptr(neg),
+                                    C.c_void_p(_stream(stream))), "ebcc_t1_decode_dev")
+
+
+def ebcc_pcrd_dev(npass, pass_len, dD, D0, maxpass, budget, npass_out, stream=None):
+    _check(lib().ebcc_pcrd_dev(_ptr(npass), _ptr(pass_len), _ptr(dD), _ptr(D0), npass.numel(), maxpass,
+                               float(budget), _ptr(npass_out), C.c_void_p(_stream(stream))), "ebcc_pcrd_dev")
+
+
+def ebcc_spiht_encode_dev(s, levels, out, nbits, nmax, sig_pos, lsp_idx, refine_start, stream=None):
+    ny, nx = s.shape
+    return lib().ebcc_spiht_encode_dev(_ptr(s), ny, nx, levels, _ptr(out), out.numel(), _ptr(nbits), _ptr(nmax),
+                                       _ptr(sig_pos), _ptr(lsp_idx), _ptr(refine_start),
+                                       C.c_void_p(_stream(stream)))
+
+
+def ebcc_spiht_decode_dev(data, nbits, ny, nx, levels, nmax, mag, plane, neg, stream=None):
+    _check(lib().ebcc_spiht_decode_dev(_ptr(data), int(nbits), ny, nx, levels, int(nmax), _ptr(mag), _ptr(plane),
+                                       _ptr(neg), C.c_void_p(_stream(stream))), "ebcc_spiht_decode_dev")
+
+
+def ebcc_spiht_prefix_recon_dev(s, sig_pos, lsp_idx, refine_start, nbits, step_exp, out, stream=None):
+    _check(lib().ebcc_spiht_prefix_recon_dev(_ptr(s), _ptr(sig_pos), _ptr(lsp_idx), _ptr(refine_start),
+                                             int(nbits), s.numel(), step_exp, _ptr(out),
+                                             C.c_void_p(_stream(stream))), "ebcc_spiht_prefix_recon_dev")
+
+
+def ebcc_count_within_dev(x, an_hat, mn, rng, eps_abs, guard, count_out, stream=None):
+    _check(lib().ebcc_count_within_dev(_ptr(x), _ptr(an_hat), x.numel(), mn, rng, eps_abs, guard, _ptr(count_out),
+                                       C.c_void_p(_stream(stream))), "ebcc_count_within_dev")

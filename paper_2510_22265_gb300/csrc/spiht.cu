@@ -1,0 +1,549 @@
+// SPIHT (Said & Pearlman 1996) on GB300 -- EBCC's residual layer (Materials
+// and Methods; Algorithm 1 enc_SPIHT, dec_SPIHT).
+//
+// Trees: an LL coefficient has as children the coefficients at the same place
+// in the coarsest HL, LH and HH bands; a detail coefficient at band position
+// (a, b) has the 2x2 block (2a.., 2b..) of the same orientation one level
+// finer, the last row / column of a band also taking the extra row / column an
+// odd-sized finer band has.
+//
+// Encoder: the set maxima (max |s| over all descendants, and over descendants
+// beyond the children) come from one full-grid kernel per level, bottom up.
+// Then one CTA per field runs the bit-planes.  Each list pass is processed in
+// chunks of 1024 entries: every thread evaluates its entry's tests, a
+// block-wide exclusive scan of (bits, LIP appends, LSP appends, next-wave
+// appends, stays) gives every output position, and the chunk's 1-bits are
+// gathered in a shared-memory window before being OR-ed into the stream.  A
+// sorting pass over the LIS runs as waves: the entries a pass appends form the
+// next wave, processed in append order -- exactly the order of the sequential
+// algorithm, where appended entries are visited later in the same pass.  The
+// encoder records, per coefficient, the bit offset of its sign bit and its
+// place in the LSP, and per plane where the refinement pass starts: enough to
+// reconstruct any prefix without decoding (spiht_prefix_recon).
+//
+// Decoder: one thread per field walks the lists (the bit positions depend on
+// the decoded bits).
+#include "ebcc_internal.cuh"
+
+namespace {
+
+struct SG {
+    int ny, nx, L;
+    int h[EBCC_MAX_LEVELS + 1], w[EBCC_MAX_LEVELS + 1];
+};
+
+SG make_sg(int ny, int nx, int L) {
+    SG g;
+    g.ny = ny; g.nx = nx; g.L = L;
+    for (int l = 0; l <= L; l++) {
+        g.h[l] = (int)(((long)ny + (1L << l) - 1) >> l);
+        g.w[l] = (int)(((long)nx + (1L << l) - 1) >> l);
+    }
+    return g;
+}
+
+__device__ __forceinline__ void band_box(const SG &g, int l, int o, int &y0, int &x0, int &bh, int &bw) {
+    y0 = (o == 1) ? 0 : g.h[l];
+    x0 = (o == 2) ? 0 : g.w[l];
+    bh = (o == 1) ? g.h[l] : g.h[l - 1] - g.h[l];
+    bw = (o == 2) ? g.w[l] : g.w[l - 1] - g.w[l];
+}
+
+__device__ __forceinline__ void locate(const SG &g, int i, int j, int &lev, int &o) {
+    for (int l = 1; l <= g.L; l++)
+        if (i >= g.h[l] || j >= g.w[l]) {
+            lev = l;
+            o = (i < g.h[l]) ? 1 : (j < g.w[l] ? 2 : 3);
+            return;
+        }
+    lev = g.L; o = 0;
+}
+
+__device__ int children(const SG &g, uint32_t idx, uint32_t *c) {
+    if (g.L == 0) return 0;
+    int i = (int)(idx / g.nx), j = (int)(idx - (uint32_t)i * g.nx), lev, o, n = 0;
+    locate(g, i, j, lev, o);
+    if (o == 0) {
+        for (int oo = 1; oo <= 3; oo++) {
+            int y0, x0, bh, bw;
+            band_box(g, g.L, oo, y0, x0, bh, bw);
+            if (i < bh && j < bw) c[n++] = (uint32_t)(y0 + i) * g.nx + x0 + j;
+        }
+        return n;
+    }
+    if (lev <= 1) return 0;
+    int y0, x0, bh, bw, cy0, cx0, cbh, cbw;
+    band_box(g, lev, o, y0, x0, bh, bw);
+    band_box(g, lev - 1, o, cy0, cx0, cbh, cbw);
+    int a = i - y0, b = j - x0;
+    int r1 = (a == bh - 1) ? 2 * a + 2 : 2 * a + 1;
+    int s1 = (b == bw - 1) ? 2 * b + 2 : 2 * b + 1;
+    for (int r = 2 * a; r <= r1 && r < cbh; r++)
+        for (int s = 2 * b; s <= s1 && s < cbw; s++) c[n++] = (uint32_t)(cy0 + r) * g.nx + cx0 + s;
+    return n;
+}
+
+// has descendants beyond the children (the set L is not empty)
+__device__ __forceinline__ bool has_L(const SG &g, uint32_t idx) {
+    int i = (int)(idx / g.nx), j = (int)(idx - (uint32_t)i * g.nx), lev, o;
+    locate(g, i, j, lev, o);
+    if (o != 0) return lev >= 3;
+    if (g.L < 2) return false;
+    return (j < g.w[g.L - 1] - g.w[g.L]) || (i < g.h[g.L - 1] - g.h[g.L]);
+}
+
+__device__ __forceinline__ uint32_t absi(int32_t v) { return (uint32_t)(v < 0 ? -v : v); }
+
+// maxima of one level's nodes (level l detail bands, or the LL band when l = 0)
+__global__ void maxima_kernel(SG g, int l, const int32_t *__restrict__ s, uint32_t *maxd, uint32_t *maxl) {
+    int nb = l == 0 ? 1 : 3;
+    int y0s[3], x0s[3], bhs[3], bws[3];
+    long cnt[4] = {0, 0, 0, 0};
+    for (int k = 0; k < nb; k++) {
+        if (l == 0) { y0s[k] = 0; x0s[k] = 0; bhs[k] = g.h[g.L]; bws[k] = g.w[g.L]; }
+        else band_box(g, l, k + 1, y0s[k], x0s[k], bhs[k], bws[k]);
+        cnt[k + 1] = cnt[k] + (long)bhs[k] * bws[k];
+    }
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < cnt[nb]; t += (long)gridDim.x * blockDim.x) {
+        int k = t < cnt[1] ? 0 : (t < cnt[2] ? 1 : 2);
+        long r = t - cnt[k];
+        int a = (int)(r / bws[k]), b = (int)(r - (long)a * bws[k]);
+        uint32_t idx = (uint32_t)(y0s[k] + a) * g.nx + x0s[k] + b;
+        uint32_t c[9];
+        int n = children(g, idx, c);
+        uint32_t md = 0, ml = 0;
+        for (int q = 0; q < n; q++) {
+            uint32_t cd = maxd[c[q]];
+            md = max(md, max(absi(s[c[q]]), cd));
+            ml = max(ml, cd);
+        }
+        maxd[idx] = md;
+        maxl[idx] = ml;
+    }
+}
+
+constexpr int ET = 1024;
+constexpr int NQ = 5;
+constexpr int WIN_WORDS = 640;  // >= 1024 entries * 19 bits / 32 + 2
+
+struct EncShared {
+    unsigned long long pos;
+    long long nlip, nlsp, nlis, nnext, nstay;
+    int wsum[ET / 32][NQ];
+    int tot[NQ];
+    uint32_t win[WIN_WORDS];
+    unsigned long long wbase;
+    int nmax_red[ET / 32];
+};
+
+// exclusive block scan of NQ quantities; results in v[], totals in sh.tot
+__device__ __forceinline__ void block_scan(int (&v)[NQ], EncShared &sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; q++) {
+        int x = v[q];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        incl[q] = x;
+        if (lane == 31) sh.wsum[wid][q] = x;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            int x = sh.wsum[lane][q];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            sh.wsum[lane][q] = x;  // inclusive over warps
+            if (lane == 31) sh.tot[q] = x;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NQ; q++) v[q] = incl[q] - v[q] + (wid ? sh.wsum[wid - 1][q] : 0);
+}
+
+__device__ __forceinline__ uint32_t bitmask(unsigned long long b) {
+    return 1u << ((((unsigned)(b >> 3)) & 3) * 8 + 7 - (unsigned)(b & 7));
+}
+
+// window for the chunk's bits [base, base + nbits): clear, (set), flush
+__device__ __forceinline__ void win_clear(EncShared &sh) {
+    for (int k = threadIdx.x; k < WIN_WORDS; k += ET) sh.win[k] = 0;
+}
+__device__ __forceinline__ void win_set(EncShared &sh, unsigned long long b) {
+    atomicOr(&sh.win[(b >> 5) - sh.wbase], bitmask(b));
+}
+__device__ __forceinline__ void win_flush(EncShared &sh, uint32_t *out32, unsigned long long cap_words,
+                                          unsigned long long end_bit, int *status) {
+    unsigned long long nw = ((end_bit + 31) >> 5) - sh.wbase;
+    for (unsigned long long k = threadIdx.x; k < nw && k < WIN_WORDS; k += ET) {
+        uint32_t v = sh.win[k];
+        if (!v) continue;
+        unsigned long long gw = sh.wbase + k;
+        if (gw < cap_words) atomicOr(&out32[gw], v);
+        else atomicOr(status, 1);
+    }
+}
+
+__global__ void __launch_bounds__(ET) encode_kernel(SG g, const int32_t *__restrict__ s, const uint32_t *__restrict__ maxd,
+                                                    const uint32_t *__restrict__ maxl, uint32_t *out32,
+                                                    unsigned long long cap_words, long long *nbits_out, int *nmax_out,
+                                                    uint32_t *sig_pos, uint32_t *lsp_idx, long long *refine_start,
+                                                    int *status, uint32_t *lip, uint32_t *lsp, uint32_t *lis,
+                                                    uint32_t *lis_new, uint32_t *wave_a, uint32_t *wave_b) {
+    __shared__ EncShared sh;
+    const int tid = threadIdx.x;
+    const int hL = g.h[g.L], wL = g.w[g.L];
+    const long nroot = (long)hL * wL;
+    // top plane from the LL roots (every coefficient is a root or below one)
+    uint32_t mx = 0;
+    for (long k = tid; k < nroot; k += ET) {
+        uint32_t idx = (uint32_t)(k / wL) * g.nx + (uint32_t)(k % wL);
+        mx = max(mx, max(absi(s[idx]), maxd[idx]));
+    }
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((tid & 31) == 0) sh.nmax_red[tid >> 5] = (int)mx;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t m = 0;
+        for (int k = 0; k < ET / 32; k++) m = max(m, (uint32_t)sh.nmax_red[k]);
+        sh.nmax_red[0] = m ? 31 - __clz(m) : -1;
+    }
+    __syncthreads();
+    const int nmax = sh.nmax_red[0];
+    // initial lists: LIP = LL row-major, LIS = LL nodes with descendants, type A
+    if (tid == 0) { sh.pos = 0; sh.nlip = nroot; sh.nlsp = 0; sh.nlis = 0; }
+    __syncthreads();
+    for (long base = 0; base < nroot; base += ET) {
+        long k = base + tid;
+        int v[NQ] = {0, 0, 0, 0, 0};
+        uint32_t idx = 0;
+        if (k < nroot) {
+            idx = (uint32_t)(k / wL) * g.nx + (uint32_t)(k % wL);
+            lip[k] = idx;
+            uint32_t c[9];
+            v[0] = children(g, idx, c) > 0;
+        }
+        block_scan(v, sh);
+        if (k < nroot && v[0] != (int)0x7FFFFFFF) {
+            uint32_t c[9];
+            if (children(g, idx, c) > 0) lis[sh.nlis + v[0]] = idx << 1;
+        }
+        __syncthreads();
+        if (tid == 0) sh.nlis += sh.tot[0];
+        __syncthreads();
+    }
+    for (int n = nmax; n >= 0; n--) {
+        const uint32_t T = 1u << n;
+        const long long lsp_before = sh.nlsp;
+        // ---- sorting pass: LIP
+        {
+            const long long nl = sh.nlip;
+            long long keep_n = 0;
+            for (long long base = 0; base < nl; base += ET) {
+                long long k = base + tid;
+                int v[NQ] = {0, 0, 0, 0, 0};
+                uint32_t x = 0;
+                bool sg = false;
+                if (k < nl) {
+                    x = lip[k];
+                    sg = absi(s[x]) >= T;
+                    v[0] = 1 + sg; v[1] = !sg; v[2] = sg;
+                }
+                if (tid == 0) sh.wbase = sh.pos >> 5;
+                win_clear(sh);
+                block_scan(v, sh);
+                const unsigned long long bp = sh.pos + v[0];
+                if (k < nl) {
+                    if (sg) {
+                        win_set(sh, bp);
+                        if (s[x] < 0) win_set(sh, bp + 1);
+                        sig_pos[x] = (uint32_t)(bp + 1);
+                        lsp_idx[x] = (uint32_t)(sh.nlsp + v[2]);
+                        lsp[sh.nlsp + v[2]] = x;
+                    } else {
+                        lip[keep_n + v[1]] = x;
+                    }
+                }
+                __syncthreads();
+                win_flush(sh, out32, cap_words, sh.pos + sh.tot[0], status);
+                keep_n += sh.tot[1];
+                __syncthreads();
+                if (tid == 0) { sh.pos += sh.tot[0]; sh.nlsp += sh.tot[2]; }
+                __syncthreads();
+            }
+            if (tid == 0) sh.nlip = keep_n;
+            __syncthreads();
+        }
+        // ---- sorting pass: LIS, in waves
+        {
+            const uint32_t *cur = lis;
+            long long ncur = sh.nlis;
+            uint32_t *nxt = wave_a;
+            if (tid == 0) sh.nstay = 0;
+            __syncthreads();
+            while (ncur > 0) {
+                if (tid == 0) sh.nnext = 0;
+                __syncthreads();
+                for (long long base = 0; base < ncur; base += ET) {
+                    long long k = base + tid;
+                    int v[NQ] = {0, 0, 0, 0, 0};
+                    uint32_t e = 0, idx = 0, c[9];
+                    int nc = 0;
+                    bool sg = false;
+                    uint32_t sigmask = 0;
+                    if (k < ncur) {
+                        e = cur[k];
+                        idx = e >> 1;
+                        v[0] = 1;
+                        if ((e & 1) == 0) {  // type A: S_n(D)
+                            sg = maxd[idx] >= T;
+                            if (sg) {
+                                nc = children(g, idx, c);
+                                for (int q = 0; q < nc; q++) {
+                                    bool cs = absi(s[c[q]]) >= T;
+                                    sigmask |= (uint32_t)cs << q;
+                                    v[0] += 1 + cs; v[1] += !cs; v[2] += cs;
+                                }
+                                v[3] = has_L(g, idx);
+                            } else {
+                                v[4] = 1;
+                            }
+                        } else {  // type B: S_n(L)
+                            sg = maxl[idx] >= T;
+                            if (sg) { nc = children(g, idx, c); v[3] = nc; }
+                            else v[4] = 1;
+                        }
+                    }
+                    if (tid == 0) sh.wbase = sh.pos >> 5;
+                    win_clear(sh);
+                    block_scan(v, sh);
+                    if (k < ncur) {
+                        unsigned long long bp = sh.pos + v[0];
+                        if (!sg) {
+                            lis_new[sh.nstay + v[4]] = e;
+                        } else if ((e & 1) == 0) {
+                            win_set(sh, bp++);
+                            long long li = sh.nlip + v[1], ls = sh.nlsp + v[2];
+                            for (int q = 0; q < nc; q++) {
+                                if ((sigmask >> q) & 1) {
+                                    win_set(sh, bp);
+                                    if (s[c[q]] < 0) win_set(sh, bp + 1);
+                                    sig_pos[c[q]] = (uint32_t)(bp + 1);
+                                    lsp_idx[c[q]] = (uint32_t)ls;
+                                    lsp[ls++] = c[q];
+                                    bp += 2;
+                                } else {
+                                    lip[li++] = c[q];
+                                    bp += 1;
+                                }
+                            }
+                            if (v[3] != (int)0x7FFFFFFF && has_L(g, idx)) nxt[sh.nnext + v[3]] = (idx << 1) | 1;
+                        } else {
+                            win_set(sh, bp);
+                            for (int q = 0; q < nc; q++) nxt[sh.nnext + v[3] + q] = c[q] << 1;
+                        }
+                    }
+                    __syncthreads();
+                    win_flush(sh, out32, cap_words, sh.pos + sh.tot[0], status);
+                    __syncthreads();
+                    if (tid == 0) {
+                        sh.pos += sh.tot[0]; sh.nlip += sh.tot[1]; sh.nlsp += sh.tot[2];
+                        sh.nnext += sh.tot[3]; sh.nstay += sh.tot[4];
+                    }
+                    __syncthreads();
+                }
+                cur = nxt;
+                ncur = sh.nnext;
+                nxt = (nxt == wave_a) ? wave_b : wave_a;
+            }
+            // the stayers become the LIS of the next plane
+            const long long ns = sh.nstay;
+            for (long long k = tid; k < ns; k += ET) lis[k] = lis_new[k];
+            __syncthreads();
+            if (tid == 0) sh.nlis = ns;
+            __syncthreads();
+        }
+        // ---- refinement pass over the LSP entries of earlier planes
+        {
+            if (tid == 0) refine_start[n] = (long long)sh.pos;
+            for (long long base = 0; base < lsp_before; base += ET) {
+                long long k = base + tid;
+                if (tid == 0) sh.wbase = (sh.pos + base) >> 5;
+                win_clear(sh);
+                __syncthreads();
+                if (k < lsp_before && ((absi(s[lsp[k]]) >> n) & 1)) win_set(sh, sh.pos + k);
+                __syncthreads();
+                long long end = base + ET < lsp_before ? base + ET : lsp_before;
+                win_flush(sh, out32, cap_words, sh.pos + end, status);
+                __syncthreads();
+            }
+            if (tid == 0) sh.pos += lsp_before;
+            __syncthreads();
+        }
+    }
+    if (tid == 0) {
+        *nbits_out = (long long)sh.pos;
+        *nmax_out = nmax;
+        if (((sh.pos + 7) >> 3) > cap_words * 4) atomicOr(status, 1);
+    }
+}
+
+// ------------------------------------------------------------ decoder
+struct BitR {
+    const uint8_t *buf;
+    long long pos, n;
+    __device__ __forceinline__ int get() {
+        if (pos >= n) return -1;
+        int b = (buf[pos >> 3] >> (7 - (pos & 7))) & 1;
+        pos++;
+        return b;
+    }
+};
+
+__global__ void decode_kernel(SG g, const uint8_t *in, long long nbits, int nmax, int32_t *mag, int8_t *plane,
+                              uint8_t *neg, float *coef, int e, uint32_t *lip, uint32_t *lsp, uint32_t *lis,
+                              long long lis_cap) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int hL = g.h[g.L], wL = g.w[g.L];
+    long long nlip = 0, nlsp = 0, nlis = 0;
+    uint32_t c[9];
+    for (int a = 0; a < hL; a++)
+        for (int b = 0; b < wL; b++) {
+            uint32_t idx = (uint32_t)a * g.nx + b;
+            lip[nlip++] = idx;
+            if (children(g, idx, c) > 0) lis[nlis++] = idx << 1;
+        }
+    BitR r{in, 0, nbits};
+    for (int n = nmax; n >= 0; n--) {
+        long long lsp_before = nlsp, keep = 0;
+        int bit, sg;
+        for (long long k = 0; k < nlip; k++) {
+            uint32_t x = lip[k];
+            if ((bit = r.get()) < 0) goto done;
+            if (bit) {
+                if ((sg = r.get()) < 0) goto done;
+                neg[x] = (uint8_t)sg; mag[x] = 1 << n; plane[x] = (int8_t)n;
+                lsp[nlsp++] = x;
+            } else {
+                lip[keep++] = x;
+            }
+        }
+        nlip = keep;
+        for (long long k = 0; k < nlis; k++) {
+            uint32_t en = lis[k];
+            if (en == 0xFFFFFFFFu) continue;
+            uint32_t x = en >> 1;
+            if ((bit = r.get()) < 0) goto done;
+            if (!bit) continue;
+            int nc = children(g, x, c);
+            if ((en & 1) == 0) {
+                for (int q = 0; q < nc; q++) {
+                    int b;
+                    if ((b = r.get()) < 0) goto done;
+                    if (b) {
+                        if ((sg = r.get()) < 0) goto done;
+                        neg[c[q]] = (uint8_t)sg; mag[c[q]] = 1 << n; plane[c[q]] = (int8_t)n;
+                        lsp[nlsp++] = c[q];
+                    } else {
+                        lip[nlip++] = c[q];
+                    }
+                }
+                lis[k] = 0xFFFFFFFFu;
+                if (has_L(g, x) && nlis < lis_cap) lis[nlis++] = (x << 1) | 1;
+            } else {
+                for (int q = 0; q < nc && nlis < lis_cap; q++) lis[nlis++] = c[q] << 1;
+                lis[k] = 0xFFFFFFFFu;
+            }
+        }
+        keep = 0;
+        for (long long k = 0; k < nlis; k++)
+            if (lis[k] != 0xFFFFFFFFu) lis[keep++] = lis[k];
+        nlis = keep;
+        for (long long k = 0; k < lsp_before; k++) {
+            if ((bit = r.get()) < 0) goto done;
+            mag[lsp[k]] |= bit << n;
+            plane[lsp[k]] = (int8_t)n;
+        }
+    }
+done:
+    return;
+}
+
+__global__ void dequant_kernel(const int32_t *mag, const int8_t *plane, const uint8_t *neg, size_t n, int e,
+                               float *coef) {
+    const float step = ldexpf(1.0f, e);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        int p = plane[i];
+        float v = p >= 0 ? deq((uint32_t)mag[i], p, step) : 0.0f;
+        coef[i] = neg[i] && p >= 0 ? -v : v;
+    }
+}
+
+}  // namespace
+
+size_t spiht_work_bytes(size_t n) { return (size_t)4 * n * (2 + 2 + 4) + 256; }
+
+void spiht_work_carve(uint8_t *base, size_t n, SpihtWork *w) {
+    uint32_t *p = (uint32_t *)(((uintptr_t)base + 255) & ~(uintptr_t)255);
+    w->maxd = p; p += n;
+    w->maxl = p; p += n;
+    w->lip = p; p += n;
+    w->lsp = p; p += n;
+    w->lis_a = p; p += 2 * n;  // lis (n) + lis_new (n)
+    w->lis_b = p; p += 2 * n;  // wave_a (n) + wave_b (n)
+    w->tmp = w->lis_a;
+}
+
+int spiht_encode(const int32_t *s, int ny, int nx, int L, uint8_t *out, size_t cap_bytes, int64_t *nbits_dev,
+                 int32_t *nmax_dev, uint32_t *sig_pos, uint32_t *lsp_idx, int64_t *refine_start, int32_t *status_dev,
+                 const SpihtWork &w, cudaStream_t st) {
+    const size_t n = (size_t)ny * nx;
+    if (n >= 0x7FFFFFFFu) return EBCC_EINVAL;
+    SG g = make_sg(ny, nx, L);
+    CK(cudaMemsetAsync(w.maxd, 0, 2 * n * sizeof(uint32_t), st));
+    CK(cudaMemsetAsync(sig_pos, 0xFF, n * sizeof(uint32_t), st));
+    CK(cudaMemsetAsync(lsp_idx, 0xFF, n * sizeof(uint32_t), st));
+    CK(cudaMemsetAsync(refine_start, 0, 32 * sizeof(int64_t), st));
+    CK(cudaMemsetAsync(out, 0, cap_bytes & ~(size_t)3, st));
+    for (int l = 2; l <= L; l++) {
+        maxima_kernel<<<152 * 4, 256, 0, st>>>(g, l, s, w.maxd, w.maxl);
+        CK(cudaGetLastError());
+    }
+    if (L >= 1) {
+        maxima_kernel<<<152, 256, 0, st>>>(g, 0, s, w.maxd, w.maxl);
+        CK(cudaGetLastError());
+    }
+    encode_kernel<<<1, ET, 0, st>>>(g, s, w.maxd, w.maxl, (uint32_t *)out, cap_bytes / 4, (long long *)nbits_dev,
+                                    nmax_dev, sig_pos, lsp_idx, (long long *)refine_start, status_dev, w.lip, w.lsp,
+                                    w.lis_a, w.lis_a + n, w.lis_b, w.lis_b + n);
+    CK(cudaGetLastError());
+    return EBCC_OK;
+}
+
+int spiht_decode(const uint8_t *in, int64_t nbits, int ny, int nx, int L, int nmax, int32_t *mag, int8_t *plane,
+                 uint8_t *neg, float *coef_out, int step_exp, const SpihtWork &w, cudaStream_t st) {
+    const size_t n = (size_t)ny * nx;
+    SG g = make_sg(ny, nx, L);
+    CK(cudaMemsetAsync(mag, 0, n * sizeof(int32_t), st));
+    CK(cudaMemsetAsync(plane, 0xFF, n, st));
+    CK(cudaMemsetAsync(neg, 0, n, st));
+    if (nmax >= 0 && nbits > 0) {
+        decode_kernel<<<1, 32, 0, st>>>(g, in, nbits, nmax, mag, plane, neg, coef_out, step_exp, w.lip, w.lsp,
+                                        w.lis_a, (long long)(4 * n));
+        CK(cudaGetLastError());
+    }
+    if (coef_out) {
+        dequant_kernel<<<152 * 4, 256, 0, st>>>(mag, plane, neg, n, step_exp, coef_out);
+        CK(cudaGetLastError());
+    }
+    return EBCC_OK;
+}

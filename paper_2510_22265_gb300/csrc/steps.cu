@@ -1,0 +1,209 @@
+// Step-level entry points of the C ABI: each runs one kernel stage of the hot
+// path on caller-owned device buffers so it can be checked against the CPU
+// oracle on its own.  Temporary scratch is allocated per call.
+#include <math.h>
+#include <vector>
+#include "ebcc_internal.cuh"
+
+namespace {
+struct Tmp {
+    std::vector<void *> ptrs;
+    ~Tmp() {
+        for (void *p : ptrs) cudaFree(p);
+    }
+    template <typename T>
+    int get(T **p, size_t n) {
+        void *q = nullptr;
+        CK(cudaMalloc(&q, n * sizeof(T) + 16));
+        ptrs.push_back(q);
+        *p = (T *)q;
+        return EBCC_OK;
+    }
+};
+
+int shape_ok(size_t ny, size_t nx) {
+    return (ny == 0 || nx == 0 || ny > (1u << 30) || nx > (1u << 30) || ny * nx >= 0x7FFFFFFFull) ? EBCC_EINVAL
+                                                                                             : EBCC_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int ebcc_dwt_fwd_dev(const float *in, float *out, size_t ny, size_t nx, int levels, double norm_min,
+                     double norm_range, void *stream) {
+    RC(shape_ok(ny, nx));
+    if (levels < 0 || !in || !out) return EBCC_EINVAL;
+    int L = effective_levels((int)ny, (int)nx, levels);
+    Tmp t;
+    float *s1, *s2;
+    RC(t.get(&s1, ((ny + 1) / 2) * ((nx + 1) / 2) + 16));
+    RC(t.get(&s2, ((ny + 3) / 4) * ((nx + 3) / 4) + 16));
+    double inv = norm_range > 0 ? 1.0 / norm_range : 0.0;
+    RC(dwt_forward(in, out, s1, s2, (int)ny, (int)nx, L, norm_min, inv, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    return EBCC_OK;
+}
+
+int ebcc_dwt_inv_dev(const float *in, float *out, size_t ny, size_t nx, int levels, void *stream) {
+    RC(shape_ok(ny, nx));
+    if (levels < 0 || !in || !out) return EBCC_EINVAL;
+    int L = effective_levels((int)ny, (int)nx, levels);
+    Tmp t;
+    float *s1, *s2;
+    RC(t.get(&s1, ((ny + 1) / 2) * ((nx + 1) / 2) + 16));
+    RC(t.get(&s2, ((ny + 3) / 4) * ((nx + 3) / 4) + 16));
+    InvFinal fin{-1, nullptr, nullptr, nullptr};
+    RC(dwt_inverse_ex(in, out, s1, s2, (int)ny, (int)nx, L, fin, 0.0, 1.0, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    return EBCC_OK;
+}
+
+int ebcc_quantise_dev(const float *coef, int32_t *q, size_t ny, size_t nx, int levels, int P, void *stream) {
+    RC(shape_ok(ny, nx));
+    if (levels < 0 || P < 1 || P > 30 || !coef || !q) return EBCC_EINVAL;
+    FieldGeom g;
+    make_geom(&g, (int)ny, (int)nx, levels, 32, 32, P);
+    RC(quantise_base(coef, q, g, 0, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    return EBCC_OK;
+}
+
+int ebcc_t1_encode_dev(const int32_t *q, const int32_t *orient, int nblk, int w, int h, uint8_t *bytes, int cap,
+                       int maxpass, int32_t *K, int32_t *npass, int32_t *pass_len, uint32_t *tail, int32_t *tail_len,
+                       int64_t *dD, int64_t *D0, uint8_t *spp, void *stream) {
+    if (nblk < 0 || w < 1 || w > 64 || h < 1 || h > 64 || cap < 1 || maxpass < 1 || !q || !orient) return EBCC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int32_t> ho(nblk);
+    if (nblk) CK(cudaMemcpy(ho.data(), orient, nblk * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    std::vector<BlockDesc> bd(nblk);
+    for (int k = 0; k < nblk; k++) {
+        if (ho[k] < 0 || ho[k] > 3) return EBCC_EINVAL;
+        bd[k].off = (long long)k * w * h; bd[k].stride = w; bd[k].w = w; bd[k].h = h; bd[k].orient = ho[k];
+        bd[k].delta = 1.0f;
+    }
+    Tmp t;
+    BlockDesc *dbd;
+    int32_t *status;
+    RC(t.get(&dbd, nblk + 1));
+    RC(t.get(&status, 4));
+    if (nblk) CK(cudaMemcpy(dbd, bd.data(), nblk * sizeof(BlockDesc), cudaMemcpyHostToDevice));
+    CK(cudaMemset(status, 0, 4));
+    T1Out o{bytes, cap, maxpass, K, npass, pass_len, tail, tail_len, dD, D0, status};
+    RC(t1_encode_blocks(const_cast<int32_t *>(q), dbd, nblk, w, h, o, 0, spp, st));
+    int hs = 0;
+    CK(cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return hs ? EBCC_ECAPACITY : EBCC_OK;
+}
+
+int ebcc_t1_decode_dev(const uint8_t *bytes, const int64_t *off, const int32_t *len, const int32_t *orient,
+                       const int32_t *K, const int32_t *npass, int nblk, int w, int h, int32_t *mag, int8_t *plane,
+                       uint8_t *neg, void *stream) {
+    if (nblk < 0 || w < 1 || w > 64 || h < 1 || h > 64 || !orient) return EBCC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int32_t> ho(nblk);
+    if (nblk) CK(cudaMemcpy(ho.data(), orient, nblk * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    std::vector<BlockDesc> bd(nblk);
+    for (int k = 0; k < nblk; k++) {
+        if (ho[k] < 0 || ho[k] > 3) return EBCC_EINVAL;
+        bd[k].off = (long long)k * w * h; bd[k].stride = w; bd[k].w = w; bd[k].h = h; bd[k].orient = ho[k];
+        bd[k].delta = 1.0f;
+    }
+    Tmp t;
+    BlockDesc *dbd;
+    RC(t.get(&dbd, nblk + 1));
+    if (nblk) CK(cudaMemcpy(dbd, bd.data(), nblk * sizeof(BlockDesc), cudaMemcpyHostToDevice));
+    RC(t1_decode_blocks(bytes, off, len, dbd, K, npass, nblk, w, h, nullptr, mag, plane, neg, st));
+    CK(cudaStreamSynchronize(st));
+    return EBCC_OK;
+}
+
+int ebcc_pcrd_dev(const int32_t *npass, const int32_t *pass_len, const int64_t *dD, const int64_t *D0, int nblk,
+                  int maxpass, double budget, int32_t *npass_out, void *stream) {
+    if (nblk < 0 || maxpass < 1 || maxpass > T1_MAXPASS || !(budget >= 0)) return EBCC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    Tmp t;
+    Hulls hl;
+    hl.maxpt = T1_MAXPASS + 1;
+    double *db;
+    Sel *sel;
+    RC(t.get(&hl.nh, nblk + 1));
+    RC(t.get(&hl.pt, (size_t)(nblk + 1) * hl.maxpt));
+    RC(t.get(&hl.rate, (size_t)(nblk + 1) * hl.maxpt));
+    RC(t.get(&hl.key, (size_t)(nblk + 1) * hl.maxpt));
+    RC(t.get(&db, 1));
+    RC(t.get(&sel, 1));
+    CK(cudaMemcpyAsync(db, &budget, 8, cudaMemcpyHostToDevice, st));
+    RC(pcrd_hulls(npass, pass_len, dD, D0, nblk, maxpass, hl, st));
+    RC(pcrd_select(hl, nblk, db, sel, st));
+    RC(pcrd_npass(hl, nblk, sel, npass_out, st));
+    CK(cudaStreamSynchronize(st));
+    return EBCC_OK;
+}
+
+int ebcc_spiht_encode_dev(const int32_t *s, size_t ny, size_t nx, int levels, uint8_t *out, size_t cap_bytes,
+                          int64_t *nbits_out, int32_t *nmax_out, uint32_t *sig_pos, uint32_t *lsp_idx,
+                          int64_t *refine_start, void *stream) {
+    RC(shape_ok(ny, nx));
+    if (levels < 0 || !s || !out) return EBCC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = ny * nx;
+    int L = effective_levels((int)ny, (int)nx, levels);
+    Tmp t;
+    uint8_t *w;
+    int32_t *status;
+    RC(t.get(&w, spiht_work_bytes(n)));
+    RC(t.get(&status, 4));
+    SpihtWork sw;
+    spiht_work_carve(w, n, &sw);
+    CK(cudaMemsetAsync(status, 0, 4, st));
+    RC(spiht_encode(s, (int)ny, (int)nx, L, out, cap_bytes, nbits_out, nmax_out, sig_pos, lsp_idx, refine_start,
+                    status, sw, st));
+    int hs = 0;
+    CK(cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return hs ? EBCC_ECAPACITY : EBCC_OK;
+}
+
+int ebcc_spiht_decode_dev(const uint8_t *in, int64_t nbits, size_t ny, size_t nx, int levels, int nmax, int32_t *mag,
+                          int8_t *plane, uint8_t *neg, void *stream) {
+    RC(shape_ok(ny, nx));
+    if (levels < 0 || nbits < 0 || nmax > 30) return EBCC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = ny * nx;
+    int L = effective_levels((int)ny, (int)nx, levels);
+    Tmp t;
+    uint8_t *w;
+    RC(t.get(&w, spiht_work_bytes(n)));
+    SpihtWork sw;
+    spiht_work_carve(w, n, &sw);
+    RC(spiht_decode(in, nbits, (int)ny, (int)nx, L, nmax, mag, plane, neg, nullptr, 0, sw, st));
+    CK(cudaStreamSynchronize(st));
+    return EBCC_OK;
+}
+
+int ebcc_spiht_prefix_recon_dev(const int32_t *s, const uint32_t *sig_pos, const uint32_t *lsp_idx,
+                                const int64_t *refine_start, int64_t nbits, size_t n, int step_exp, float *out,
+                                void *stream) {
+    if (!s || !sig_pos || !lsp_idx || !refine_start || !out || nbits < 0) return EBCC_EINVAL;
+    RC(spiht_prefix_recon(s, sig_pos, lsp_idx, refine_start, nullptr, nbits, n, step_exp, out, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    return EBCC_OK;
+}
+
+int ebcc_count_within_dev(const float *x, const float *an_hat, size_t n, double mn, double range, double eps_abs,
+                          double guard, int64_t *count_out, void *stream) {
+    if (!x || !an_hat || !count_out || !(range > 0) || !(eps_abs > guard)) return EBCC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    Tmp t;
+    float2 *b;
+    RC(t.get(&b, n + 1));
+    RC(make_bounds(x, n, mn, range, eps_abs, guard, b, st));
+    CK(cudaMemsetAsync(count_out, 0, 8, st));
+    InvFinal fin{1, b, nullptr, (unsigned long long *)count_out};
+    RC(dwt_inverse_ex(an_hat, nullptr, nullptr, nullptr, 1, (int)n, 0, fin, 0.0, 1.0, st));
+    CK(cudaStreamSynchronize(st));
+    return EBCC_OK;
+}
+
+}  // extern "C"

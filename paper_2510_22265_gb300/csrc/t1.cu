@@ -1,0 +1,612 @@
+// EBCOT tier-1 coding on GB300 (T.800 Annex D, default mode switches) with
+// the MQ arithmetic coder of Annex C -- EBCC's base layer is JPEG2000
+// (Materials and Methods).
+//
+// One warp per code-block.  The warp stages the block's magnitudes (and sign,
+// trace flag) in shared memory, finds the number of bit-planes with a warp max,
+// and keeps the coding state as one 64-bit word per row for significance,
+// visited, refined and sign.  Lane 0 runs the serial chain -- context formation
+// from the row words (8-neighbour pattern -> context through 256-entry tables)
+// and the MQ coder in registers -- skipping whole stripe columns with nothing
+// to code by word masks.  At every pass end it records what the rate search of
+// Algorithm 1 needs: the length of the stream terminated there (flushed copy of
+// the coder state, with its tail bytes) and the pass's decrease of squared error
+// in (step/2)^2 units.  The warp then writes the significance-pass trace flags
+// back with coalesced stores.
+#include <mutex>
+#include "ebcc_internal.cuh"
+
+namespace {
+
+// T.800 Table C.2 (this library's own copy): Qe | NMPS << 16 | NLPS << 24, SWITCH
+__constant__ uint32_t c_mq[47];
+__constant__ uint8_t c_mqsw[47];
+// context tables: significance context by orientation and 8-neighbour pattern;
+// sign context (bits 0-3) and XOR bit (bit 4) by the 4-neighbour sign pattern
+__constant__ uint8_t c_sigctx[4][256];
+__constant__ uint8_t c_signctx[256];
+
+constexpr int WARPS = 4;
+
+struct MQEnc {
+    uint32_t A, C, B;
+    int CT, bp, cap, overflow;
+    uint8_t *out;
+
+    __device__ void init(uint8_t *o, int c) {
+        A = 0x8000; C = 0; CT = 12; bp = -1; B = 0; out = o; cap = c; overflow = 0;
+    }
+    __device__ __forceinline__ void put(int i, uint32_t v) {
+        if (i >= cap) overflow = 1;
+        else if (i >= 0) out[i] = (uint8_t)v;
+    }
+    __device__ __forceinline__ void byteout() {
+        if (B == 0xFF) {
+            bp++; B = (C >> 20) & 0xFF; put(bp, B); C &= 0xFFFFF; CT = 7;
+        } else if (C < 0x8000000) {
+            bp++; B = (C >> 19) & 0xFF; put(bp, B); C &= 0x7FFFF; CT = 8;
+        } else {
+            B = B + 1;
+            put(bp, B);
+            if (B == 0xFF) {
+                C &= 0x7FFFFFF;
+                bp++; B = (C >> 20) & 0xFF; put(bp, B); C &= 0xFFFFF; CT = 7;
+            } else {
+                bp++; B = (C >> 19) & 0xFF; put(bp, B); C &= 0x7FFFF; CT = 8;
+            }
+        }
+    }
+    __device__ __forceinline__ void encode(uint8_t *I, uint8_t *M, int cx, int d) {
+        int i = I[cx];
+        uint32_t e = c_mq[i], qe = e & 0xFFFF;
+        A -= qe;
+        if (d == M[cx]) {
+            if (A & 0x8000) { C += qe; return; }
+            if (A < qe) A = qe; else C += qe;
+            I[cx] = (uint8_t)((e >> 16) & 0xFF);
+        } else {
+            if (A < qe) C += qe; else A = qe;
+            if (c_mqsw[i]) M[cx] ^= 1;
+            I[cx] = (uint8_t)(e >> 24);
+        }
+        do {
+            A <<= 1; C <<= 1; CT--;
+            if (CT == 0) byteout();
+        } while (!(A & 0x8000));
+    }
+    // terminate a copy of the state (SETBITS, two BYTEOUTs, drop a final 0xFF)
+    __device__ int trunc(uint32_t &tail, int &tl) const {
+        uint32_t a = A, c = C, b = B;
+        int ct = CT, li = bp < 0 ? -1 : 0;
+        uint32_t loc[4] = {b, 0, 0, 0};
+        uint32_t tempc = c + a;
+        c |= 0xFFFF;
+        if (c >= tempc) c -= 0x8000;
+        for (int k = 0; k < 2; k++) {
+            c <<= ct;
+            uint32_t cb = li >= 0 ? loc[li] : 0;
+            if (cb == 0xFF) {
+                li++; loc[li] = (c >> 20) & 0xFF; c &= 0xFFFFF; ct = 7;
+            } else if (c < 0x8000000) {
+                li++; loc[li] = (c >> 19) & 0xFF; c &= 0x7FFFF; ct = 8;
+            } else {
+                cb = cb + 1;
+                if (li >= 0) loc[li] = cb;
+                if (cb == 0xFF) {
+                    c &= 0x7FFFFFF;
+                    li++; loc[li] = (c >> 20) & 0xFF; c &= 0xFFFFF; ct = 7;
+                } else {
+                    li++; loc[li] = (c >> 19) & 0xFF; c &= 0x7FFFF; ct = 8;
+                }
+            }
+        }
+        int end = (li >= 0 && loc[li] != 0xFF) ? li + 1 : li;
+        if (end < 0) end = 0;
+        tail = 0;
+        for (int k = 0; k < end; k++) tail |= (loc[k] & 0xFF) << (8 * k);
+        tl = end;
+        return (bp < 0 ? 0 : bp) + end;
+    }
+};
+
+struct MQDec {
+    uint32_t A, C;
+    int CT, bp, len;
+    const uint8_t *in;
+    __device__ __forceinline__ uint32_t byte(int i) const { return i < len ? in[i] : 0xFF; }
+    __device__ __forceinline__ void bytein() {
+        if (byte(bp) == 0xFF) {
+            if (byte(bp + 1) > 0x8F) { C += 0xFF00; CT = 8; }
+            else { bp++; C += byte(bp) << 9; CT = 7; }
+        } else {
+            bp++; C += byte(bp) << 8; CT = 8;
+        }
+    }
+    __device__ void init(const uint8_t *p, int l) {
+        in = p; len = l; bp = 0;
+        C = byte(0) << 16;
+        bytein();
+        C <<= 7; CT -= 7; A = 0x8000;
+    }
+    __device__ __forceinline__ int decode(uint8_t *I, uint8_t *M, int cx) {
+        int i = I[cx], D;
+        uint32_t e = c_mq[i], qe = e & 0xFFFF;
+        A -= qe;
+        if ((C >> 16) < qe) {
+            if (A < qe) { A = qe; D = M[cx]; I[cx] = (uint8_t)((e >> 16) & 0xFF); }
+            else { A = qe; D = 1 - M[cx]; if (c_mqsw[i]) M[cx] ^= 1; I[cx] = (uint8_t)(e >> 24); }
+        } else {
+            C -= qe << 16;
+            if (A & 0x8000) return M[cx];
+            if (A < qe) { D = 1 - M[cx]; if (c_mqsw[i]) M[cx] ^= 1; I[cx] = (uint8_t)(e >> 24); }
+            else { D = M[cx]; I[cx] = (uint8_t)((e >> 16) & 0xFF); }
+        }
+        do {
+            if (CT == 0) bytein();
+            A <<= 1; C <<= 1; CT--;
+        } while (!(A & 0x8000));
+        return D;
+    }
+};
+
+__device__ __forceinline__ void reset_ctx(uint8_t *I, uint8_t *M) {
+    for (int k = 0; k < 19; k++) { I[k] = 0; M[k] = 0; }
+    I[0] = 4; I[17] = 3; I[18] = 46;
+}
+
+// 3-bit window (columns j-1, j, j+1) of a row word
+__device__ __forceinline__ uint32_t win(uint64_t w, int j) {
+    return (uint32_t)((j == 0 ? (w << 1) : (w >> (j - 1))) & 7);
+}
+
+struct Blk {  // shared-memory state of one code-block
+    uint64_t *sig, *vis, *ref, *neg;
+    int w, h;
+    __device__ __forceinline__ uint32_t nbr(int r, int j) const {
+        uint32_t up = r > 0 ? win(sig[r - 1], j) : 0;
+        uint32_t mid = win(sig[r], j);
+        uint32_t dn = r + 1 < h ? win(sig[r + 1], j) : 0;
+        return up | ((mid & 1) << 3) | ((mid >> 2) << 4) | (dn << 5);
+    }
+    // sign pattern: sigL negL sigR negR sigU negU sigD negD
+    __device__ __forceinline__ uint32_t signpat(int r, int j) const {
+        uint32_t ms = win(sig[r], j), mn = win(neg[r], j);
+        uint32_t us = r > 0 ? (uint32_t)(sig[r - 1] >> j) & 1 : 0, un = r > 0 ? (uint32_t)(neg[r - 1] >> j) & 1 : 0;
+        uint32_t ds = r + 1 < h ? (uint32_t)(sig[r + 1] >> j) & 1 : 0;
+        uint32_t dn = r + 1 < h ? (uint32_t)(neg[r + 1] >> j) & 1 : 0;
+        return (ms & 1) | ((mn & 1) << 1) | ((ms >> 2) << 2) | ((mn >> 2) << 3) | (us << 4) | (un << 5) |
+               (ds << 6) | (dn << 7);
+    }
+};
+
+__device__ __forceinline__ int64_t rec2(int64_t m, int p) { return 2 * ((m >> p) << p) + ((int64_t)1 << p); }
+
+// per-warp dynamic shared memory for blocks of at most maxn coefficients and
+// maxh rows: mag[maxn] u32 | sig, vis, ref, neg [maxh] u64 | contexts 64 B |
+// (decoder) lowest decoded plane [maxn] i8
+struct SmemLayout {
+    int sig_off, ctx_off, pl_off, per_warp;
+};
+__host__ __device__ inline SmemLayout smem_layout(int maxn, int maxh, bool dec) {
+    SmemLayout L;
+    L.sig_off = (maxn * 4 + 15) & ~15;
+    L.ctx_off = L.sig_off + 4 * maxh * 8;
+    L.pl_off = L.ctx_off + 64;
+    L.per_warp = (L.pl_off + (dec ? maxn : 0) + 15) & ~15;
+    return L;
+}
+
+__global__ void __launch_bounds__(WARPS * 32) t1_encode_kernel(int32_t *qt, const BlockDesc *blk, int nblk, T1Out o,
+                                                               int mark_spp_in_q, uint8_t *spp_out, SmemLayout SL,
+                                                               int maxh) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t *base = sm + wid * SL.per_warp;
+    uint32_t *mag = (uint32_t *)base;
+    Blk S;
+    S.sig = (uint64_t *)(base + SL.sig_off);
+    S.vis = S.sig + maxh;
+    S.ref = S.vis + maxh;
+    S.neg = S.ref + maxh;
+    uint8_t *I = base + SL.ctx_off, *M = I + 24;
+    for (int b = blockIdx.x * WARPS + wid; b < nblk; b += gridDim.x * WARPS) {
+        const BlockDesc d = blk[b];
+        const int w = d.w, h = d.h, n = w * h;
+        S.w = w; S.h = h;
+        uint32_t mx = 0;
+        for (int i = lane; i < n; i += 32) {
+            int r = i / w, c = i - r * w;
+            int32_t v = qt[d.off + (int64_t)r * d.stride + c];
+            // sign-magnitude Mallat array (bit 31 sign, bit 30 trace flag) or two's complement
+            uint32_t m = mark_spp_in_q ? (uint32_t)v & 0x3FFFFFFFu : (uint32_t)(v < 0 ? -v : v);
+            mag[i] = m | (v < 0 ? 0x80000000u : 0);
+            mx = max(mx, m);
+        }
+        for (int r = lane; r < h; r += 32) {
+            uint64_t ng = 0;
+            for (int c = 0; c < w; c++) ng |= (uint64_t)(mag[r * w + c] >> 31) << c;
+            S.sig[r] = 0; S.vis[r] = 0; S.ref[r] = 0; S.neg[r] = ng;
+        }
+        for (int s = 16; s; s >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, s));
+        const int K = mx ? 32 - __clz(mx) : 0;
+        __syncwarp();
+        if (lane == 0) {
+            int64_t D0 = 0;
+            for (int i = 0; i < n; i++) {
+                int64_t m = mag[i] & 0x3FFFFFFF;
+                D0 += (2 * m + 1) * (2 * m + 1);
+            }
+            o.D0[b] = D0;
+            o.K[b] = K;
+            int np = K ? 3 * K - 2 : 0;
+            if (np > o.maxpass) { atomicOr(o.status, 2); np = 0; }
+            o.npass[b] = np;
+            if (np) {
+                reset_ctx(I, M);
+                MQEnc e;
+                e.init(o.bytes + (size_t)b * o.cap, o.cap);
+                const int orient = d.orient;
+                int pass = 0;
+                const size_t pb = (size_t)b * o.maxpass;
+                const uint64_t full = w == 64 ? ~0ull : ((1ull << w) - 1);
+                auto end_pass = [&](int64_t dd) {
+                    uint32_t tail;
+                    int tl;
+                    o.pass_len[pb + pass] = e.trunc(tail, tl);
+                    o.tail[pb + pass] = tail;
+                    o.tail_len[pb + pass] = tl;
+                    o.dD[pb + pass] = dd;
+                    pass++;
+                };
+                auto code_sign = [&](int r, int j) {
+                    uint32_t sc = c_signctx[S.signpat(r, j)];
+                    e.encode(I, M, sc & 15, (int)((S.neg[r] >> j) & 1) ^ (int)(sc >> 4));
+                };
+                for (int p = K - 1; p >= 0; p--) {
+                    if (p < K - 1) {
+                        int64_t dd = 0;
+                        for (int s = 0; s < h; s += 4) {  // significance propagation
+                            const int r1 = min(s + 4, h);
+                            for (int j = 0; j < w; j++) {
+                                for (int r = s; r < r1; r++) {
+                                    if ((S.sig[r] >> j) & 1) continue;
+                                    uint32_t nb = S.nbr(r, j);
+                                    if (!nb) continue;
+                                    uint32_t m = mag[r * w + j] & 0x3FFFFFFF;
+                                    int bit = (m >> p) & 1;
+                                    e.encode(I, M, c_sigctx[orient][nb], bit);
+                                    S.vis[r] |= 1ull << j;
+                                    if (bit) {
+                                        code_sign(r, j);
+                                        S.sig[r] |= 1ull << j;
+                                        mag[r * w + j] |= 0x40000000u;
+                                        int64_t t = 2 * (int64_t)m + 1;
+                                        dd += t * t - (t - rec2(m, p)) * (t - rec2(m, p));
+                                    }
+                                }
+                            }
+                        }
+                        end_pass(dd);
+                        dd = 0;
+                        for (int s = 0; s < h; s += 4) {  // magnitude refinement
+                            const int r1 = min(s + 4, h);
+                            uint64_t cm = 0;
+                            for (int r = s; r < r1; r++) cm |= S.sig[r] & ~S.vis[r];
+                            while (cm) {
+                                int j = __ffsll((long long)cm) - 1;
+                                cm &= cm - 1;
+                                for (int r = s; r < r1; r++) {
+                                    if (!(((S.sig[r] & ~S.vis[r]) >> j) & 1)) continue;
+                                    int cx = ((S.ref[r] >> j) & 1) ? 16 : (S.nbr(r, j) ? 15 : 14);
+                                    uint32_t m = mag[r * w + j] & 0x3FFFFFFF;
+                                    e.encode(I, M, cx, (m >> p) & 1);
+                                    S.ref[r] |= 1ull << j;
+                                    int64_t t = 2 * (int64_t)m + 1;
+                                    int64_t a = t - rec2(m, p + 1), c2 = t - rec2(m, p);
+                                    dd += a * a - c2 * c2;
+                                }
+                            }
+                        }
+                        end_pass(dd);
+                    }
+                    int64_t dd = 0;
+                    for (int s = 0; s < h; s += 4) {  // cleanup
+                        const int r1 = min(s + 4, h);
+                        uint64_t cm = 0;
+                        for (int r = s; r < r1; r++) cm |= ~S.sig[r] & ~S.vis[r];
+                        cm &= full;
+                        while (cm) {
+                            int j = __ffsll((long long)cm) - 1;
+                            cm &= cm - 1;
+                            int r = s;
+                            if (r1 - s == 4) {
+                                bool rl = true;
+                                for (int k = 0; k < 4 && rl; k++)
+                                    if ((((S.sig[s + k] | S.vis[s + k]) >> j) & 1) || S.nbr(s + k, j)) rl = false;
+                                if (rl) {
+                                    int rr = -1;
+                                    for (int k = 0; k < 4; k++)
+                                        if (((mag[(s + k) * w + j] & 0x3FFFFFFF) >> p) & 1) { rr = k; break; }
+                                    if (rr < 0) { e.encode(I, M, 17, 0); continue; }
+                                    e.encode(I, M, 17, 1);
+                                    e.encode(I, M, 18, rr >> 1);
+                                    e.encode(I, M, 18, rr & 1);
+                                    int rs = s + rr;
+                                    code_sign(rs, j);
+                                    S.sig[rs] |= 1ull << j;
+                                    uint32_t m = mag[rs * w + j] & 0x3FFFFFFF;
+                                    int64_t t = 2 * (int64_t)m + 1;
+                                    dd += t * t - (t - rec2(m, p)) * (t - rec2(m, p));
+                                    r = rs + 1;
+                                }
+                            }
+                            for (; r < r1; r++) {
+                                if ((((S.sig[r] | S.vis[r]) >> j) & 1)) continue;
+                                uint32_t m = mag[r * w + j] & 0x3FFFFFFF;
+                                int bit = (m >> p) & 1;
+                                e.encode(I, M, c_sigctx[orient][S.nbr(r, j)], bit);
+                                if (bit) {
+                                    code_sign(r, j);
+                                    S.sig[r] |= 1ull << j;
+                                    int64_t t = 2 * (int64_t)m + 1;
+                                    dd += t * t - (t - rec2(m, p)) * (t - rec2(m, p));
+                                }
+                            }
+                        }
+                    }
+                    end_pass(dd);
+                    for (int r = 0; r < h; r++) S.vis[r] = 0;
+                }
+                if (e.overflow) atomicOr(o.status, 1);
+            }
+        }
+        __syncwarp();
+        // trace flags back (bit 30 of the Mallat array, or a byte array)
+        for (int i = lane; i < n; i += 32) {
+            int r = i / w, c = i - r * w;
+            uint32_t f = (mag[i] >> 30) & 1;
+            if (mark_spp_in_q) {
+                int64_t at = d.off + (int64_t)r * d.stride + c;
+                qt[at] = (qt[at] & ~0x40000000) | (int32_t)(f << 30);
+            }
+            if (spp_out) spp_out[(size_t)b * n + i] = (uint8_t)f;
+        }
+        __syncwarp();
+    }
+}
+
+// decode npass passes of each block; writes dequantised values into coef
+// (Mallat) when coef != null, else mag/plane/neg (packed per block)
+__global__ void __launch_bounds__(WARPS * 32) t1_decode_kernel(const uint8_t *bytes, const int64_t *off,
+                                                               const int32_t *len, const BlockDesc *blk,
+                                                               const int32_t *Kb, const int32_t *npb, int nblk,
+                                                               float *coef, int32_t *omag, int8_t *oplane,
+                                                               uint8_t *oneg, SmemLayout SL, int maxh) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t *base = sm + wid * SL.per_warp;
+    uint32_t *mag = (uint32_t *)base;
+    Blk S;
+    S.sig = (uint64_t *)(base + SL.sig_off);
+    S.vis = S.sig + maxh;
+    S.ref = S.vis + maxh;
+    S.neg = S.ref + maxh;
+    uint8_t *I = base + SL.ctx_off, *M = I + 24;
+    int8_t *pl = (int8_t *)(base + SL.pl_off);
+    for (int b = blockIdx.x * WARPS + wid; b < nblk; b += gridDim.x * WARPS) {
+        const BlockDesc d = blk[b];
+        const int w = d.w, h = d.h, n = w * h;
+        S.w = w; S.h = h;
+        for (int i = lane; i < n; i += 32) { mag[i] = 0; pl[i] = -1; }
+        for (int r = lane; r < h; r += 32) { S.sig[r] = 0; S.vis[r] = 0; S.ref[r] = 0; S.neg[r] = 0; }
+        __syncwarp();
+        const int K = Kb[b], np = npb[b];
+        if (lane == 0 && np > 0 && np <= 3 * K - 2) {
+            reset_ctx(I, M);
+            MQDec dc;
+            dc.init(bytes + off[b], len[b]);
+            const int orient = d.orient;
+            const uint64_t full = w == 64 ? ~0ull : ((1ull << w) - 1);
+            int pass = 0;
+            auto dec_sign = [&](int r, int j, int p) {
+                uint32_t sc = c_signctx[S.signpat(r, j)];
+                int ng = dc.decode(I, M, sc & 15) ^ (int)(sc >> 4);
+                S.neg[r] |= (uint64_t)ng << j;
+                S.sig[r] |= 1ull << j;
+                mag[r * w + j] = 1u << p;
+                pl[r * w + j] = (int8_t)p;
+            };
+            for (int p = K - 1; p >= 0 && pass < np; p--) {
+                if (p < K - 1) {
+                    for (int s = 0; s < h; s += 4) {
+                        const int r1 = min(s + 4, h);
+                        for (int j = 0; j < w; j++)
+                            for (int r = s; r < r1; r++) {
+                                if ((S.sig[r] >> j) & 1) continue;
+                                uint32_t nb = S.nbr(r, j);
+                                if (!nb) continue;
+                                S.vis[r] |= 1ull << j;
+                                if (dc.decode(I, M, c_sigctx[orient][nb])) dec_sign(r, j, p);
+                            }
+                    }
+                    if (++pass >= np) break;
+                    for (int s = 0; s < h; s += 4) {
+                        const int r1 = min(s + 4, h);
+                        uint64_t cm = 0;
+                        for (int r = s; r < r1; r++) cm |= S.sig[r] & ~S.vis[r];
+                        while (cm) {
+                            int j = __ffsll((long long)cm) - 1;
+                            cm &= cm - 1;
+                            for (int r = s; r < r1; r++) {
+                                if (!(((S.sig[r] & ~S.vis[r]) >> j) & 1)) continue;
+                                int cx = ((S.ref[r] >> j) & 1) ? 16 : (S.nbr(r, j) ? 15 : 14);
+                                uint32_t bit = dc.decode(I, M, cx);
+                                mag[r * w + j] |= bit << p;
+                                pl[r * w + j] = (int8_t)p;
+                                S.ref[r] |= 1ull << j;
+                            }
+                        }
+                    }
+                    if (++pass >= np) break;
+                }
+                for (int s = 0; s < h; s += 4) {
+                    const int r1 = min(s + 4, h);
+                    uint64_t cm = 0;
+                    for (int r = s; r < r1; r++) cm |= ~S.sig[r] & ~S.vis[r];
+                    cm &= full;
+                    while (cm) {
+                        int j = __ffsll((long long)cm) - 1;
+                        cm &= cm - 1;
+                        int r = s;
+                        if (r1 - s == 4) {
+                            bool rl = true;
+                            for (int k = 0; k < 4 && rl; k++)
+                                if ((((S.sig[s + k] | S.vis[s + k]) >> j) & 1) || S.nbr(s + k, j)) rl = false;
+                            if (rl) {
+                                if (!dc.decode(I, M, 17)) continue;
+                                int rr = dc.decode(I, M, 18) << 1;
+                                rr |= dc.decode(I, M, 18);
+                                dec_sign(s + rr, j, p);
+                                r = s + rr + 1;
+                            }
+                        }
+                        for (; r < r1; r++) {
+                            if ((((S.sig[r] | S.vis[r]) >> j) & 1)) continue;
+                            if (dc.decode(I, M, c_sigctx[orient][S.nbr(r, j)])) dec_sign(r, j, p);
+                        }
+                    }
+                }
+                pass++;
+                for (int r = 0; r < h; r++) S.vis[r] = 0;
+            }
+        }
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+            int r = i / w, c = i - r * w;
+            int p = pl[i];
+            int ng = (int)((S.neg[r] >> c) & 1);
+            uint32_t m = mag[i];
+            if (coef) {
+                float val = p >= 0 ? deq(m, p, d.delta) : 0.0f;
+                coef[d.off + (int64_t)r * d.stride + c] = ng ? -val : val;
+            } else {
+                omag[(size_t)b * n + i] = p >= 0 ? (int32_t)m : 0;
+                oplane[(size_t)b * n + i] = (int8_t)p;
+                oneg[(size_t)b * n + i] = p >= 0 ? (uint8_t)ng : 0;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+bool g_tables_ready[64];
+std::mutex g_tables_mu;
+
+int upload_tables() {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_tables_mu);
+    if (dev < 64 && g_tables_ready[dev]) return EBCC_OK;
+    static const uint16_t QE[47] = {
+        0x5601, 0x3401, 0x1801, 0x0AC1, 0x0521, 0x0221, 0x5601, 0x5401, 0x4801, 0x3801, 0x3001, 0x2401,
+        0x1C01, 0x1601, 0x5601, 0x5401, 0x5101, 0x4801, 0x3801, 0x3401, 0x3001, 0x2801, 0x2401, 0x2201,
+        0x1C01, 0x1801, 0x1601, 0x1401, 0x1201, 0x1101, 0x0AC1, 0x09C1, 0x08A1, 0x0521, 0x0441, 0x02A1,
+        0x0221, 0x0141, 0x0111, 0x0085, 0x0049, 0x0025, 0x0015, 0x0009, 0x0005, 0x0001, 0x5601};
+    static const uint8_t NM[47] = {1,  2,  3,  4,  5,  38, 7,  8,  9,  10, 11, 12, 13, 29, 15, 16,
+                                   17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32,
+                                   33, 34, 35, 36, 37, 38, 39, 40, 41, 42, 43, 44, 45, 45, 46};
+    static const uint8_t NL[47] = {1,  6,  9,  12, 29, 33, 6,  14, 14, 14, 17, 18, 20, 21, 14, 14,
+                                   15, 16, 17, 18, 19, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29,
+                                   30, 31, 32, 33, 34, 35, 36, 37, 38, 39, 40, 41, 42, 43, 46};
+    uint32_t mq[47];
+    uint8_t sw[47];
+    for (int i = 0; i < 47; i++) {
+        mq[i] = QE[i] | ((uint32_t)NM[i] << 16) | ((uint32_t)NL[i] << 24);
+        sw[i] = (i == 0 || i == 6 || i == 14);
+    }
+    uint8_t sig[4][256], sgn[256];
+    for (int o = 0; o < 4; o++)
+        for (int pat = 0; pat < 256; pat++) {
+            // pattern bits: 0 UL 1 U 2 UR 3 L 4 R 5 DL 6 D 7 DR
+            int H = ((pat >> 3) & 1) + ((pat >> 4) & 1);
+            int V = ((pat >> 1) & 1) + ((pat >> 6) & 1);
+            int D = (pat & 1) + ((pat >> 2) & 1) + ((pat >> 5) & 1) + ((pat >> 7) & 1);
+            int c;
+            if (o == 1) { int t = H; H = V; V = t; }
+            if (o != 3) {
+                if (H == 2) c = 8;
+                else if (H == 1) c = V >= 1 ? 7 : (D >= 1 ? 6 : 5);
+                else if (V == 2) c = 4;
+                else if (V == 1) c = 3;
+                else c = D >= 2 ? 2 : (D == 1 ? 1 : 0);
+            } else {
+                int HV = H + V;
+                if (D >= 3) c = 8;
+                else if (D == 2) c = HV >= 1 ? 7 : 6;
+                else if (D == 1) c = HV >= 2 ? 5 : (HV == 1 ? 4 : 3);
+                else c = HV >= 2 ? 2 : (HV == 1 ? 1 : 0);
+            }
+            sig[o][pat] = (uint8_t)c;
+        }
+    for (int pat = 0; pat < 256; pat++) {
+        auto contrib = [&](int s, int n) { return s ? (n ? -1 : 1) : 0; };
+        int H = contrib(pat & 1, (pat >> 1) & 1) + contrib((pat >> 2) & 1, (pat >> 3) & 1);
+        int V = contrib((pat >> 4) & 1, (pat >> 5) & 1) + contrib((pat >> 6) & 1, (pat >> 7) & 1);
+        H = H > 1 ? 1 : (H < -1 ? -1 : H);
+        V = V > 1 ? 1 : (V < -1 ? -1 : V);
+        int cx, x;
+        if (H == 0 && V == 0) { cx = 9; x = 0; }
+        else if (H == 0) { cx = 10; x = V < 0; }
+        else {
+            x = H < 0;
+            int v = H < 0 ? -V : V;
+            cx = v == 1 ? 13 : (v == 0 ? 12 : 11);
+        }
+        sgn[pat] = (uint8_t)(cx | (x << 4));
+    }
+    CK(cudaMemcpyToSymbol(c_mq, mq, sizeof(mq)));
+    CK(cudaMemcpyToSymbol(c_mqsw, sw, sizeof(sw)));
+    CK(cudaMemcpyToSymbol(c_sigctx, sig, sizeof(sig)));
+    CK(cudaMemcpyToSymbol(c_signctx, sgn, sizeof(sgn)));
+    {
+        SmemLayout big = smem_layout(64 * 64, 64, true);
+        CK(cudaFuncSetAttribute(t1_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WARPS * big.per_warp));
+        CK(cudaFuncSetAttribute(t1_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WARPS * big.per_warp));
+    }
+    if (dev < 64) g_tables_ready[dev] = true;
+    return EBCC_OK;
+}
+
+int grid_for(int nblk) {
+    int g = (nblk + WARPS - 1) / WARPS;
+    return g < 1 ? 1 : (g > 152 * 16 ? 152 * 16 : g);
+}
+
+}  // namespace
+
+int t1_encode_blocks(int32_t *qt, const BlockDesc *blk, int nblk, int maxw, int maxh, const T1Out &o,
+                     int mark_spp_in_q, uint8_t *spp_out, cudaStream_t st) {
+    int rc = upload_tables();
+    if (rc) return rc;
+    if (nblk <= 0) return EBCC_OK;
+    if (maxw > 64 || maxh > 64) return EBCC_EINVAL;
+    SmemLayout SL = smem_layout(maxw * maxh, maxh, false);
+    t1_encode_kernel<<<grid_for(nblk), WARPS * 32, WARPS * SL.per_warp, st>>>(qt, blk, nblk, o, mark_spp_in_q,
+                                                                             spp_out, SL, maxh);
+    CK(cudaGetLastError());
+    return EBCC_OK;
+}
+
+int t1_decode_blocks(const uint8_t *bytes, const int64_t *off, const int32_t *len, const BlockDesc *blk,
+                     const int32_t *K, const int32_t *npass, int nblk, int maxw, int maxh, float *coef, int32_t *mag,
+                     int8_t *plane, uint8_t *neg, cudaStream_t st) {
+    int rc = upload_tables();
+    if (rc) return rc;
+    if (nblk <= 0) return EBCC_OK;
+    if (maxw > 64 || maxh > 64) return EBCC_EINVAL;
+    SmemLayout SL = smem_layout(maxw * maxh, maxh, true);
+    t1_decode_kernel<<<grid_for(nblk), WARPS * 32, WARPS * SL.per_warp, st>>>(bytes, off, len, blk, K, npass, nblk,
+                                                                             coef, mag, plane, neg, SL, maxh);
+    CK(cudaGetLastError());
+    return EBCC_OK;
+}

@@ -1,0 +1,138 @@
+"""End-to-end GPU parity: Algorithm 1 on the GPU against the oracle.
+
+* every GPU stream decodes on the oracle within the bound at every point, and
+  on the GPU within the bound at every point;
+* GPU and oracle decoders agree to FP32 rounding on the same stream;
+* compression ratio within 1% of the oracle's on the same field;
+* error codes, degenerate fields, batched == plain.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2510_22265_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    import os
+    import __graft_entry__ as g
+    from paper_2510_22265_gb300 import binding
+    if not os.path.exists(binding.LIBPATH):
+        g.build()
+    return binding
+
+
+def _within(x, y, eps):
+    return float(np.abs(y.astype(np.float64) - x.astype(np.float64)).max()) <= eps
+
+
+@pytest.mark.parametrize("bound", [1e-3, 1e-2, 1e-1])
+def test_config1_against_oracle(B, bound):
+    x = synth.smooth_field(181, 360, seed=0)
+    eps = bound * (float(x.max()) - float(x.min()))
+    s, st = B.ebcc_compress(x, bound, B.EBCC_BOUND_REL)
+    assert st["total_bytes"] == len(s)
+    y_orc = O.decompress(s, *x.shape)
+    y_gpu = B.ebcc_decompress(s, *x.shape)
+    assert _within(x, y_orc, eps), "oracle decode of the GPU stream breaks the bound"
+    assert _within(x, y_gpu, eps), "GPU decode breaks the bound"
+    assert np.abs(y_orc.astype(np.float64) - y_gpu).max() <= 2e-5 * eps / bound
+    so, sto = O.compress(x, bound, 1)
+    cr_g, cr_o = 4 * x.size / len(s), 4 * x.size / len(so)
+    assert abs(cr_g / cr_o - 1) <= 0.01, (cr_g, cr_o, st, sto)
+
+
+@pytest.mark.parametrize("shape", [(33, 65), (16, 16), (2, 7), (97, 13), (64, 33)])
+def test_odd_shapes(B, shape):
+    rng = np.random.default_rng(shape[0] * 100 + shape[1])
+    x = (rng.normal(size=shape).cumsum(axis=-1) + 10).astype(np.float32)
+    for b in (1e-3, 3e-2):
+        eps = b * (float(x.max()) - float(x.min()))
+        s, _ = B.ebcc_compress(x, b, B.EBCC_BOUND_REL)
+        assert _within(x, O.decompress(s, *shape), eps)
+        assert _within(x, B.ebcc_decompress(s, *shape), eps)
+
+
+def test_spiky_field_uses_residual_layer(B):
+    x = synth.smooth_field(181, 360, seed=4, spikes=0.002)
+    eps = 1e-2 * (float(x.max()) - float(x.min()))
+    s, st = B.ebcc_compress(x, 1e-2, B.EBCC_BOUND_REL)
+    assert _within(x, O.decompress(s, *x.shape), eps)
+    assert _within(x, B.ebcc_decompress(s, *x.shape), eps)
+    assert st["iters_trunc"] > 0
+
+
+def test_absolute_bound_and_escapes(B):
+    x = synth.smooth_field(64, 64, seed=6, spikes=0.01)
+    p = B.params(guard_bits=-12, q=0.99)
+    s, st = B.ebcc_compress(x, 1e-3, B.EBCC_BOUND_REL, p)
+    eps = 1e-3 * (float(x.max()) - float(x.min()))
+    assert _within(x, O.decompress(s, *x.shape), eps)
+    assert _within(x, B.ebcc_decompress(s, *x.shape), eps)
+    e = 0.05 * (float(x.max()) - float(x.min()))
+    s, st = B.ebcc_compress(x, e, B.EBCC_BOUND_ABS)
+    assert _within(x, B.ebcc_decompress(s, *x.shape), e)
+
+
+def test_constant_nonfinite_and_errors(B):
+    x = np.full((40, 30), 7.5, np.float32)
+    s, _ = B.ebcc_compress(x, 1e-2)
+    assert len(s) == 64 and (B.ebcc_decompress(s, 40, 30) == 7.5).all()
+    y = synth.smooth_field(20, 20, seed=1)
+    y[3, 4] = np.inf
+    with pytest.raises(B.EbccError) as e:
+        B.ebcc_compress(y, 1e-2)
+    assert e.value.code == -2
+    with pytest.raises(B.EbccError) as e:
+        B.ebcc_compress(synth.smooth_field(20, 20, seed=1), -1.0)
+    assert e.value.code == -1
+    s, _ = B.ebcc_compress(synth.smooth_field(20, 20, seed=1), 1e-2)
+    with pytest.raises(B.EbccError) as e:
+        B.ebcc_decompress(s[:-1], 20, 20)
+    assert e.value.code == -3
+    with pytest.raises(B.EbccError):
+        B.ebcc_decompress(s, 21, 20)
+
+
+def test_determinism_and_params(B):
+    x = synth.smooth_field(91, 180, seed=2)
+    a, _ = B.ebcc_compress(x, 1e-2)
+    b, _ = B.ebcc_compress(x, 1e-2)
+    assert a == b
+    eps = 1e-2 * (float(x.max()) - float(x.min()))
+    for cb in [(64, 64), (32, 64), (16, 16)]:
+        s, _ = B.ebcc_compress(x, 1e-2, B.EBCC_BOUND_REL, B.params(cblk=cb))
+        assert _within(x, O.decompress(s, *x.shape), eps)
+
+
+def test_batch_equals_plain(B):
+    fields = [synth.smooth_field(91, 180, seed=s) for s in range(3)] + [synth.smooth_field(64, 48, seed=9)]
+    bounds = [1e-2, 1e-3, 5e-2, 1e-2]
+    plain = [B.ebcc_compress(f, b)[0] for f, b in zip(fields, bounds)]
+    rc, res = B.ebcc_compress_batch_dev([torch.from_numpy(f).cuda() for f in fields], bounds)
+    assert rc == 0
+    for (buf, ln, st, _), ref in zip(res, plain):
+        assert st == 0
+        assert bytes(buf[:ln].cpu().numpy()) == ref
+    outs = [torch.empty(f.shape, dtype=torch.float32, device="cuda") for f in fields]
+    assert B.ebcc_decompress_batch_dev([r[0] for r in res], [r[1] for r in res], [f.shape for f in fields],
+                                       outs) == 0
+    for f, o, b in zip(fields, outs, bounds):
+        assert _within(f, o.cpu().numpy(), b * (float(f.max()) - float(f.min())))
+
+
+@pytest.mark.slow
+def test_era5_shaped_full_size(B):
+    # 721 x 1440 fields at the three bounds: GPU streams decode on the oracle
+    for var in (0, 2):
+        x = synth.era5_like(var, 5)
+        for b in (1e-3, 1e-2, 1e-1):
+            eps = b * (float(x.max()) - float(x.min()))
+            s, st = B.ebcc_compress(x, b)
+            assert _within(x, O.decompress(s, *x.shape), eps)
+            assert _within(x, B.ebcc_decompress(s, *x.shape), eps)
