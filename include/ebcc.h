@@ -264,6 +264,16 @@ int ebcc_spiht_prefix_recon_dev(const int32_t *s, const uint32_t *sig_pos, const
 int ebcc_count_within_dev(const float *x, const float *an_hat, size_t n, double mn, double range,
                           double eps_abs, double guard, int64_t *count_out, void *stream);
 
+/* ------------------------------------------------------------- profiling
+ * Kernel timing for measurement: while enabled, every kernel launch of the
+ * library is bracketed by CUDA events recorded on its own stream.  Entries are
+ * named after the kernel; total_ms is the summed device duration, bytes the
+ * summed algorithmic bytes (minimum the kernel must move) of its launches. */
+void ebcc_profile_enable(int on);
+void ebcc_profile_reset(void);
+int ebcc_profile_count(void);
+int ebcc_profile_get(int i, const char **name, double *total_ms, long long *launches, double *bytes);
+
 #ifdef __cplusplus
 }
 #endif

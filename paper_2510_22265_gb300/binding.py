@@ -30,7 +30,8 @@ EXPORTS = [
     "ebcc_server_destroy", "ebcc_dwt_fwd_dev", "ebcc_dwt_inv_dev", "ebcc_effective_levels",
     "ebcc_quantise_dev", "ebcc_band_step", "ebcc_t1_encode_dev", "ebcc_t1_decode_dev", "ebcc_pcrd_dev",
     "ebcc_spiht_encode_dev", "ebcc_spiht_decode_dev", "ebcc_spiht_prefix_recon_dev",
-    "ebcc_count_within_dev",
+    "ebcc_count_within_dev", "ebcc_profile_enable", "ebcc_profile_reset", "ebcc_profile_count",
+    "ebcc_profile_get",
 ]
 
 
@@ -127,8 +128,23 @@ def lib():
         L.ebcc_server_poll.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.POINTER(ebcc_result)]
         L.ebcc_server_cancel.argtypes = [C.c_void_p, C.c_uint64]
         L.ebcc_server_destroy.argtypes = [C.c_void_p]
+        L.ebcc_profile_enable.argtypes = [C.c_int]
+        L.ebcc_profile_get.argtypes = [C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
+                                       C.POINTER(C.c_longlong), C.POINTER(C.c_double)]
         _lib = L
     return _lib
+
+
+def profile_read() -> list:
+    """Per-kernel device time, launch count and algorithmic bytes since the last reset."""
+    L = lib()
+    out = []
+    for i in range(L.ebcc_profile_count()):
+        nm, ms, n, by = C.c_char_p(), C.c_double(), C.c_longlong(), C.c_double()
+        L.ebcc_profile_get(i, C.byref(nm), C.byref(ms), C.byref(n), C.byref(by))
+        if n.value:
+            out.append({"name": nm.value.decode(), "ms": ms.value, "launches": n.value, "bytes": by.value})
+    return sorted(out, key=lambda e: -e["ms"])
 
 
 def _check(rc: int, what: str):

@@ -71,13 +71,13 @@ __device__ __forceinline__ void scale(float (*t)[EX + 1], float even_f, float od
 template <bool NORM>
 __global__ void __launch_bounds__(NT) fwd_level(const float *__restrict__ src, int ss, int hp, int wp,
                                                 float *__restrict__ coef, int nx, float *__restrict__ ll,
-                                                int ls, int ll_in_coef, double mn, double inv) {
+                                                int ls, int ll_in_coef, double mn, double inv, long long ncoef) {
     __shared__ float t[EY][EX + 1];
     const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
     for (int k = threadIdx.x; k < EY * EX; k += NT) {
         int ly = k / EX, lx = k % EX;
         int gy = reflect(ty0 - HALO + ly, hp), gx = reflect(tx0 - HALO + lx, wp);
-        float v = src[(size_t)gy * ss + gx];
+        float v = INB((long long)gy * ss + gx, (long long)hp * ss) ? src[(size_t)gy * ss + gx] : 0.0f;
         if (NORM) v = (float)(((double)v - mn) * inv);
         t[ly][lx] = v;
     }
@@ -102,16 +102,18 @@ __global__ void __launch_bounds__(NT) fwd_level(const float *__restrict__ src, i
         float v = t[HALO + 2 * r + pv][HALO + 2 * c + ph];
         int oy = (gy >> 1) + (pv ? hl : 0), ox = (gx >> 1) + (ph ? wl : 0);
         if (!pv && !ph) {
-            if (ll) ll[(size_t)oy * ls + ox] = v;
-            if (ll_in_coef) coef[(size_t)oy * nx + ox] = v;
+            if (ll && INB((long long)oy * ls + ox, (long long)((hp + 1) >> 1) * ls)) ll[(size_t)oy * ls + ox] = v;
+            if (ll_in_coef && INB((long long)oy * nx + ox, ncoef)) coef[(size_t)oy * nx + ox] = v;
         } else {
-            coef[(size_t)oy * nx + ox] = v;
+            if (INB((long long)oy * nx + ox, ncoef)) coef[(size_t)oy * nx + ox] = v;
         }
     }
 }
 
 __device__ __forceinline__ void finish_point(const InvFinal &f, float v, size_t gi, float *out,
-                                             size_t oi, unsigned long long &cnt, double mn, double range) {
+                                             size_t oi, unsigned long long &cnt, double mn, double range,
+                                             long long nall) {
+    if (!INB((long long)gi, nall) || !INB((long long)oi, nall)) return;
     if (f.mode == 0) {
         if (f.base) v = v + f.base[gi];
         out[oi] = v;
@@ -145,7 +147,7 @@ __device__ __forceinline__ void block_count_add(unsigned long long v, unsigned l
 __global__ void __launch_bounds__(NT) inv_level(const float *__restrict__ ll, int ls,
                                                 const float *__restrict__ coef, int nx, int hp, int wp,
                                                 float *__restrict__ dst, int ds, InvFinal fin, double mn,
-                                                double range) {
+                                                double range, long long ncoef) {
     __shared__ float t[EY][EX + 1];
     const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
     const int hl = (hp + 1) >> 1, wl = (wp + 1) >> 1;
@@ -155,8 +157,11 @@ __global__ void __launch_bounds__(NT) inv_level(const float *__restrict__ ll, in
         int pv = gy & 1, ph = gx & 1;
         int sy = gy >> 1, sx = gx >> 1;
         float v;
-        if (!pv && !ph) v = ll[(size_t)sy * ls + sx];
-        else v = coef[(size_t)(sy + (pv ? hl : 0)) * nx + sx + (ph ? wl : 0)];
+        if (!pv && !ph) v = INB((long long)sy * ls + sx, (long long)hl * ls) ? ll[(size_t)sy * ls + sx] : 0.0f;
+        else {
+            long long ci = (long long)(sy + (pv ? hl : 0)) * nx + sx + (ph ? wl : 0);
+            v = INB(ci, ncoef) ? coef[ci] : 0.0f;
+        }
         t[ly][lx] = v;
     }
     __syncthreads();
@@ -176,8 +181,8 @@ __global__ void __launch_bounds__(NT) inv_level(const float *__restrict__ ll, in
         int gy = ty0 + r, gx = tx0 + c;
         if (gy >= hp || gx >= wp) continue;
         float v = t[HALO + r][HALO + c];
-        if (fin.mode < 0) dst[(size_t)gy * ds + gx] = v;
-        else finish_point(fin, v, (size_t)gy * nx + gx, dst, (size_t)gy * ds + gx, cnt, mn, range);
+        if (fin.mode < 0) { if (INB((long long)gy * ds + gx, (long long)hp * ds)) dst[(size_t)gy * ds + gx] = v; }
+        else finish_point(fin, v, (size_t)gy * nx + gx, dst, (size_t)gy * ds + gx, cnt, mn, range, ncoef);
     }
     if (fin.mode == 1 || fin.mode == 2) block_count_add(cnt, fin.count);
 }
@@ -195,7 +200,7 @@ __global__ void __launch_bounds__(NT) finish_identity(const float *__restrict__ 
                                                       InvFinal fin, double mn, double range) {
     unsigned long long cnt = 0;
     for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT)
-        finish_point(fin, in[i], i, out, i, cnt, mn, range);
+        finish_point(fin, in[i], i, out, i, cnt, mn, range, (long long)n);
     if (fin.mode == 1 || fin.mode == 2) block_count_add(cnt, fin.count);
 }
 
@@ -220,9 +225,10 @@ int dwt_forward(const float *in, float *coef, float *s1, float *s2, int ny, int 
         float *ll = last ? nullptr : ((l & 1) ? s1 : s2);
         dim3 grid((wp + TX - 1) / TX, (hp + TY - 1) / TY);
         if (l == 1 && norm)
-            fwd_level<true><<<grid, NT, 0, st>>>(src, ss, hp, wp, coef, nx, ll, wl, last, mn, inv);
+            PROF("fwd_level", st, 8.0 * hp * wp, fwd_level<true><<<grid, NT, 0, st>>>(src, ss, hp, wp, coef, nx, ll, wl, last, mn, inv, (long long)ny * nx););
         else
-            fwd_level<false><<<grid, NT, 0, st>>>(src, ss, hp, wp, coef, nx, ll, wl, last, 0.0, 0.0);
+            PROF("fwd_level", st, 8.0 * hp * wp, fwd_level<false><<<grid, NT, 0, st>>>(src, ss, hp, wp, coef, nx, ll, wl, last, 0.0, 0.0,
+                                                  (long long)ny * nx););
         CK(cudaGetLastError());
         src = ll;
         ss = wl;
@@ -251,7 +257,7 @@ int dwt_inverse_ex(const float *coef, float *out, float *s1, float *s2, int ny, 
         InvFinal f = fin;
         if (l > 1) f.mode = -1;
         dim3 grid((wp + TX - 1) / TX, (hp + TY - 1) / TY);
-        inv_level<<<grid, NT, 0, st>>>(ll, ls, coef, nx, hp, wp, dst, ds, f, mn, range);
+        PROF("inv_level", st, (4.0 + (f.mode == 1 ? 8.0 : f.mode == 2 ? 12.0 : (f.base ? 8.0 : 4.0))) * hp * wp, inv_level<<<grid, NT, 0, st>>>(ll, ls, coef, nx, hp, wp, dst, ds, f, mn, range, (long long)ny * nx););
         CK(cudaGetLastError());
         ll = dst;
         ls = wp;

@@ -99,10 +99,10 @@ struct T1Out {
     int32_t *status;     // bit 0 byte overflow, bit 1 too many passes
 };
 int t1_encode_blocks(int32_t *qt, const BlockDesc *blk, int nblk, int maxw, int maxh, const T1Out &o,
-                     int sign_magnitude_q, uint8_t *spp_out, cudaStream_t st);
+                     int sign_magnitude_q, uint8_t *spp_out, long long nq, cudaStream_t st);
 int t1_decode_blocks(const uint8_t *bytes, const int64_t *off, const int32_t *len, const BlockDesc *blk,
                      const int32_t *K, const int32_t *npass, int nblk, int maxw, int maxh, float *coef,
-                     int32_t *mag, int8_t *plane, uint8_t *neg, cudaStream_t st);
+                     int32_t *mag, int8_t *plane, uint8_t *neg, long long nq, cudaStream_t st);
 
 // ------------------------------------------------------------ PCRD
 struct Hulls {
@@ -151,6 +151,49 @@ int spiht_encode(const int32_t *s, int ny, int nx, int L, uint8_t *out, size_t c
                  const SpihtWork &w, cudaStream_t st);
 int spiht_decode(const uint8_t *in, int64_t nbits, int ny, int nx, int L, int nmax, int32_t *mag, int8_t *plane,
                  uint8_t *neg, float *coef_out, int step_exp, const SpihtWork &w, cudaStream_t st);
+
+// ------------------------------------------------------------ diagnostics
+// Every guarded access checks its index; an index out of range is reported
+// (source line, index, size) and the access skipped instead of faulting.
+// -DEBCC_UNCHECKED removes the guards.  EBCC_DEBUG_SYNC=1 in the environment
+// makes the host synchronise after every pipeline stage and name the stage
+// that failed.
+int ebcc_debug_sync_enabled();
+
+// kernel profiler (events on the launching stream; see ebcc_profile_*)
+int prof_id(const char *name);
+void *prof_begin(int id, cudaStream_t st);
+void prof_end(void *tok, cudaStream_t st, double bytes);
+#define PROF(name, st, bytes, ...)                    \
+    do {                                             \
+        static int pid_ = prof_id(name);             \
+        void *tok_ = prof_begin(pid_, (st));         \
+        __VA_ARGS__;                                 \
+        prof_end(tok_, (st), (double)(bytes));       \
+    } while (0)
+int ebcc_stage_check(cudaStream_t st, const char *what, int line);
+#define STAGE(st, what)                                                 \
+    do {                                                                \
+        if (ebcc_debug_sync_enabled()) {                                \
+            int r_ = ebcc_stage_check((st), (what), __LINE__);          \
+            if (r_ != EBCC_OK) return r_;                               \
+        }                                                               \
+    } while (0)
+
+#ifdef __CUDACC__
+#ifndef EBCC_UNCHECKED
+#include <cstdio>
+__device__ __forceinline__ bool ebcc_inb(long long i, long long n, int line) {
+    if (i >= 0 && i < n) return true;
+    printf("EBCC_OOB line %d: index %lld size %lld block %d thread %d\n", line, i, n, (int)blockIdx.x,
+           (int)threadIdx.x);
+    return false;
+}
+#define INB(i, n) ebcc_inb((long long)(i), (long long)(n), __LINE__)
+#else
+#define INB(i, n) true
+#endif
+#endif
 
 // ------------------------------------------------------------ device helpers
 #ifdef __CUDACC__

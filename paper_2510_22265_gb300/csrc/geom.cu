@@ -142,6 +142,25 @@ void make_blocks(const FieldGeom &g, std::vector<BlockDesc> &out) {
     }
 }
 
+int ebcc_debug_sync_enabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("EBCC_DEBUG_SYNC");
+        v = (e && e[0] == '1') ? 1 : 0;
+    }
+    return v;
+}
+
+int ebcc_stage_check(cudaStream_t st, const char *what, int line) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        fprintf(stderr, "ebcc: stage '%s' (line %d) failed: %s\n", what, line, cudaGetErrorString(e));
+        return EBCC_ECUDA;
+    }
+    return EBCC_OK;
+}
+
 int ebcc_cuda_fail(cudaError_t e, const char *file, int line) {
     if (getenv("EBCC_DEBUG")) fprintf(stderr, "ebcc: CUDA error %s at %s:%d\n", cudaGetErrorString(e), file, line);
     if (e == cudaErrorMemoryAllocation) {
@@ -188,6 +207,103 @@ int ebcc_effective_levels(size_t ny, size_t nx, int levels) {
 double ebcc_band_step(int P, int level, int orient) {
     if (level < 0 || level > EBCC_MAX_LEVELS || orient < 0 || orient > 3) return 0.0;
     return band_step(P, level, orient);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ kernel profiler
+// When enabled, launch sites bracket their kernels with CUDA events recorded
+// on the launching stream; durations are resolved when the table is read.
+namespace {
+struct ProfPending {
+    int id;
+    cudaEvent_t a, b;
+    double bytes;
+};
+struct ProfEntry {
+    const char *name;
+    double ms = 0, bytes = 0;
+    long long launches = 0;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfPending> g_prof_pending;
+std::vector<ProfEntry> g_prof;
+
+void prof_resolve_locked() {
+    for (auto &p : g_prof_pending) {
+        float ms = 0;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            g_prof[p.id].ms += ms;
+            g_prof[p.id].bytes += p.bytes;
+            g_prof[p.id].launches++;
+        }
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    g_prof_pending.clear();
+}
+}  // namespace
+
+int prof_id(const char *name) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (size_t i = 0; i < g_prof.size(); i++)
+        if (strcmp(g_prof[i].name, name) == 0) return (int)i;
+    ProfEntry e;
+    e.name = name;
+    g_prof.push_back(e);
+    return (int)g_prof.size() - 1;
+}
+
+void *prof_begin(int id, cudaStream_t st) {
+    if (!g_prof_on) return nullptr;
+    ProfPending *p = new ProfPending{id, nullptr, nullptr, 0};
+    cudaEventCreate(&p->a);
+    cudaEventCreate(&p->b);
+    cudaEventRecord(p->a, st);
+    return p;
+}
+
+void prof_end(void *tok, cudaStream_t st, double bytes) {
+    if (!tok) return;
+    ProfPending *p = (ProfPending *)tok;
+    cudaEventRecord(p->b, st);
+    p->bytes = bytes;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_pending.push_back(*p);
+    delete p;
+    if (g_prof_pending.size() > 20000) prof_resolve_locked();
+}
+
+extern "C" {
+
+void ebcc_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!on) prof_resolve_locked();
+    g_prof_on = on != 0;
+}
+
+void ebcc_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_resolve_locked();
+    for (auto &e : g_prof) { e.ms = 0; e.bytes = 0; e.launches = 0; }
+}
+
+int ebcc_profile_count(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_resolve_locked();
+    return (int)g_prof.size();
+}
+
+int ebcc_profile_get(int i, const char **name, double *total_ms, long long *launches, double *bytes) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_resolve_locked();
+    if (i < 0 || i >= (int)g_prof.size()) return EBCC_EINVAL;
+    if (name) *name = g_prof[i].name;
+    if (total_ms) *total_ms = g_prof[i].ms;
+    if (launches) *launches = g_prof[i].launches;
+    if (bytes) *bytes = g_prof[i].bytes;
+    return EBCC_OK;
 }
 
 }  // extern "C"

@@ -108,6 +108,7 @@ __global__ void npass_kernel(Hulls h, int nblk, const Sel *sel, int32_t *npass_o
         const size_t base = (size_t)b * h.maxpt;
         int n = 0;
         for (int k = 1; k < nh; k++) {
+            if (!INB(k, h.maxpt)) break;
             if (s.all || h.key[base + k] > s.thr) n = h.pt[base + k];
             else break;
         }
@@ -125,20 +126,20 @@ unsigned grid1(int n, int t) {
 int pcrd_hulls(const int32_t *npass, const int32_t *pass_len, const int64_t *dD, const int64_t *D0, int nblk,
                int maxpass, const Hulls &h, cudaStream_t st) {
     if (nblk <= 0) return EBCC_OK;
-    hull_kernel<<<grid1(nblk, 128), 128, 0, st>>>(npass, pass_len, dD, D0, nblk, maxpass, h);
+    PROF("hull_kernel", st, 0.0, hull_kernel<<<grid1(nblk, 128), 128, 0, st>>>(npass, pass_len, dD, D0, nblk, maxpass, h););
     CK(cudaGetLastError());
     return EBCC_OK;
 }
 
 int pcrd_select(const Hulls &h, int nblk, const double *budget_dev, Sel *sel_dev, cudaStream_t st) {
-    select_kernel<<<1, SEL_T, 0, st>>>(h, nblk, budget_dev, sel_dev);
+    PROF("select_kernel", st, 0.0, select_kernel<<<1, SEL_T, 0, st>>>(h, nblk, budget_dev, sel_dev););
     CK(cudaGetLastError());
     return EBCC_OK;
 }
 
 int pcrd_npass(const Hulls &h, int nblk, const Sel *sel_dev, int32_t *npass_out, cudaStream_t st) {
     if (nblk <= 0) return EBCC_OK;
-    npass_kernel<<<grid1(nblk, 128), 128, 0, st>>>(h, nblk, sel_dev, npass_out);
+    PROF("npass_kernel", st, 0.0, npass_kernel<<<grid1(nblk, 128), 128, 0, st>>>(h, nblk, sel_dev, npass_out););
     CK(cudaGetLastError());
     return EBCC_OK;
 }

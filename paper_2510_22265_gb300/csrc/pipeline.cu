@@ -210,16 +210,18 @@ __global__ void base_sizes(const int32_t *np, const int32_t *pass_len, int maxpa
 __global__ void base_write(const int32_t *np, const int32_t *K, const int32_t *pass_len, const uint32_t *tail,
                            const int32_t *tail_len, const uint8_t *bytes, int cap, int maxpass, int nblk,
                            const uint32_t *meta_off, const uint32_t *pay_off, const unsigned long long *tot,
-                           uint8_t *out) {
+                           uint8_t *out, long long out_cap) {
     const int lane = threadIdx.x & 31;
     const unsigned long long meta_total = tot[0];
     for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nblk; b += (gridDim.x * blockDim.x) >> 5) {
         const int n = np[b];
         uint8_t *m = out + meta_off[b];
+        if (!INB((long long)meta_off[b] + 6, out_cap + 6)) continue;
         if (n <= 0) {
             if (lane == 0) m[0] = 0;
             continue;
         }
+        if (!INB(n - 1, maxpass)) continue;
         const size_t pi = (size_t)b * maxpass + n - 1;
         const uint32_t l = (uint32_t)pass_len[pi];
         const int tl = tail_len[pi];
@@ -234,7 +236,9 @@ __global__ void base_write(const int32_t *np, const int32_t *K, const int32_t *p
         uint8_t *p = out + meta_total + pay_off[b];
         const uint8_t *src = bytes + (size_t)b * cap;
         const uint32_t nf = l - tl;
-        for (uint32_t k = lane; k < l; k += 32) p[k] = k < nf ? src[k] : (uint8_t)(tail[pi] >> (8 * (k - nf)));
+        for (uint32_t k = lane; k < l; k += 32)
+            if (INB((long long)meta_total + pay_off[b] + k, out_cap) && INB(k < nf ? k : 0, cap))
+                p[k] = k < nf ? src[k] : (uint8_t)(tail[pi] >> (8 * (k - nf)));
     }
 }
 
@@ -458,11 +462,13 @@ int run_base_loop(FieldBufs &f, const FieldGeom &g, double q, int fallback, cons
     int rc = EBCC_OK;
     for (int step = 0; step < 400; step++) {
         rc = pcrd_select(f.hull, g.nblocks, &f.bl->budget, &f.bl->sel_eval, st);
+        STAGE(st, "select");
         if (!rc) rc = pcrd_npass(f.hull, g.nblocks, &f.bl->sel_eval, f.npass, st);
         if (!rc) rc = base_recon(f.qt, g, f.t1.K, f.npass, f.W, st);
         if (!rc) rc = dwt_inverse_ex(f.W, nullptr, f.s1, f.s2, g.ny, g.nx, g.L, fin, 0.0, 1.0, st);
         if (rc) break;
-        bl_update<<<1, 1, 0, st>>>(f.bl);
+        PROF("bl_update", st, 0.0, bl_update<<<1, 1, 0, st>>>(f.bl););
+        if (ebcc_debug_sync_enabled() && ebcc_stage_check(st, "base eval", __LINE__)) { rc = EBCC_ECUDA; break; }
         if (cudaMemcpyAsync(&hdone[step & 1], &f.bl->done, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaEventRecord(ev[step & 1], st) != cudaSuccess) { rc = EBCC_ECUDA; break; }
         if (step >= 1) {
@@ -481,7 +487,8 @@ int run_base_loop(FieldBufs &f, const FieldGeom &g, double q, int fallback, cons
 
 int pack_base_size(FieldBufs &f, const FieldGeom &g, const Sel *sel_dev, unsigned long long &bl, cudaStream_t st) {
     RC(pcrd_npass(f.hull, g.nblocks, sel_dev, f.npass, st));
-    base_sizes<<<1, 1024, 0, st>>>(f.npass, f.t1.pass_len, T1_MAXPASS, g.nblocks, f.meta_off, f.pay_off, f.tot);
+    STAGE(st, "npass for pack");
+    PROF("base_sizes", st, 0.0, base_sizes<<<1, 1024, 0, st>>>(f.npass, f.t1.pass_len, T1_MAXPASS, g.nblocks, f.meta_off, f.pay_off, f.tot););
     CK(cudaGetLastError());
     unsigned long long t[2];
     CK(cudaMemcpyAsync(t, f.tot, sizeof(t), cudaMemcpyDeviceToHost, st));
@@ -490,10 +497,10 @@ int pack_base_size(FieldBufs &f, const FieldGeom &g, const Sel *sel_dev, unsigne
     return EBCC_OK;
 }
 
-int pack_base_write(FieldBufs &f, const FieldGeom &g, uint8_t *out, cudaStream_t st) {
+int pack_base_write(FieldBufs &f, const FieldGeom &g, uint8_t *out, long long out_cap, cudaStream_t st) {
     // f.npass / meta_off / pay_off / tot are those of the last pack_base_size
-    base_write<<<152 * 2, 256, 0, st>>>(f.npass, f.t1.K, f.t1.pass_len, f.t1.tail, f.t1.tail_len, f.t1.bytes,
-                                        f.t1.cap, T1_MAXPASS, g.nblocks, f.meta_off, f.pay_off, f.tot, out);
+    PROF("base_write", st, 0.0, base_write<<<152 * 2, 256, 0, st>>>(f.npass, f.t1.K, f.t1.pass_len, f.t1.tail, f.t1.tail_len, f.t1.bytes,
+                                        f.t1.cap, T1_MAXPASS, g.nblocks, f.meta_off, f.pay_off, f.tot, out, out_cap););
     CK(cudaGetLastError());
     return EBCC_OK;
 }
@@ -537,12 +544,17 @@ int compress_field(FieldBufs &f, const float *x_dev, int ny, int nx, double boun
     CK(cudaMemcpyAsync(f.blk, blk.data(), blk.size() * sizeof(BlockDesc), cudaMemcpyHostToDevice, st));
     // ---- per-point acceptance intervals of the bound test (FP64, once)
     RC(make_bounds(x_dev, N, mn, range, eps_abs, guard, f.bounds, st));
+    STAGE(st, "bounds");
     // ---- base layer: DWT of the normalised field, quantise, tier-1, hulls
     RC(dwt_forward(x_dev, f.W, f.s1, f.s2, ny, nx, L, mn, 1.0 / range, st));
+    STAGE(st, "dwt fwd");
     RC(quantise_base(f.W, f.qt, g, 1, st));
+    STAGE(st, "quantise");
     CK(cudaMemsetAsync(f.t1.status, 0, 4, st));
-    RC(t1_encode_blocks(f.qt, f.blk, g.nblocks, g.cw, g.ch, f.t1, 1, nullptr, st));
+    RC(t1_encode_blocks(f.qt, f.blk, g.nblocks, g.cw, g.ch, f.t1, 1, nullptr, (long long)N, st));
+    STAGE(st, "tier-1");
     RC(pcrd_hulls(f.t1.npass, f.t1.pass_len, f.t1.dD, f.t1.D0, g.nblocks, T1_MAXPASS, f.hull, st));
+    STAGE(st, "hulls");
     // ---- base loop with q
     BaseLoop b1;
     RC(run_base_loop(f, g, p.q, 0, p, b1, st));
@@ -556,11 +568,13 @@ int compress_field(FieldBufs &f, const float *x_dev, int ny, int nx, double boun
     RC(base_recon(f.qt, g, f.t1.K, f.npass, f.W, st));
     InvFinal store{0, nullptr, nullptr, nullptr};
     RC(dwt_inverse_ex(f.W, f.Abase, f.s1, f.s2, ny, nx, L, store, 0.0, 1.0, st));
+    STAGE(st, "A_base");
     Sel sel_two;
     CK(cudaMemcpyAsync(&sel_two, &f.bl->sel_f, sizeof(Sel), cudaMemcpyDeviceToHost, st));
     // ---- residual layer: A_residue (FP64), DWT, SPIHT with guard retries
     RC(residue(x_dev, f.Abase, N, mn, 1.0 / range, f.R, st));
     RC(dwt_forward(f.R, f.W, f.s1, f.s2, ny, nx, L, 0.0, 0.0, st));
+    STAGE(st, "residue dwt");
     int G = p.spiht_guard_bits, es = 0, nmax = -1;
     long long nbits = 0;
     unsigned long long bad = 0;
@@ -568,16 +582,20 @@ int compress_field(FieldBufs &f, const float *x_dev, int ny, int nx, double boun
     for (int attempt = 0; attempt < 3; attempt++) {
         es = (int)floor(log2(eps_n)) - G;
         RC(spiht_quantise(f.W, N, es, f.s, st));
+        STAGE(st, "spiht quantise");
         CK(cudaMemsetAsync(f.status, 0, 4, st));
         RC(spiht_encode(f.s, ny, nx, L, f.sp_stream, f.sp_cap, f.nbits, f.nmax, f.sig_pos, f.lsp_idx, f.refine_start,
                         f.status, f.sw, st));
+        STAGE(st, "spiht encode");
         int sstat = 0;
         CK(cudaMemcpyAsync(&nbits, f.nbits, 8, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(&nmax, f.nmax, 4, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(&sstat, f.status, 4, cudaMemcpyDeviceToHost, st));
         CK(cudaMemsetAsync(&f.tl->count, 0, 8, st));
         RC(spiht_prefix_recon(f.s, f.sig_pos, f.lsp_idx, f.refine_start, f.nbits, 0, N, es, f.R, st));
+        STAGE(st, "prefix recon");
         RC(dwt_inverse_ex(f.R, nullptr, f.s1, f.s2, ny, nx, L, chk, 0.0, 1.0, st));
+        STAGE(st, "full check");
         CK(cudaMemcpyAsync(&bad, &f.tl->count, 8, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         if (sstat) return EBCC_ECAPACITY;
@@ -590,7 +608,7 @@ int compress_field(FieldBufs &f, const float *x_dev, int ny, int nx, double boun
     if (bad > 0) {  // last resort: exact values of the points still outside the bound
         InvFinal st0{0, nullptr, nullptr, nullptr};
         RC(dwt_inverse_ex(f.R, f.W, f.s1, f.s2, ny, nx, L, st0, 0.0, 1.0, st));  // R holds the full-stream residual coefs
-        escape_kernel<<<1, 1024, 0, st>>>(f.Abase, f.W, f.bounds, x_dev, N, f.esc, f.nesc, f.esc_cap);
+        PROF("escape_kernel", st, 0.0, escape_kernel<<<1, 1024, 0, st>>>(f.Abase, f.W, f.bounds, x_dev, N, f.esc, f.nesc, f.esc_cap););
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(&nesc, f.nesc, 8, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -598,7 +616,7 @@ int compress_field(FieldBufs &f, const float *x_dev, int ny, int nx, double boun
     }
     stt.n_escape = (int)nesc;
     // ---- binary search for the truncation point
-    tl_init<<<1, 1, 0, st>>>(f.tl, len, nbits);
+    PROF("tl_init", st, 0.0, tl_init<<<1, 1, 0, st>>>(f.tl, len, nbits););
     CK(cudaGetLastError());
     {
         int *hdone = nullptr;
@@ -615,7 +633,8 @@ int compress_field(FieldBufs &f, const float *x_dev, int ny, int nx, double boun
                                     f.R, st);
             if (!rc) rc = dwt_inverse_ex(f.R, nullptr, f.s1, f.s2, ny, nx, L, chk, 0.0, 1.0, st);
             if (rc) break;
-            tl_update<<<1, 1, 0, st>>>(f.tl);
+            PROF("tl_update", st, 0.0, tl_update<<<1, 1, 0, st>>>(f.tl););
+            if (ebcc_debug_sync_enabled() && ebcc_stage_check(st, "trunc eval", __LINE__)) { rc = EBCC_ECUDA; break; }
             cudaMemcpyAsync(&hdone[step & 1], &f.tl->done, 4, cudaMemcpyDeviceToHost, st);
             cudaEventRecord(ev[step & 1], st);
             if (step >= 1) {
@@ -640,6 +659,9 @@ int compress_field(FieldBufs &f, const float *x_dev, int ny, int nx, double boun
     RC(pack_base_size(f, g, &f.bl->sel_f, bl2, st));  // sel_f of the q loop is still in f.bl
     const unsigned long long len2 = HDR_BYTES + bl2 + t_high + 8 * nesc;
     stt.len_two = (long long)len2;
+    // escaped points had their acceptance interval opened up for the
+    // truncation search; the base-only candidate is judged on the true bound
+    if (nesc) RC(make_bounds(x_dev, N, mn, range, eps_abs, guard, f.bounds, st));
     BaseLoop b2;
     RC(run_base_loop(f, g, 1.0, 1, p, b2, st));
     stt.r_base1 = b2.r_f; stt.iters_base1 = b2.iters;
@@ -653,7 +675,7 @@ int compress_field(FieldBufs &f, const float *x_dev, int ny, int nx, double boun
     if (use_one) {
         if (cap < HDR_BYTES + bl1) return EBCC_ECAPACITY;
         write_header(hh, 0, L, g.cw, g.ch, g.P, 0, -1, ny, nx, (uint32_t)bl1, 0, 0, mn, mx, eps_abs);
-        RC(pack_base_write(f, g, out + HDR_BYTES, st));
+        RC(pack_base_write(f, g, out + HDR_BYTES, (long long)(cap - HDR_BYTES), st));
         CK(cudaMemcpyAsync(out, hh.b, HDR_BYTES, cudaMemcpyHostToDevice, st));
         *out_len = HDR_BYTES + bl1;
         stt.used_fallback = 1;
@@ -668,7 +690,7 @@ int compress_field(FieldBufs &f, const float *x_dev, int ny, int nx, double boun
         int flags = (t_high > 0 ? 2 : 0) | (nesc ? 4 : 0);
         write_header(hh, flags, L, g.cw, g.ch, g.P, es, nmax, ny, nx, (uint32_t)bl2, (uint32_t)t_high,
                      (uint32_t)nesc, mn, mx, eps_abs);
-        RC(pack_base_write(f, g, out + HDR_BYTES, st));
+        RC(pack_base_write(f, g, out + HDR_BYTES, (long long)(cap - HDR_BYTES), st));
         if (t_high > 0)
             CK(cudaMemcpyAsync(out + HDR_BYTES + bl2, f.sp_stream, t_high, cudaMemcpyDeviceToDevice, st));
         if (nesc)
@@ -719,7 +741,7 @@ __global__ void fill_kernel(float *o, size_t n, float v) {
 int decompress_field(const uint8_t *s_dev, size_t len, const ParsedHeader &h, float *out, Arena &a, cudaStream_t st) {
     const size_t N = (size_t)h.ny * h.nx;
     if (h.flags & 1) {
-        fill_kernel<<<152 * 4, 256, 0, st>>>(out, N, (float)h.mn);
+        PROF("fill_kernel", st, 0.0, fill_kernel<<<152 * 4, 256, 0, st>>>(out, N, (float)h.mn););
         CK(cudaGetLastError());
         return EBCC_OK;
     }
@@ -745,13 +767,14 @@ int decompress_field(const uint8_t *s_dev, size_t len, const ParsedHeader &h, fl
     SpihtWork sw;
     spiht_work_carve(spw, N, &sw);
     CK(cudaMemcpyAsync(bd, blk.data(), nb * sizeof(BlockDesc), cudaMemcpyHostToDevice, st));
-    base_parse<<<1, 1, 0, st>>>(s_dev, HDR_BYTES, h.bl, (int)nb, np, K, bl, off, ok);
+    PROF("base_parse", st, 0.0, base_parse<<<1, 1, 0, st>>>(s_dev, HDR_BYTES, h.bl, (int)nb, np, K, bl, off, ok););
     CK(cudaGetLastError());
     int hok = 0;
     CK(cudaMemcpyAsync(&hok, ok, 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (!hok) return EBCC_ECORRUPT;
-    RC(t1_decode_blocks(s_dev, off, bl, bd, K, np, (int)nb, g.cw, g.ch, W, nullptr, nullptr, nullptr, st));
+    RC(t1_decode_blocks(s_dev, off, bl, bd, K, np, (int)nb, g.cw, g.ch, W, nullptr, nullptr, nullptr, (long long)N,
+                         st));
     const double range = h.mx - h.mn;
     if ((h.flags & 2) && h.rl > 0) {
         InvFinal store{0, nullptr, nullptr, nullptr};
@@ -766,7 +789,7 @@ int decompress_field(const uint8_t *s_dev, size_t len, const ParsedHeader &h, fl
     }
     if (h.ne) {
         CK(cudaMemsetAsync(ok, 0xFF, 4, st));
-        scatter_escapes<<<64, 256, 0, st>>>(s_dev + HDR_BYTES + h.bl + h.rl, h.ne, out, (long long)N, ok);
+        PROF("scatter_escapes", st, 0.0, scatter_escapes<<<64, 256, 0, st>>>(s_dev + HDR_BYTES + h.bl + h.rl, h.ne, out, (long long)N, ok););
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(&hok, ok, 4, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));

@@ -88,6 +88,7 @@ __global__ void __launch_bounds__(NT) recon_kernel(const int32_t *__restrict__ q
         if (m) {
             const BandGeom &B = g.band[band_of(g, y, x)];
             int blk = B.blk0 + ((y - B.y0) / g.ch) * B.nbx + (x - B.x0) / g.cw;
+            if (!INB(blk, g.nblocks)) blk = 0;
             int K = Kb[blk], np = npb[blk];
             int s = 31 - __clz(m);
             int spp = (v >> 30) & 1;
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(NT) sprefix_kernel(const int32_t *__restrict__
         if (m && sp != 0xFFFFFFFFu && (long long)sp < T) {
             int ns = 31 - __clz(m), p = ns;
             long long li = lsp_idx[i];
-            while (p > 0 && rs[p - 1] + li < T) p--;
+            while (p > 0 && INB(p - 1, 32) && rs[p - 1] + li < T) p--;
             float val = deq((m >> p) << p, p, step);
             o = v < 0 ? -val : val;
         }
@@ -210,40 +211,40 @@ int minmax_finite(const float *x, size_t n, double *mm_dev, int *nonfinite_dev, 
     // the two uint32 keys live right after the two doubles
     uint32_t *keys = (uint32_t *)(mm_dev + 2);
     mm_init<<<1, 1, 0, st>>>(keys, nonfinite_dev);
-    mm_kernel<<<grid_for(n), NT, 0, st>>>(x, n, keys, nonfinite_dev);
+    PROF("mm_kernel", st, 4.0 * n, mm_kernel<<<grid_for(n), NT, 0, st>>>(x, n, keys, nonfinite_dev););
     mm_final<<<1, 1, 0, st>>>(keys, mm_dev);
     CK(cudaGetLastError());
     return EBCC_OK;
 }
 
 int quantise_base(const float *coef, int32_t *qt, const FieldGeom &g, int sign_magnitude, cudaStream_t st) {
-    quant_kernel<<<grid_for((size_t)g.ny * g.nx), NT, 0, st>>>(coef, qt, g, sign_magnitude);
+    PROF("quant_kernel", st, 8.0 * g.ny * g.nx, quant_kernel<<<grid_for((size_t)g.ny * g.nx), NT, 0, st>>>(coef, qt, g, sign_magnitude););
     CK(cudaGetLastError());
     return EBCC_OK;
 }
 
 int base_recon(const int32_t *qt, const FieldGeom &g, const int32_t *K, const int32_t *npass, float *coef,
                cudaStream_t st) {
-    recon_kernel<<<grid_for((size_t)g.ny * g.nx), NT, 0, st>>>(qt, g, K, npass, coef);
+    PROF("recon_kernel", st, 8.0 * g.ny * g.nx, recon_kernel<<<grid_for((size_t)g.ny * g.nx), NT, 0, st>>>(qt, g, K, npass, coef););
     CK(cudaGetLastError());
     return EBCC_OK;
 }
 
 int make_bounds(const float *x, size_t n, double mn, double range, double eps_abs, double guard, float2 *bounds,
                 cudaStream_t st) {
-    bounds_kernel<<<grid_for(n), NT, 0, st>>>(x, n, mn, range, eps_abs - guard, bounds);
+    PROF("bounds_kernel", st, 12.0 * n, bounds_kernel<<<grid_for(n), NT, 0, st>>>(x, n, mn, range, eps_abs - guard, bounds););
     CK(cudaGetLastError());
     return EBCC_OK;
 }
 
 int residue(const float *x, const float *abase, size_t n, double mn, double inv_range, float *res, cudaStream_t st) {
-    residue_kernel<<<grid_for(n), NT, 0, st>>>(x, abase, n, mn, inv_range, res);
+    PROF("residue_kernel", st, 12.0 * n, residue_kernel<<<grid_for(n), NT, 0, st>>>(x, abase, n, mn, inv_range, res););
     CK(cudaGetLastError());
     return EBCC_OK;
 }
 
 int spiht_quantise(const float *w, size_t n, int step_exp, int32_t *s, cudaStream_t st) {
-    squant_kernel<<<grid_for(n), NT, 0, st>>>(w, n, step_exp, s);
+    PROF("squant_kernel", st, 8.0 * n, squant_kernel<<<grid_for(n), NT, 0, st>>>(w, n, step_exp, s););
     CK(cudaGetLastError());
     return EBCC_OK;
 }
@@ -251,8 +252,8 @@ int spiht_quantise(const float *w, size_t n, int step_exp, int32_t *s, cudaStrea
 int spiht_prefix_recon(const int32_t *s, const uint32_t *sig_pos, const uint32_t *lsp_idx, const int64_t *refine_start,
                        const int64_t *nbits_dev, int64_t nbits_host, size_t n, int step_exp, float *out,
                        cudaStream_t st) {
-    sprefix_kernel<<<grid_for(n), NT, 0, st>>>(s, sig_pos, lsp_idx, refine_start, nbits_dev, nbits_host, n, step_exp,
-                                               out);
+    PROF("sprefix_kernel", st, 16.0 * n, sprefix_kernel<<<grid_for(n), NT, 0, st>>>(s, sig_pos, lsp_idx, refine_start, nbits_dev, nbits_host, n, step_exp,
+                                               out););
     CK(cudaGetLastError());
     return EBCC_OK;
 }

@@ -113,10 +113,12 @@ __global__ void maxima_kernel(SG g, int l, const int32_t *__restrict__ s, uint32
         int n = children(g, idx, c);
         uint32_t md = 0, ml = 0;
         for (int q = 0; q < n; q++) {
+            if (!INB(c[q], (long long)g.ny * g.nx)) continue;
             uint32_t cd = maxd[c[q]];
             md = max(md, max(absi(s[c[q]]), cd));
             ml = max(ml, cd);
         }
+        if (!INB(idx, (long long)g.ny * g.nx)) continue;
         maxd[idx] = md;
         maxl[idx] = ml;
     }
@@ -179,7 +181,7 @@ __device__ __forceinline__ void win_clear(EncShared &sh) {
     for (int k = threadIdx.x; k < WIN_WORDS; k += ET) sh.win[k] = 0;
 }
 __device__ __forceinline__ void win_set(EncShared &sh, unsigned long long b) {
-    atomicOr(&sh.win[(b >> 5) - sh.wbase], bitmask(b));
+    if (INB((long long)(b >> 5) - (long long)sh.wbase, WIN_WORDS)) atomicOr(&sh.win[(b >> 5) - sh.wbase], bitmask(b));
 }
 __device__ __forceinline__ void win_flush(EncShared &sh, uint32_t *out32, unsigned long long cap_words,
                                           unsigned long long end_bit, int *status) {
@@ -201,6 +203,8 @@ __global__ void __launch_bounds__(ET) encode_kernel(SG g, const int32_t *__restr
                                                     uint32_t *lis_new, uint32_t *wave_a, uint32_t *wave_b) {
     __shared__ EncShared sh;
     const int tid = threadIdx.x;
+    const long long NN = (long long)g.ny * g.nx;
+    (void)NN;
     const int hL = g.h[g.L], wL = g.w[g.L];
     const long nroot = (long)hL * wL;
     // top plane from the LL roots (every coefficient is a root or below one)
@@ -228,14 +232,14 @@ __global__ void __launch_bounds__(ET) encode_kernel(SG g, const int32_t *__restr
         uint32_t idx = 0;
         if (k < nroot) {
             idx = (uint32_t)(k / wL) * g.nx + (uint32_t)(k % wL);
-            lip[k] = idx;
+            if (INB(k, NN)) lip[k] = idx;
             uint32_t c[9];
             v[0] = children(g, idx, c) > 0;
         }
         block_scan(v, sh);
         if (k < nroot && v[0] != (int)0x7FFFFFFF) {
             uint32_t c[9];
-            if (children(g, idx, c) > 0) lis[sh.nlis + v[0]] = idx << 1;
+            if (children(g, idx, c) > 0 && INB(sh.nlis + v[0], NN)) lis[sh.nlis + v[0]] = idx << 1;
         }
         __syncthreads();
         if (tid == 0) sh.nlis += sh.tot[0];
@@ -254,7 +258,8 @@ __global__ void __launch_bounds__(ET) encode_kernel(SG g, const int32_t *__restr
                 uint32_t x = 0;
                 bool sg = false;
                 if (k < nl) {
-                    x = lip[k];
+                    x = INB(k, NN) ? lip[k] : 0;
+                    if (!INB(x, NN)) x = 0;
                     sg = absi(s[x]) >= T;
                     v[0] = 1 + sg; v[1] = !sg; v[2] = sg;
                 }
@@ -266,11 +271,13 @@ __global__ void __launch_bounds__(ET) encode_kernel(SG g, const int32_t *__restr
                     if (sg) {
                         win_set(sh, bp);
                         if (s[x] < 0) win_set(sh, bp + 1);
+                        if (INB(sh.nlsp + v[2], NN)) {
                         sig_pos[x] = (uint32_t)(bp + 1);
                         lsp_idx[x] = (uint32_t)(sh.nlsp + v[2]);
                         lsp[sh.nlsp + v[2]] = x;
+                        }
                     } else {
-                        lip[keep_n + v[1]] = x;
+                        if (INB(keep_n + v[1], NN)) lip[keep_n + v[1]] = x;
                     }
                 }
                 __syncthreads();
@@ -301,7 +308,8 @@ __global__ void __launch_bounds__(ET) encode_kernel(SG g, const int32_t *__restr
                     bool sg = false;
                     uint32_t sigmask = 0;
                     if (k < ncur) {
-                        e = cur[k];
+                        e = INB(k, NN) ? cur[k] : 0;
+                        if (!INB(e >> 1, NN)) e = 0;
                         idx = e >> 1;
                         v[0] = 1;
                         if ((e & 1) == 0) {  // type A: S_n(D)
@@ -309,6 +317,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(SG g, const int32_t *__restr
                             if (sg) {
                                 nc = children(g, idx, c);
                                 for (int q = 0; q < nc; q++) {
+                                    if (!INB(c[q], NN)) c[q] = 0;
                                     bool cs = absi(s[c[q]]) >= T;
                                     sigmask |= (uint32_t)cs << q;
                                     v[0] += 1 + cs; v[1] += !cs; v[2] += cs;
@@ -329,7 +338,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(SG g, const int32_t *__restr
                     if (k < ncur) {
                         unsigned long long bp = sh.pos + v[0];
                         if (!sg) {
-                            lis_new[sh.nstay + v[4]] = e;
+                            if (INB(sh.nstay + v[4], NN)) lis_new[sh.nstay + v[4]] = e;
                         } else if ((e & 1) == 0) {
                             win_set(sh, bp++);
                             long long li = sh.nlip + v[1], ls = sh.nlsp + v[2];
@@ -339,17 +348,20 @@ __global__ void __launch_bounds__(ET) encode_kernel(SG g, const int32_t *__restr
                                     if (s[c[q]] < 0) win_set(sh, bp + 1);
                                     sig_pos[c[q]] = (uint32_t)(bp + 1);
                                     lsp_idx[c[q]] = (uint32_t)ls;
-                                    lsp[ls++] = c[q];
+                                    if (INB(ls, NN)) lsp[ls] = c[q];
+                                    ls++;
                                     bp += 2;
                                 } else {
-                                    lip[li++] = c[q];
+                                    if (INB(li, NN)) lip[li] = c[q];
+                                    li++;
                                     bp += 1;
                                 }
                             }
-                            if (v[3] != (int)0x7FFFFFFF && has_L(g, idx)) nxt[sh.nnext + v[3]] = (idx << 1) | 1;
+                            if (has_L(g, idx) && INB(sh.nnext + v[3], NN)) nxt[sh.nnext + v[3]] = (idx << 1) | 1;
                         } else {
                             win_set(sh, bp);
-                            for (int q = 0; q < nc; q++) nxt[sh.nnext + v[3] + q] = c[q] << 1;
+                            for (int q = 0; q < nc; q++)
+                                if (INB(sh.nnext + v[3] + q, NN)) nxt[sh.nnext + v[3] + q] = c[q] << 1;
                         }
                     }
                     __syncthreads();
@@ -364,6 +376,9 @@ __global__ void __launch_bounds__(ET) encode_kernel(SG g, const int32_t *__restr
                 cur = nxt;
                 ncur = sh.nnext;
                 nxt = (nxt == wave_a) ? wave_b : wave_a;
+                // every thread must have read the wave size before thread 0
+                // resets the counter for the next wave
+                __syncthreads();
             }
             // the stayers become the LIS of the next plane
             const long long ns = sh.nstay;
@@ -380,7 +395,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(SG g, const int32_t *__restr
                 if (tid == 0) sh.wbase = (sh.pos + base) >> 5;
                 win_clear(sh);
                 __syncthreads();
-                if (k < lsp_before && ((absi(s[lsp[k]]) >> n) & 1)) win_set(sh, sh.pos + k);
+                if (k < lsp_before && INB(k, NN) && INB(lsp[k], NN) && ((absi(s[lsp[k]]) >> n) & 1)) win_set(sh, sh.pos + k);
                 __syncthreads();
                 long long end = base + ET < lsp_before ? base + ET : lsp_before;
                 win_flush(sh, out32, cap_words, sh.pos + end, status);
@@ -515,16 +530,16 @@ int spiht_encode(const int32_t *s, int ny, int nx, int L, uint8_t *out, size_t c
     CK(cudaMemsetAsync(refine_start, 0, 32 * sizeof(int64_t), st));
     CK(cudaMemsetAsync(out, 0, cap_bytes & ~(size_t)3, st));
     for (int l = 2; l <= L; l++) {
-        maxima_kernel<<<152 * 4, 256, 0, st>>>(g, l, s, w.maxd, w.maxl);
+        PROF("maxima_kernel", st, 0.0, maxima_kernel<<<152 * 4, 256, 0, st>>>(g, l, s, w.maxd, w.maxl););
         CK(cudaGetLastError());
     }
     if (L >= 1) {
-        maxima_kernel<<<152, 256, 0, st>>>(g, 0, s, w.maxd, w.maxl);
+        PROF("maxima_kernel", st, 0.0, maxima_kernel<<<152, 256, 0, st>>>(g, 0, s, w.maxd, w.maxl););
         CK(cudaGetLastError());
     }
-    encode_kernel<<<1, ET, 0, st>>>(g, s, w.maxd, w.maxl, (uint32_t *)out, cap_bytes / 4, (long long *)nbits_dev,
+    PROF("encode_kernel", st, 0.0, encode_kernel<<<1, ET, 0, st>>>(g, s, w.maxd, w.maxl, (uint32_t *)out, cap_bytes / 4, (long long *)nbits_dev,
                                     nmax_dev, sig_pos, lsp_idx, (long long *)refine_start, status_dev, w.lip, w.lsp,
-                                    w.lis_a, w.lis_a + n, w.lis_b, w.lis_b + n);
+                                    w.lis_a, w.lis_a + n, w.lis_b, w.lis_b + n););
     CK(cudaGetLastError());
     return EBCC_OK;
 }
@@ -537,12 +552,12 @@ int spiht_decode(const uint8_t *in, int64_t nbits, int ny, int nx, int L, int nm
     CK(cudaMemsetAsync(plane, 0xFF, n, st));
     CK(cudaMemsetAsync(neg, 0, n, st));
     if (nmax >= 0 && nbits > 0) {
-        decode_kernel<<<1, 32, 0, st>>>(g, in, nbits, nmax, mag, plane, neg, coef_out, step_exp, w.lip, w.lsp,
-                                        w.lis_a, (long long)(4 * n));
+        PROF("decode_kernel", st, 0.0, decode_kernel<<<1, 32, 0, st>>>(g, in, nbits, nmax, mag, plane, neg, coef_out, step_exp, w.lip, w.lsp,
+                                        w.lis_a, (long long)(4 * n)););
         CK(cudaGetLastError());
     }
     if (coef_out) {
-        dequant_kernel<<<152 * 4, 256, 0, st>>>(mag, plane, neg, n, step_exp, coef_out);
+        PROF("dequant_kernel", st, 0.0, dequant_kernel<<<152 * 4, 256, 0, st>>>(mag, plane, neg, n, step_exp, coef_out););
         CK(cudaGetLastError());
     }
     return EBCC_OK;

@@ -89,7 +89,7 @@ int ebcc_t1_encode_dev(const int32_t *q, const int32_t *orient, int nblk, int w,
     if (nblk) CK(cudaMemcpy(dbd, bd.data(), nblk * sizeof(BlockDesc), cudaMemcpyHostToDevice));
     CK(cudaMemset(status, 0, 4));
     T1Out o{bytes, cap, maxpass, K, npass, pass_len, tail, tail_len, dD, D0, status};
-    RC(t1_encode_blocks(const_cast<int32_t *>(q), dbd, nblk, w, h, o, 0, spp, st));
+    RC(t1_encode_blocks(const_cast<int32_t *>(q), dbd, nblk, w, h, o, 0, spp, (long long)nblk * w * h, st));
     int hs = 0;
     CK(cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -113,7 +113,8 @@ int ebcc_t1_decode_dev(const uint8_t *bytes, const int64_t *off, const int32_t *
     BlockDesc *dbd;
     RC(t.get(&dbd, nblk + 1));
     if (nblk) CK(cudaMemcpy(dbd, bd.data(), nblk * sizeof(BlockDesc), cudaMemcpyHostToDevice));
-    RC(t1_decode_blocks(bytes, off, len, dbd, K, npass, nblk, w, h, nullptr, mag, plane, neg, st));
+    RC(t1_decode_blocks(bytes, off, len, dbd, K, npass, nblk, w, h, nullptr, mag, plane, neg, (long long)nblk * w * h,
+                         st));
     CK(cudaStreamSynchronize(st));
     return EBCC_OK;
 }

@@ -198,7 +198,7 @@ __host__ __device__ inline SmemLayout smem_layout(int maxn, int maxh, bool dec) 
 
 __global__ void __launch_bounds__(WARPS * 32) t1_encode_kernel(int32_t *qt, const BlockDesc *blk, int nblk, T1Out o,
                                                                int mark_spp_in_q, uint8_t *spp_out, SmemLayout SL,
-                                                               int maxh) {
+                                                               int maxh, long long nq) {
     extern __shared__ __align__(16) uint8_t sm[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint8_t *base = sm + wid * SL.per_warp;
@@ -216,12 +216,13 @@ __global__ void __launch_bounds__(WARPS * 32) t1_encode_kernel(int32_t *qt, cons
         uint32_t mx = 0;
         for (int i = lane; i < n; i += 32) {
             int r = i / w, c = i - r * w;
-            int32_t v = qt[d.off + (int64_t)r * d.stride + c];
+            int32_t v = INB(d.off + (int64_t)r * d.stride + c, nq) ? qt[d.off + (int64_t)r * d.stride + c] : 0;
             // sign-magnitude Mallat array (bit 31 sign, bit 30 trace flag) or two's complement
             uint32_t m = mark_spp_in_q ? (uint32_t)v & 0x3FFFFFFFu : (uint32_t)(v < 0 ? -v : v);
             mag[i] = m | (v < 0 ? 0x80000000u : 0);
             mx = max(mx, m);
         }
+        __syncwarp();  // the sign words below read magnitudes staged by other lanes
         for (int r = lane; r < h; r += 32) {
             uint64_t ng = 0;
             for (int c = 0; c < w; c++) ng |= (uint64_t)(mag[r * w + c] >> 31) << c;
@@ -252,6 +253,7 @@ __global__ void __launch_bounds__(WARPS * 32) t1_encode_kernel(int32_t *qt, cons
                 auto end_pass = [&](int64_t dd) {
                     uint32_t tail;
                     int tl;
+                    if (!INB(pass, o.maxpass)) return;
                     o.pass_len[pb + pass] = e.trunc(tail, tl);
                     o.tail[pb + pass] = tail;
                     o.tail_len[pb + pass] = tl;
@@ -367,7 +369,7 @@ __global__ void __launch_bounds__(WARPS * 32) t1_encode_kernel(int32_t *qt, cons
             uint32_t f = (mag[i] >> 30) & 1;
             if (mark_spp_in_q) {
                 int64_t at = d.off + (int64_t)r * d.stride + c;
-                qt[at] = (qt[at] & ~0x40000000) | (int32_t)(f << 30);
+                if (INB(at, nq)) qt[at] = (qt[at] & ~0x40000000) | (int32_t)(f << 30);
             }
             if (spp_out) spp_out[(size_t)b * n + i] = (uint8_t)f;
         }
@@ -381,7 +383,7 @@ __global__ void __launch_bounds__(WARPS * 32) t1_decode_kernel(const uint8_t *by
                                                                const int32_t *len, const BlockDesc *blk,
                                                                const int32_t *Kb, const int32_t *npb, int nblk,
                                                                float *coef, int32_t *omag, int8_t *oplane,
-                                                               uint8_t *oneg, SmemLayout SL, int maxh) {
+                                                               uint8_t *oneg, SmemLayout SL, int maxh, long long nq) {
     extern __shared__ __align__(16) uint8_t sm[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint8_t *base = sm + wid * SL.per_warp;
@@ -488,7 +490,7 @@ __global__ void __launch_bounds__(WARPS * 32) t1_decode_kernel(const uint8_t *by
             uint32_t m = mag[i];
             if (coef) {
                 float val = p >= 0 ? deq(m, p, d.delta) : 0.0f;
-                coef[d.off + (int64_t)r * d.stride + c] = ng ? -val : val;
+                if (INB(d.off + (int64_t)r * d.stride + c, nq)) coef[d.off + (int64_t)r * d.stride + c] = ng ? -val : val;
             } else {
                 omag[(size_t)b * n + i] = p >= 0 ? (int32_t)m : 0;
                 oplane[(size_t)b * n + i] = (int8_t)p;
@@ -585,28 +587,28 @@ int grid_for(int nblk) {
 }  // namespace
 
 int t1_encode_blocks(int32_t *qt, const BlockDesc *blk, int nblk, int maxw, int maxh, const T1Out &o,
-                     int mark_spp_in_q, uint8_t *spp_out, cudaStream_t st) {
+                     int mark_spp_in_q, uint8_t *spp_out, long long nq, cudaStream_t st) {
     int rc = upload_tables();
     if (rc) return rc;
     if (nblk <= 0) return EBCC_OK;
     if (maxw > 64 || maxh > 64) return EBCC_EINVAL;
     SmemLayout SL = smem_layout(maxw * maxh, maxh, false);
-    t1_encode_kernel<<<grid_for(nblk), WARPS * 32, WARPS * SL.per_warp, st>>>(qt, blk, nblk, o, mark_spp_in_q,
-                                                                             spp_out, SL, maxh);
+    PROF("t1_encode_kernel", st, 0.0, t1_encode_kernel<<<grid_for(nblk), WARPS * 32, WARPS * SL.per_warp, st>>>(qt, blk, nblk, o, mark_spp_in_q,
+                                                                             spp_out, SL, maxh, nq););
     CK(cudaGetLastError());
     return EBCC_OK;
 }
 
 int t1_decode_blocks(const uint8_t *bytes, const int64_t *off, const int32_t *len, const BlockDesc *blk,
                      const int32_t *K, const int32_t *npass, int nblk, int maxw, int maxh, float *coef, int32_t *mag,
-                     int8_t *plane, uint8_t *neg, cudaStream_t st) {
+                     int8_t *plane, uint8_t *neg, long long nq, cudaStream_t st) {
     int rc = upload_tables();
     if (rc) return rc;
     if (nblk <= 0) return EBCC_OK;
     if (maxw > 64 || maxh > 64) return EBCC_EINVAL;
     SmemLayout SL = smem_layout(maxw * maxh, maxh, true);
-    t1_decode_kernel<<<grid_for(nblk), WARPS * 32, WARPS * SL.per_warp, st>>>(bytes, off, len, blk, K, npass, nblk,
-                                                                             coef, mag, plane, neg, SL, maxh);
+    PROF("t1_decode_kernel", st, 0.0, t1_decode_kernel<<<grid_for(nblk), WARPS * 32, WARPS * SL.per_warp, st>>>(bytes, off, len, blk, K, npass, nblk,
+                                                                             coef, mag, plane, neg, SL, maxh, nq););
     CK(cudaGetLastError());
     return EBCC_OK;
 }
