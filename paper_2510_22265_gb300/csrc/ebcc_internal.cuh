@@ -111,17 +111,54 @@ struct Hulls {
     int32_t *pt;        // nblk * maxpt   truncation point (passes)
     int32_t *rate;      // nblk * maxpt   bytes at the point
     uint64_t *key;      // nblk * maxpt   slope of the segment ending there (double bits)
+    // all hull segments of the field sorted by slope, highest first, with the
+    // running byte total: built once per field, then every budget is a search
+    uint64_t *skey, *skey2;           // nblk * (maxpt - 1) each
+    uint32_t *sdr, *sdr2;             // nblk * (maxpt - 1) each
+    unsigned long long *cum;          // nblk * (maxpt - 1)
+    int *nseg;                        // device count of segments
 };
 int pcrd_hulls(const int32_t *npass, const int32_t *pass_len, const int64_t *dD, const int64_t *D0, int nblk,
                int maxpass, const Hulls &h, cudaStream_t st);
-// selection threshold for a device-side budget: included = key > thr (or all)
+int pcrd_prepare(const Hulls &h, int nblk, cudaStream_t st);
+// selection for a byte budget: mode 0 = nothing, 1 = every segment with key >= thr
 struct Sel {
     unsigned long long thr;
-    int all;
+    int mode;
     int pad;
 };
 int pcrd_select(const Hulls &h, int nblk, const double *budget_dev, Sel *sel_dev, cudaStream_t st);
 int pcrd_npass(const Hulls &h, int nblk, const Sel *sel_dev, int32_t *npass_out, cudaStream_t st);
+#ifdef __CUDACC__
+// PCRD answer for budget B: whole equal-slope groups, highest slope first,
+// while the running total stays within B (binary searches over the sorted
+// segments; keys descending, cum inclusive)
+__device__ __forceinline__ Sel select_for_budget(const uint64_t *skey, const unsigned long long *cum, int m,
+                                                 double B) {
+    Sel s;
+    s.thr = 0; s.mode = 0; s.pad = 0;
+    int lo = -1, hi = m;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if ((double)cum[mid] <= B) lo = mid; else hi = mid;
+    }
+    int i = lo;
+    if (i < 0) return s;
+    if (i + 1 < m && skey[i + 1] == skey[i]) {  // that group does not fit whole
+        const unsigned long long kk = skey[i];
+        int a = -1, b = i;
+        while (b - a > 1) {
+            int mid = (a + b) >> 1;
+            if (skey[mid] > kk) a = mid; else b = mid;
+        }
+        i = b - 1;
+        if (i < 0) return s;
+    }
+    s.thr = skey[i];
+    s.mode = 1;
+    return s;
+}
+#endif
 
 // ------------------------------------------------------------ pointwise kernels
 int minmax_finite(const float *x, size_t n, double *mm_dev /*[2]*/, int *nonfinite_dev, cudaStream_t st);

@@ -7,13 +7,13 @@
 // (rate, distortion) truncation points, slopes in FP64 from integer distortion
 // and byte counts.  The hull does not depend on r, so it is built once per
 // field.
-// pcrd_select: one CTA per query finds the exact selection for a budget with
-// an MSD radix select over the 64-bit patterns of the (positive) slopes: eight
-// rounds of a rate-weighted 256-bin histogram in shared memory, each round
-// descending into the digit where the running rate crosses the budget.  The
-// result is the first slope group that does not fit; a block keeps the hull
-// points above it.  No sort, and the answer equals taking whole equal-slope
-// groups in descending order while the total stays within the budget.
+// pcrd_prepare: the hull segments of all blocks are compacted, sorted by
+// slope (highest first; a stable one-CTA radix sort on the 64-bit patterns of
+// the positive FP64 slopes) and given a running byte total -- once per field.
+// pcrd_select / select_for_budget: each budget of the ratio search is then
+// answered by binary search: whole equal-slope groups, highest first, while
+// the total stays within the budget; a block keeps its hull points with slope
+// at least the last slope taken.
 #include "ebcc_internal.cuh"
 
 namespace {
@@ -55,50 +55,132 @@ __global__ void hull_kernel(const int32_t *__restrict__ npass, const int32_t *__
     }
 }
 
-constexpr int SEL_T = 512;
+constexpr int ST = 1024;
 
-__global__ void __launch_bounds__(SEL_T) select_kernel(Hulls h, int nblk, const double *budget, Sel *out) {
-    __shared__ unsigned long long hist[256];
-    __shared__ unsigned long long s_prefix, s_mask, s_above;
-    __shared__ int s_all;
-    const double B = *budget;
-    if (threadIdx.x == 0) { s_prefix = 0; s_mask = 0; s_above = 0; s_all = 0; }
-    for (int round = 0; round < 8; round++) {
-        const int shift = 56 - 8 * round;
-        for (int i = threadIdx.x; i < 256; i += SEL_T) hist[i] = 0;
+// compact the hull segments of all blocks: (slope key, byte increment)
+__global__ void __launch_bounds__(ST) seg_build_kernel(Hulls h, int nblk) {
+    __shared__ unsigned int ws[ST / 32];
+    __shared__ unsigned int run;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) run = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nblk; b0 += ST) {
+        const int b = b0 + threadIdx.x;
+        const int cnt = b < nblk ? h.nh[b] - 1 : 0;
+        unsigned int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) ws[wid] = incl;
         __syncthreads();
-        const unsigned long long prefix = s_prefix, mask = s_mask;
-        for (int b = threadIdx.x; b < nblk; b += SEL_T) {
-            const int nh = h.nh[b];
+        unsigned int off = run;
+        for (int k = 0; k < wid; k++) off += ws[k];
+        off += incl - cnt;
+        if (b < nblk) {
             const size_t base = (size_t)b * h.maxpt;
-            int prev = 0;
-            for (int k = 1; k < nh; k++) {
-                const unsigned long long key = h.key[base + k];
-                const int r = h.rate[base + k];
-                if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255], (unsigned long long)(r - prev));
-                prev = r;
+            for (int k = 1; k <= cnt; k++) {
+                if (!INB(off + k - 1, (long long)nblk * (h.maxpt - 1))) break;
+                h.skey[off + k - 1] = h.key[base + k];
+                h.sdr[off + k - 1] = (uint32_t)(h.rate[base + k] - h.rate[base + k - 1]);
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long cum = s_above;
-            int d = 255;
-            while (d >= 0 && (double)(cum + hist[d]) <= B) cum += hist[d--];
-            if (d < 0) {
-                s_all = 1;  // everything fits (only possible in the first round)
-            } else {
-                s_above = cum;
-                s_prefix = prefix | ((unsigned long long)d << shift);
-                s_mask = mask | (255ull << shift);
-            }
+        if (threadIdx.x == 0)
+            for (int k = 0; k < ST / 32; k++) run += ws[k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *h.nseg = (int)run;
+}
+
+// stable LSD radix sort of the segments by key, descending (8 passes of 8
+// bits on the complemented key); one CTA, tiles of 1024 ranked with warp
+// match-any and per-warp digit counts
+__global__ void __launch_bounds__(ST) seg_sort_kernel(Hulls h) {
+    __shared__ unsigned int base[256], tilecnt[256];
+    __shared__ unsigned short wcnt[ST / 32][256];
+    const int m = *h.nseg;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const unsigned int lt = (1u << lane) - 1;
+    uint64_t *ks = h.skey, *kd = h.skey2;
+    uint32_t *vs = h.sdr, *vd = h.sdr2;
+    for (int pass = 0; pass < 8; pass++) {
+        const int shift = 8 * pass;
+        for (int i = tid; i < 256; i += ST) base[i] = 0;
+        __syncthreads();
+        for (int i = tid; i < m; i += ST) atomicAdd(&base[(int)((~ks[i] >> shift) & 255)], 1u);
+        __syncthreads();
+        if (tid == 0) {
+            unsigned int acc = 0;
+            for (int d = 0; d < 256; d++) { unsigned int c = base[d]; base[d] = acc; acc += c; }
         }
         __syncthreads();
-        if (s_all) break;
+        for (int t0 = 0; t0 < m; t0 += ST) {
+            const int i = t0 + tid;
+            const bool valid = i < m;
+            const uint64_t key = valid ? ks[i] : 0;
+            const uint32_t val = valid ? vs[i] : 0;
+            const int d = valid ? (int)((~key >> shift) & 255) : 256 + lane;
+            const unsigned int peers = __match_any_sync(0xffffffffu, d);
+            const int rank = __popc(peers & lt);
+            for (int k = lane; k < 256; k += 32) wcnt[wid][k] = 0;
+            __syncwarp();
+            if (valid && rank == 0) wcnt[wid][d] = (unsigned short)__popc(peers);
+            __syncthreads();
+            if (tid < 256) {
+                unsigned int acc = 0;
+                for (int w = 0; w < ST / 32; w++) {
+                    unsigned int c = wcnt[w][tid];
+                    wcnt[w][tid] = (unsigned short)acc;
+                    acc += c;
+                }
+                tilecnt[tid] = acc;
+            }
+            __syncthreads();
+            if (valid) {
+                const unsigned int pos = base[d] + wcnt[wid][d] + rank;
+                if (INB(pos, m)) { kd[pos] = key; vd[pos] = val; }
+            }
+            __syncthreads();
+            if (tid < 256) base[tid] += tilecnt[tid];
+            __syncthreads();
+        }
+        uint64_t *tk = ks; ks = kd; kd = tk;
+        uint32_t *tv = vs; vs = vd; vd = tv;
     }
-    if (threadIdx.x == 0) {
-        out->thr = s_prefix;
-        out->all = s_all;
+}
+
+// running byte total over the sorted segments (inclusive)
+__global__ void __launch_bounds__(ST) seg_cum_kernel(Hulls h) {
+    __shared__ unsigned long long ws[ST / 32];
+    __shared__ unsigned long long run;
+    const int m = *h.nseg;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) run = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < m; b0 += ST) {
+        const int i = b0 + threadIdx.x;
+        const unsigned long long v = i < m ? h.sdr[i] : 0;
+        unsigned long long incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) ws[wid] = incl;
+        __syncthreads();
+        unsigned long long off = run;
+        for (int k = 0; k < wid; k++) off += ws[k];
+        if (i < m) h.cum[i] = off + incl;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int k = 0; k < ST / 32; k++) run += ws[k];
+        __syncthreads();
     }
+}
+
+__global__ void select_kernel(Hulls h, const double *budget, Sel *out) {
+    if (threadIdx.x || blockIdx.x) return;
+    *out = select_for_budget(h.skey, h.cum, *h.nseg, *budget);
 }
 
 __global__ void npass_kernel(Hulls h, int nblk, const Sel *sel, int32_t *npass_out) {
@@ -107,11 +189,12 @@ __global__ void npass_kernel(Hulls h, int nblk, const Sel *sel, int32_t *npass_o
         const int nh = h.nh[b];
         const size_t base = (size_t)b * h.maxpt;
         int n = 0;
-        for (int k = 1; k < nh; k++) {
-            if (!INB(k, h.maxpt)) break;
-            if (s.all || h.key[base + k] > s.thr) n = h.pt[base + k];
-            else break;
-        }
+        if (s.mode == 1)
+            for (int k = 1; k < nh; k++) {
+                if (!INB(k, h.maxpt)) break;
+                if (h.key[base + k] >= s.thr) n = h.pt[base + k];
+                else break;
+            }
         npass_out[b] = n;
     }
 }
@@ -131,8 +214,17 @@ int pcrd_hulls(const int32_t *npass, const int32_t *pass_len, const int64_t *dD,
     return EBCC_OK;
 }
 
+int pcrd_prepare(const Hulls &h, int nblk, cudaStream_t st) {
+    PROF("seg_build_kernel", st, 0.0, seg_build_kernel<<<1, ST, 0, st>>>(h, nblk));
+    PROF("seg_sort_kernel", st, 0.0, seg_sort_kernel<<<1, ST, 0, st>>>(h));
+    PROF("seg_cum_kernel", st, 0.0, seg_cum_kernel<<<1, ST, 0, st>>>(h));
+    CK(cudaGetLastError());
+    return EBCC_OK;
+}
+
 int pcrd_select(const Hulls &h, int nblk, const double *budget_dev, Sel *sel_dev, cudaStream_t st) {
-    PROF("select_kernel", st, 0.0, select_kernel<<<1, SEL_T, 0, st>>>(h, nblk, budget_dev, sel_dev););
+    (void)nblk;
+    PROF("select_kernel", st, 0.0, select_kernel<<<1, 32, 0, st>>>(h, budget_dev, sel_dev));
     CK(cudaGetLastError());
     return EBCC_OK;
 }

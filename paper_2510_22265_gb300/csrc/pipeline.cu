@@ -58,7 +58,7 @@ __device__ void bl_down(BaseLoop &s) {
 
 // Algorithm 1: bracketing (halve r_low while q_A < q, double r_high while
 // q_A > q) and bisection keeping the last feasible encoding e_f
-__global__ void bl_update(BaseLoop *sp) {
+__global__ void bl_update(BaseLoop *sp, Hulls h) {
     BaseLoop s = *sp;
     if (s.done) return;
     const double qA = (double)s.count / s.N;
@@ -86,6 +86,7 @@ __global__ void bl_update(BaseLoop *sp) {
         bl_bisect(s);
         break;
     }
+    if (!s.done) s.sel_eval = select_for_budget(h.skey, h.cum, *h.nseg, s.budget);  // next evaluation
     *sp = s;
 }
 
@@ -354,6 +355,7 @@ size_t field_bytes(const FieldGeom &g, int cap_per_blk) {
     b += spiht_work_bytes(N);
     b += nb * T1_MAXPASS * (4 + 4 + 4 + 8) + nb * (4 * 4 + 8);
     b += nb * (T1_MAXPASS + 1) * (4 + 4 + 8) + nb * 4;
+    b += nb * T1_MAXPASS * (8 + 8 + 4 + 4 + 8);  // sorted segments
     b += nb * sizeof(BlockDesc) + nb * 4 * 3;
     b += 2 * 4 * 4096 + 4096;  // escapes
     b += 64 * 256;           // small structs and alignment
@@ -395,6 +397,12 @@ void carve_field(Arena &a, const FieldGeom &g, int cap_per_blk, FieldBufs &f) {
     f.hull.pt = carve<int32_t>(a, nb * (T1_MAXPASS + 1));
     f.hull.rate = carve<int32_t>(a, nb * (T1_MAXPASS + 1));
     f.hull.key = carve<uint64_t>(a, nb * (T1_MAXPASS + 1));
+    f.hull.skey = carve<uint64_t>(a, nb * T1_MAXPASS);
+    f.hull.skey2 = carve<uint64_t>(a, nb * T1_MAXPASS);
+    f.hull.sdr = carve<uint32_t>(a, nb * T1_MAXPASS);
+    f.hull.sdr2 = carve<uint32_t>(a, nb * T1_MAXPASS);
+    f.hull.cum = carve<unsigned long long>(a, nb * T1_MAXPASS);
+    f.hull.nseg = carve<int>(a, 4);
     f.blk = carve<BlockDesc>(a, nb);
     f.npass = carve<int32_t>(a, nb);
     f.meta_off = carve<uint32_t>(a, nb);
@@ -459,15 +467,13 @@ int run_base_loop(FieldBufs &f, const FieldGeom &g, double q, int fallback, cons
     CK(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
     InvFinal fin{1, f.bounds, nullptr, &f.bl->count};
-    int rc = EBCC_OK;
-    for (int step = 0; step < 400; step++) {
-        rc = pcrd_select(f.hull, g.nblocks, &f.bl->budget, &f.bl->sel_eval, st);
-        STAGE(st, "select");
-        if (!rc) rc = pcrd_npass(f.hull, g.nblocks, &f.bl->sel_eval, f.npass, st);
+    int rc = pcrd_select(f.hull, g.nblocks, &f.bl->budget, &f.bl->sel_eval, st);  // r0
+    for (int step = 0; step < 400 && !rc; step++) {
+        rc = pcrd_npass(f.hull, g.nblocks, &f.bl->sel_eval, f.npass, st);
         if (!rc) rc = base_recon(f.qt, g, f.t1.K, f.npass, f.W, st);
         if (!rc) rc = dwt_inverse_ex(f.W, nullptr, f.s1, f.s2, g.ny, g.nx, g.L, fin, 0.0, 1.0, st);
         if (rc) break;
-        PROF("bl_update", st, 0.0, bl_update<<<1, 1, 0, st>>>(f.bl););
+        PROF("bl_update", st, 0.0, bl_update<<<1, 1, 0, st>>>(f.bl, f.hull));
         if (ebcc_debug_sync_enabled() && ebcc_stage_check(st, "base eval", __LINE__)) { rc = EBCC_ECUDA; break; }
         if (cudaMemcpyAsync(&hdone[step & 1], &f.bl->done, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaEventRecord(ev[step & 1], st) != cudaSuccess) { rc = EBCC_ECUDA; break; }
@@ -554,6 +560,7 @@ int compress_field(FieldBufs &f, const float *x_dev, int ny, int nx, double boun
     RC(t1_encode_blocks(f.qt, f.blk, g.nblocks, g.cw, g.ch, f.t1, 1, nullptr, (long long)N, st));
     STAGE(st, "tier-1");
     RC(pcrd_hulls(f.t1.npass, f.t1.pass_len, f.t1.dD, f.t1.D0, g.nblocks, T1_MAXPASS, f.hull, st));
+    RC(pcrd_prepare(f.hull, g.nblocks, st));
     STAGE(st, "hulls");
     // ---- base loop with q
     BaseLoop b1;

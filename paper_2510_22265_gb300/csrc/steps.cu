@@ -132,10 +132,17 @@ int ebcc_pcrd_dev(const int32_t *npass, const int32_t *pass_len, const int64_t *
     RC(t.get(&hl.pt, (size_t)(nblk + 1) * hl.maxpt));
     RC(t.get(&hl.rate, (size_t)(nblk + 1) * hl.maxpt));
     RC(t.get(&hl.key, (size_t)(nblk + 1) * hl.maxpt));
+    RC(t.get(&hl.skey, (size_t)(nblk + 1) * T1_MAXPASS));
+    RC(t.get(&hl.skey2, (size_t)(nblk + 1) * T1_MAXPASS));
+    RC(t.get(&hl.sdr, (size_t)(nblk + 1) * T1_MAXPASS));
+    RC(t.get(&hl.sdr2, (size_t)(nblk + 1) * T1_MAXPASS));
+    RC(t.get(&hl.cum, (size_t)(nblk + 1) * T1_MAXPASS));
+    RC(t.get(&hl.nseg, 4));
     RC(t.get(&db, 1));
     RC(t.get(&sel, 1));
     CK(cudaMemcpyAsync(db, &budget, 8, cudaMemcpyHostToDevice, st));
     RC(pcrd_hulls(npass, pass_len, dD, D0, nblk, maxpass, hl, st));
+    RC(pcrd_prepare(hl, nblk, st));
     RC(pcrd_select(hl, nblk, db, sel, st));
     RC(pcrd_npass(hl, nblk, sel, npass_out, st));
     CK(cudaStreamSynchronize(st));
