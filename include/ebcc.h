@@ -195,6 +195,28 @@ int ebcc_server_destroy(ebcc_server *s);
  * to (x - norm_min) / norm_range (Materials and Methods: min-max normalisation). */
 int ebcc_dwt_fwd_dev(const float *in, float *out, size_t ny, size_t nx, int levels,
                      double norm_min, double norm_range, void *stream);
+/* Same forward DWT without any device allocation (the paper has no
+ * counterpart; this is a library-usage variant).  ebcc_dwt_fwd_dev takes its
+ * two scratch regions from cudaMalloc and returns them with cudaFree, which
+ * synchronises the whole device; callers that cannot take that -- a
+ * latency-critical loop sharing the GPU with other streams, or a process whose
+ * device memory is fully committed to its own pools -- call this one instead.
+ * Its scratch is one static device array of EBCC_DWT_STATIC_SCRATCH_FLOATS
+ * floats (8 MiB) per device, owned by the library; the call needs
+ * ceil(ny/2)*ceil(nx/2) + 16 floats (rounded up to 64) plus
+ * ceil(ny/4)*ceil(nx/4) + 16, i.e. fields up to about 6.7 M points
+ * (1441 x 2880 fits), and returns EBCC_ECAPACITY, touching nothing, beyond
+ * that.  Nothing in the scratch has to start at zero.  The first call on a
+ * device looks up the array's address (cudaGetSymbolAddress, with that device
+ * current) and may load the module, so make it before any latency-critical
+ * or captured region.  All calls on one device share the scratch: calls that
+ * can overlap in time (different streams, or threads without ordering) race
+ * on it and must be serialised by the caller.  Asynchronous on `stream`: the
+ * caller synchronises before reading `out`.  Arguments and errors otherwise as
+ * ebcc_dwt_fwd_dev. */
+#define EBCC_DWT_STATIC_SCRATCH_FLOATS (2u * 1024u * 1024u)
+int ebcc_dwt_fwd_static_dev(const float *in, float *out, size_t ny, size_t nx, int levels,
+                            double norm_min, double norm_range, void *stream);
 /* Inverse DWT (Algorithm 1 "IDWT"): in -> out, ny*nx float32. */
 int ebcc_dwt_inv_dev(const float *in, float *out, size_t ny, size_t nx, int levels, void *stream);
 /* Effective number of levels for a shape. */

@@ -17,6 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(HERE, "libebcc_gb300.so")
 
 EBCC_OK = 0
+EBCC_EINVAL, EBCC_ENONFINITE, EBCC_ECORRUPT, EBCC_ENOMEM = -1, -2, -3, -4
+EBCC_EBUDGET, EBCC_ECAPACITY, EBCC_ETIMEOUT, EBCC_ECUDA = -5, -6, -7, -8
 EBCC_BOUND_ABS = 0
 EBCC_BOUND_REL = 1
 ERRORS = {-1: "EINVAL", -2: "ENONFINITE", -3: "ECORRUPT", -4: "ENOMEM", -5: "EBUDGET", -6: "ECAPACITY",
@@ -27,7 +29,7 @@ EXPORTS = [
     "ebcc_params_default", "ebcc_strerror", "ebcc_free", "ebcc_compress", "ebcc_decompress",
     "ebcc_stream_info", "ebcc_compress_batch_dev", "ebcc_decompress_batch_dev", "ebcc_max_stream_bytes",
     "ebcc_server_create", "ebcc_server_submit", "ebcc_server_poll", "ebcc_server_cancel",
-    "ebcc_server_destroy", "ebcc_dwt_fwd_dev", "ebcc_dwt_inv_dev", "ebcc_effective_levels",
+    "ebcc_server_destroy", "ebcc_dwt_fwd_dev", "ebcc_dwt_fwd_static_dev", "ebcc_dwt_inv_dev", "ebcc_effective_levels",
     "ebcc_quantise_dev", "ebcc_band_step", "ebcc_t1_encode_dev", "ebcc_t1_decode_dev", "ebcc_pcrd_dev",
     "ebcc_spiht_encode_dev", "ebcc_spiht_decode_dev", "ebcc_spiht_prefix_recon_dev",
     "ebcc_count_within_dev", "ebcc_profile_enable", "ebcc_profile_reset", "ebcc_profile_count",
@@ -108,6 +110,8 @@ def lib():
                                                 C.c_void_p]
         L.ebcc_dwt_fwd_dev.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_size_t, C.c_int, C.c_double,
                                        C.c_double, C.c_void_p]
+        L.ebcc_dwt_fwd_static_dev.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_size_t, C.c_int,
+                                              C.c_double, C.c_double, C.c_void_p]
         L.ebcc_dwt_inv_dev.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_size_t, C.c_int, C.c_void_p]
         L.ebcc_quantise_dev.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_size_t, C.c_int, C.c_int,
                                         C.c_void_p]
@@ -252,6 +256,14 @@ def ebcc_dwt_fwd_dev(inp, out, levels: int, norm_min: float = 0.0, norm_range: f
     ny, nx = inp.shape
     _check(lib().ebcc_dwt_fwd_dev(_ptr(inp), _ptr(out), ny, nx, levels, norm_min, norm_range,
                                   C.c_void_p(_stream(stream))), "ebcc_dwt_fwd_dev")
+
+
+def ebcc_dwt_fwd_static_dev(inp, out, levels: int, norm_min: float = 0.0, norm_range: float = 0.0, stream=None):
+    """Forward DWT on the library's static device scratch: no allocation per
+    call; asynchronous on `stream`; calls that can overlap must be serialised."""
+    ny, nx = inp.shape
+    _check(lib().ebcc_dwt_fwd_static_dev(_ptr(inp), _ptr(out), ny, nx, levels, norm_min, norm_range,
+                                         C.c_void_p(_stream(stream))), "ebcc_dwt_fwd_static_dev")
 
 
 def ebcc_dwt_inv_dev(inp, out, levels: int, stream=None):
