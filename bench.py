@@ -161,11 +161,26 @@ def run_gpu(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_ms = float(tt.item())
     comp_bytes = sum(r[1] for r in res)
-    # decompression of the produced streams (device-resident)
+    # the plain path: one field per call (every launch covers one field), on a
+    # bounded subset of the same fields
+    n_plain = min(n, args.plain_fields)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for i in range(n_plain):
+        rc, _ = B.ebcc_compress_batch_dev([dfields[i]], [BOUND], outs=[outs[i]], stream=stream.cuda_stream)
+        assert rc == 0, rc
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_bytes = sum(f.numel() * 4 for f in dfields[:n_plain])
+    plain_gbs = plain_bytes / (p0.elapsed_time(p1) / 1e3) / 1e9
+    # decompression of the produced streams (device-resident, one batch)
+    step()
+    torch.cuda.synchronize()
     douts = [torch.empty_like(f) for f in dfields]
     lens = [r[1] for r in res]
     shapes = [tuple(f.shape) for f in dfields]
-    B.ebcc_decompress_batch_dev([r[0] for r in res], lens, shapes, douts)
+    assert B.ebcc_decompress_batch_dev([r[0] for r in res], lens, shapes, douts) == 0
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -207,6 +222,8 @@ def run_gpu(args):
                                f"range-relative bound, device batch API", "fields": n, "raw_bytes": raw_bytes,
                    "l2": "inputs 614.6 MB > 129 MB L2"},
         "decompress_gbs": raw_bytes / (t_dec / 1e3) / 1e9, "cr": raw_bytes / comp_bytes,
+        "plain": {"compress_gbs": plain_gbs, "fields": n_plain,
+                  "what": "same fields, one field per call (every launch covers one field)"},
         "max_err_over_bound": max_err,
         "e2e": {"value": e2e_in / t_e2e / 1e9, "unit": "GB/s", "h2d_bytes_per_step": e2e_in,
                 "d2h_bytes_per_step": e2e_out, "fields": len(hfields)},
@@ -248,6 +265,7 @@ def main():
     ap.add_argument("--shape", type=int, nargs=4, default=[4, 37, 721, 1440],
                     help="variables levels ny nx")
     ap.add_argument("--e2e-fields", type=int, default=16)
+    ap.add_argument("--plain-fields", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

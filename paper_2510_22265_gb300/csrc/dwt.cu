@@ -10,6 +10,7 @@
 // The detail bands go straight to the Mallat array; the LL band goes to a
 // compact scratch buffer that the next level reads, so no level reads data a
 // concurrent tile overwrites.
+#include <string.h>
 #include "ebcc_internal.cuh"
 
 namespace {
@@ -66,14 +67,29 @@ __device__ __forceinline__ void scale(float (*t)[EX + 1], float even_f, float od
     }
 }
 
-// forward level: src (hp x wp, row stride ss) -> detail bands into coef
-// (stride nx) and LL into ll (stride ls); `ll_in_coef` also writes LL to coef.
+__device__ __forceinline__ int ceil_sh(int n, int l) { return (int)(((long long)n + (1LL << l) - 1) >> l); }
+
+// forward level l of the field in grid slot blockIdx.z: the level's input
+// (plane `src` at level 1, else the LL scratch of level l - 1) -> detail bands
+// into W, LL into the scratch of level l (into W at the last level)
 template <bool NORM>
-__global__ void __launch_bounds__(NT) fwd_level(const float *__restrict__ src, int ss, int hp, int wp,
-                                                float *__restrict__ coef, int nx, float *__restrict__ ll,
-                                                int ls, int ll_in_coef, double mn, double inv, long long ncoef) {
-    __shared__ float t[EY][EX + 1];
+__global__ void __launch_bounds__(NT) fwd_level(Live lv, const __grid_constant__ FieldRun one, int l, int src_plane) {
+    int f;
+    const FieldRun *r = pick(lv, one, blockIdx.z, f);
+    if (!r || l > r->L) return;
+    const int nx = r->nx, L = r->L;
+    const int hp = ceil_sh(r->ny, l - 1), wp = ceil_sh(nx, l - 1);
     const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
+    if (ty0 >= hp || tx0 >= wp) return;
+    const float *__restrict__ src = l == 1 ? plane_ptr(*r, src_plane) : (((l - 1) & 1) ? r->s1 : r->s2);
+    const int ss = l == 1 ? nx : wp;
+    const bool last = l == L;
+    float *__restrict__ ll = last ? nullptr : ((l & 1) ? r->s1 : r->s2);
+    float *__restrict__ coef = r->W;
+    const long long ncoef = r->N;
+    const int hl = (hp + 1) >> 1, wl = (wp + 1) >> 1, ls = wl;
+    const double mn = r->mn, inv = r->inv_range;
+    __shared__ float t[EY][EX + 1];
     for (int k = threadIdx.x; k < EY * EX; k += NT) {
         int ly = k / EX, lx = k % EX;
         int gy = reflect(ty0 - HALO + ly, hp), gx = reflect(tx0 - HALO + lx, wp);
@@ -92,41 +108,20 @@ __global__ void __launch_bounds__(NT) fwd_level(const float *__restrict__ src, i
     lift<false>(t, 1, GAMMA, HALO, HALO + TY); __syncthreads();
     lift<false>(t, 0, DELTA, HALO, HALO + TY); __syncthreads();
     scale<false>(t, INV_KAPPA, KAPPA, HALO, HALO + TY); __syncthreads();
-    const int hl = (hp + 1) >> 1, wl = (wp + 1) >> 1;
     constexpr int QH = TY / 2, QW = TX / 2;
     for (int k = threadIdx.x; k < TY * TX; k += NT) {
-        int sub = k / (QH * QW), r = (k / QW) % QH, c = k % QW;
+        int sub = k / (QH * QW), rr = (k / QW) % QH, c = k % QW;
         int pv = sub >> 1, ph = sub & 1;
-        int gy = ty0 + 2 * r + pv, gx = tx0 + 2 * c + ph;
+        int gy = ty0 + 2 * rr + pv, gx = tx0 + 2 * c + ph;
         if (gy >= hp || gx >= wp) continue;
-        float v = t[HALO + 2 * r + pv][HALO + 2 * c + ph];
+        float v = t[HALO + 2 * rr + pv][HALO + 2 * c + ph];
         int oy = (gy >> 1) + (pv ? hl : 0), ox = (gx >> 1) + (ph ? wl : 0);
         if (!pv && !ph) {
-            if (ll && INB((long long)oy * ls + ox, (long long)((hp + 1) >> 1) * ls)) ll[(size_t)oy * ls + ox] = v;
-            if (ll_in_coef && INB((long long)oy * nx + ox, ncoef)) coef[(size_t)oy * nx + ox] = v;
+            if (ll && INB((long long)oy * ls + ox, (long long)hl * ls)) ll[(size_t)oy * ls + ox] = v;
+            if (last && INB((long long)oy * nx + ox, ncoef)) coef[(size_t)oy * nx + ox] = v;
         } else {
             if (INB((long long)oy * nx + ox, ncoef)) coef[(size_t)oy * nx + ox] = v;
         }
-    }
-}
-
-__device__ __forceinline__ void finish_point(const InvFinal &f, float v, size_t gi, float *out,
-                                             size_t oi, unsigned long long &cnt, double mn, double range,
-                                             long long nall) {
-    if (!INB((long long)gi, nall) || !INB((long long)oi, nall)) return;
-    if (f.mode == 0) {
-        if (f.base) v = v + f.base[gi];
-        out[oi] = v;
-    } else if (f.mode == 1) {
-        float2 b = f.bounds[gi];
-        cnt += (v >= b.x && v <= b.y);
-    } else if (f.mode == 2) {
-        float s = f.base[gi] + v;
-        float2 b = f.bounds[gi];
-        cnt += !(s >= b.x && s <= b.y);
-    } else {  // 3: denormalise to original units
-        if (f.base) v = v + f.base[gi];
-        out[oi] = (float)(mn + (double)v * range);
     }
 }
 
@@ -142,15 +137,48 @@ __device__ __forceinline__ void block_count_add(unsigned long long v, unsigned l
     }
 }
 
-// inverse level: LL (stride ls) + detail bands of coef -> level (l-1) region
-// hp x wp written to dst (stride ds) or finished per `fin`.
-__global__ void __launch_bounds__(NT) inv_level(const float *__restrict__ ll, int ls,
-                                                const float *__restrict__ coef, int nx, int hp, int wp,
-                                                float *__restrict__ dst, int ds, InvFinal fin, double mn,
-                                                double range, long long ncoef) {
-    __shared__ float t[EY][EX + 1];
+// the last step of an inverse transform at point gi of field r
+__device__ __forceinline__ void finish_point(const InvFinal &fin, const FieldRun &r, float *dst, float v, long long gi,
+                                             unsigned long long &cnt) {
+    if (!INB(gi, r.N)) return;
+    if (fin.mode <= 0) {
+        if (fin.mode == 0 && fin.add_base) v = v + r.Abase[gi];
+        dst[gi] = v;
+    } else if (fin.mode == 1) {
+        float2 b = r.bounds[gi];
+        cnt += (v >= b.x && v <= b.y);
+    } else if (fin.mode == 2) {
+        float s = r.Abase[gi] + v;
+        float2 b = r.bounds[gi];
+        cnt += !(s >= b.x && s <= b.y);
+    } else {  // 3: denormalise to original units
+        if (fin.add_base) v = v + r.Abase[gi];
+        dst[gi] = (float)(r.mn + (double)v * r.range);
+    }
+}
+
+// inverse level l of the field in grid slot blockIdx.z: LL (the Mallat array
+// at the top level, else the scratch of level l + 1) + detail bands of plane
+// `src` -> the level-(l-1) region: the scratch of level l, or at level 1 the
+// finished output per fin
+__global__ void __launch_bounds__(NT) inv_level(Live lv, const __grid_constant__ FieldRun one, int l, int src_plane,
+                                                InvFinal fin) {
+    int f;
+    const FieldRun *r = pick(lv, one, blockIdx.z, f);
+    if (!r || l > r->L) return;
+    const int nx = r->nx, L = r->L;
+    const int hp = ceil_sh(r->ny, l - 1), wp = ceil_sh(nx, l - 1);
     const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
+    if (ty0 >= hp || tx0 >= wp) return;
+    const float *__restrict__ coef = plane_ptr(*r, src_plane);
+    const float *__restrict__ ll = l == L ? coef : (((l + 1) & 1) ? r->s2 : r->s1);
+    const int ls = l == L ? nx : ceil_sh(nx, l);
+    float *__restrict__ dst = l == 1 ? plane_ptr(*r, fin.dst) : ((l & 1) ? r->s2 : r->s1);
+    const int ds = l == 1 ? nx : wp;
+    const int mode = l == 1 ? fin.mode : -1;
+    const long long ncoef = r->N;
     const int hl = (hp + 1) >> 1, wl = (wp + 1) >> 1;
+    __shared__ float t[EY][EX + 1];
     for (int k = threadIdx.x; k < EY * EX; k += NT) {
         int ly = k / EX, lx = k % EX;
         int gy = reflect(ty0 - HALO + ly, hp), gx = reflect(tx0 - HALO + lx, wp);
@@ -177,95 +205,132 @@ __global__ void __launch_bounds__(NT) inv_level(const float *__restrict__ ll, in
     lift<true>(t, 1, -ALPHA, HALO, HALO + TX); __syncthreads();
     unsigned long long cnt = 0;
     for (int k = threadIdx.x; k < TY * TX; k += NT) {
-        int r = k / TX, c = k % TX;
-        int gy = ty0 + r, gx = tx0 + c;
+        int rr = k / TX, c = k % TX;
+        int gy = ty0 + rr, gx = tx0 + c;
         if (gy >= hp || gx >= wp) continue;
-        float v = t[HALO + r][HALO + c];
-        if (fin.mode < 0) { if (INB((long long)gy * ds + gx, (long long)hp * ds)) dst[(size_t)gy * ds + gx] = v; }
-        else finish_point(fin, v, (size_t)gy * nx + gx, dst, (size_t)gy * ds + gx, cnt, mn, range, ncoef);
+        float v = t[HALO + rr][HALO + c];
+        if (mode < 0) {
+            if (INB((long long)gy * ds + gx, l == 1 ? ncoef : (long long)hp * ds)) dst[(size_t)gy * ds + gx] = v;
+        } else {
+            finish_point(fin, *r, dst, v, (long long)gy * nx + gx, cnt);
+        }
     }
-    if (fin.mode == 1 || fin.mode == 2) block_count_add(cnt, fin.count);
+    if (mode == 1 || mode == 2) block_count_add(cnt, &r->sc->cnt[fin.counter]);
 }
 
-// L == 0: the "transform" is the identity
-__global__ void copy_norm(const float *__restrict__ in, float *__restrict__ out, size_t n, int norm, double mn,
-                          double inv) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        float v = in[i];
-        out[i] = norm ? (float)(((double)v - mn) * inv) : v;
+// fields with no DWT level: the transform is the identity
+__global__ void __launch_bounds__(NT) fwd_identity(Live lv, const __grid_constant__ FieldRun one, int src_plane,
+                                                   int norm) {
+    int f;
+    const FieldRun *r = pick(lv, one, blockIdx.y, f);
+    if (!r || r->L != 0) return;
+    const float *src = plane_ptr(*r, src_plane);
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < r->N; i += (long long)gridDim.x * NT) {
+        float v = src[i];
+        r->W[i] = norm ? (float)(((double)v - r->mn) * r->inv_range) : v;
     }
 }
 
-__global__ void __launch_bounds__(NT) finish_identity(const float *__restrict__ in, float *__restrict__ out, size_t n,
-                                                      InvFinal fin, double mn, double range) {
+__global__ void __launch_bounds__(NT) inv_identity(Live lv, const __grid_constant__ FieldRun one, int src_plane,
+                                                   InvFinal fin) {
+    int f;
+    const FieldRun *r = pick(lv, one, blockIdx.y, f);
+    if (!r || r->L != 0) return;
+    const float *coef = plane_ptr(*r, src_plane);
+    float *dst = plane_ptr(*r, fin.dst);
     unsigned long long cnt = 0;
-    for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT)
-        finish_point(fin, in[i], i, out, i, cnt, mn, range, (long long)n);
-    if (fin.mode == 1 || fin.mode == 2) block_count_add(cnt, fin.count);
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < r->N; i += (long long)gridDim.x * NT)
+        finish_point(fin, *r, dst, coef[i], i, cnt);
+    if (fin.mode == 1 || fin.mode == 2) block_count_add(cnt, &r->sc->cnt[fin.counter]);
+}
+
+unsigned pgrid(long long maxN, int nslots) {
+    long long g = (maxN + NT - 1) / NT;
+    long long cap = 2432 / (nslots > 0 ? nslots : 1);
+    if (cap < 8) cap = 8;
+    return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
 }  // namespace
 
-int dwt_forward(const float *in, float *coef, float *s1, float *s2, int ny, int nx, int L, double mn,
-                double inv, cudaStream_t st) {
-    const int norm = inv > 0;
-    if (L == 0) {
-        size_t n = (size_t)ny * nx;
-        copy_norm<<<(unsigned)((n + 255) / 256 > 4096 ? 4096 : (n + 255) / 256), 256, 0, st>>>(in, coef, n, norm, mn, inv);
-        CK(cudaGetLastError());
-        return EBCC_OK;
+void batch_dims_init(BatchDims &d) { memset(&d, 0, sizeof(d)); }
+
+void batch_dims_add(BatchDims &d, int ny, int nx, int L, int nblk) {
+    if (L > d.maxL) d.maxL = L;
+    if ((long long)ny * nx > d.maxN) d.maxN = (long long)ny * nx;
+    if (nblk > d.maxnblk) d.maxnblk = nblk;
+    for (int l = 0; l <= EBCC_MAX_LEVELS; l++) {
+        int h = (int)(((long long)ny + (1LL << l) - 1) >> l), w = (int)(((long long)nx + (1LL << l) - 1) >> l);
+        if (l <= L) {
+            if (h > d.h[l]) d.h[l] = h;
+            if (w > d.w[l]) d.w[l] = w;
+        }
     }
-    const float *src = in;
-    int ss = nx;
-    for (int l = 1; l <= L; l++) {
-        int hp = (int)(((long)ny + (1L << (l - 1)) - 1) >> (l - 1));
-        int wp = (int)(((long)nx + (1L << (l - 1)) - 1) >> (l - 1));
-        int wl = (wp + 1) >> 1;
-        bool last = l == L;
-        float *ll = last ? nullptr : ((l & 1) ? s1 : s2);
-        dim3 grid((wp + TX - 1) / TX, (hp + TY - 1) / TY);
+    if (L == 0) d.any_L0 = true;
+}
+
+int dwt_forward_b(const Live &lv, const FieldRun &one, int nslots, const BatchDims &d, int src, int norm,
+                  cudaStream_t st) {
+    if (nslots <= 0) return EBCC_OK;
+    if (d.any_L0) {
+        fwd_identity<<<dim3(pgrid(d.maxN, nslots), nslots), NT, 0, st>>>(lv, one, src, norm);
+        CK(cudaGetLastError());
+    }
+    for (int l = 1; l <= d.maxL; l++) {
+        const int hp = d.h[l - 1], wp = d.w[l - 1];
+        dim3 grid((wp + TX - 1) / TX, (hp + TY - 1) / TY, nslots);
+        const double bytes = 8.0 * hp * wp * nslots;
         if (l == 1 && norm)
-            PROF("fwd_level", st, 8.0 * hp * wp, fwd_level<true><<<grid, NT, 0, st>>>(src, ss, hp, wp, coef, nx, ll, wl, last, mn, inv, (long long)ny * nx););
+            PROF("fwd_level", st, bytes, fwd_level<true><<<grid, NT, 0, st>>>(lv, one, l, src));
         else
-            PROF("fwd_level", st, 8.0 * hp * wp, fwd_level<false><<<grid, NT, 0, st>>>(src, ss, hp, wp, coef, nx, ll, wl, last, 0.0, 0.0,
-                                                  (long long)ny * nx););
+            PROF("fwd_level", st, bytes, fwd_level<false><<<grid, NT, 0, st>>>(lv, one, l, src));
         CK(cudaGetLastError());
-        src = ll;
-        ss = wl;
     }
     return EBCC_OK;
 }
 
-// fin.mode: -1 plain store into out; 0 store (+base); 1/2 counts; 3 denormalise
-int dwt_inverse_ex(const float *coef, float *out, float *s1, float *s2, int ny, int nx, int L, InvFinal fin,
-                   double mn, double range, cudaStream_t st) {
-    if (L == 0) {
-        size_t n = (size_t)ny * nx;
-        unsigned g = (unsigned)((n + NT - 1) / NT > 4096 ? 4096 : (n + NT - 1) / NT);
-        if (fin.mode < 0) { fin.mode = 0; fin.base = nullptr; }
-        finish_identity<<<g, NT, 0, st>>>(coef, out, n, fin, mn, range);
+int dwt_inverse_b(const Live &lv, const FieldRun &one, int nslots, const BatchDims &d, int src, InvFinal fin,
+                  cudaStream_t st) {
+    if (nslots <= 0) return EBCC_OK;
+    if (d.any_L0) {
+        inv_identity<<<dim3(pgrid(d.maxN, nslots), nslots), NT, 0, st>>>(lv, one, src, fin);
         CK(cudaGetLastError());
-        return EBCC_OK;
     }
-    const float *ll = coef;
-    int ls = nx;
-    for (int l = L; l >= 1; l--) {
-        int hp = (int)(((long)ny + (1L << (l - 1)) - 1) >> (l - 1));
-        int wp = (int)(((long)nx + (1L << (l - 1)) - 1) >> (l - 1));
-        float *dst = (l == 1) ? out : ((l & 1) ? s2 : s1);
-        int ds = (l == 1) ? nx : wp;
-        InvFinal f = fin;
-        if (l > 1) f.mode = -1;
-        dim3 grid((wp + TX - 1) / TX, (hp + TY - 1) / TY);
-        PROF("inv_level", st, (4.0 + (f.mode == 1 ? 8.0 : f.mode == 2 ? 12.0 : (f.base ? 8.0 : 4.0))) * hp * wp, inv_level<<<grid, NT, 0, st>>>(ll, ls, coef, nx, hp, wp, dst, ds, f, mn, range, (long long)ny * nx););
+    for (int l = d.maxL; l >= 1; l--) {
+        const int hp = d.h[l - 1], wp = d.w[l - 1];
+        dim3 grid((wp + TX - 1) / TX, (hp + TY - 1) / TY, nslots);
+        // algorithmic bytes: read the level's coefficients, then write the
+        // region (levels > 1) or finish it (read bounds / base as needed)
+        double per = 4.0;
+        if (l > 1) per += 4.0;
+        else if (fin.mode == 1) per += 8.0;
+        else if (fin.mode == 2) per += 12.0;
+        else per += fin.add_base ? 8.0 : 4.0;
+        PROF("inv_level", st, per * hp * wp * nslots, inv_level<<<grid, NT, 0, st>>>(lv, one, l, src, fin));
         CK(cudaGetLastError());
-        ll = dst;
-        ls = wp;
     }
     return EBCC_OK;
 }
 
-int dwt_inverse(const float *coef, float *out, float *s1, float *s2, int ny, int nx, int L, InvFinal fin,
+int dwt_forward(const float *in, float *coef, float *s1, float *s2, int ny, int nx, int L, double mn, double inv,
                 cudaStream_t st) {
-    return dwt_inverse_ex(coef, out, s1, s2, ny, nx, L, fin, 0.0, 1.0, st);
+    FieldRun one;
+    memset(&one, 0, sizeof(one));
+    one.ny = ny; one.nx = nx; one.L = L; one.N = (long long)ny * nx;
+    one.x = in; one.W = coef; one.s1 = s1; one.s2 = s2; one.mn = mn; one.inv_range = inv;
+    BatchDims d;
+    batch_dims_init(d);
+    batch_dims_add(d, ny, nx, L, 0);
+    return dwt_forward_b(Live{nullptr, nullptr, nullptr}, one, 1, d, PL_X, inv > 0, st);
+}
+
+int dwt_inverse_plain(const float *coef, float *out, float *s1, float *s2, int ny, int nx, int L, cudaStream_t st) {
+    FieldRun one;
+    memset(&one, 0, sizeof(one));
+    one.ny = ny; one.nx = nx; one.L = L; one.N = (long long)ny * nx;
+    one.W = const_cast<float *>(coef); one.dst = out; one.s1 = s1; one.s2 = s2;
+    BatchDims d;
+    batch_dims_init(d);
+    batch_dims_add(d, ny, nx, L, 0);
+    return dwt_inverse_b(Live{nullptr, nullptr, nullptr}, one, 1, d, PL_W, InvFinal{-1, 0, PL_DST, 0}, st);
 }

@@ -62,29 +62,139 @@ struct Arena {
     int dev = -1;
 };
 int arena_reserve(Arena &a, size_t bytes);
-// whole-field compression / decompression on a caller-held arena (server)
+
+// A compression / decompression engine: its device workspace and pinned
+// staging persist across calls; one caller at a time.
+struct EbccEngine;
+EbccEngine *engine_create();
+void engine_destroy(EbccEngine *e);
+// Algorithm 1 on n device fields, batched (split only where the workspace
+// would exceed the device budget); per-field status in od[i].status
+int engine_compress(EbccEngine *e, const ebcc_field_desc *fd, int n, ebcc_out_desc *od, const ebcc_params &p,
+                    cudaStream_t st);
+int engine_decompress(EbccEngine *e, const ebcc_stream_desc *sd, int n, float *const *outs, int *status,
+                      cudaStream_t st);
+// device workspace of one field in a compression batch
 size_t ebcc_compress_footprint(size_t ny, size_t nx, const ebcc_params &p);
-int ebcc_compress_arena(Arena &a, const float *x_dev, size_t ny, size_t nx, double bound, int kind,
-                        const ebcc_params &p, uint8_t *out_dev, size_t cap, size_t *len, ebcc_stats *stats,
-                        cudaStream_t st);
-int ebcc_decompress_arena(Arena &a, const uint8_t *s_dev, const uint8_t *s_host, size_t len, size_t ny, size_t nx,
-                          float *out_dev, cudaStream_t st);
+
+// ------------------------------------------------------------ batches
+// Per-field device scalars (results and counters of the pipeline steps).
+struct FieldScal {
+    double mm[2];                  // min, max of the finite values
+    uint32_t mmkey[2];             // order-preserving keys of min / max
+    int nonfinite;                 // 1 if a NaN / Inf was seen
+    int spiht_status;              // bit 0: SPIHT stream capacity exceeded
+    int nmax;                      // SPIHT top bit-plane (-1: all zero)
+    int es;                        // SPIHT step exponent of the current attempt
+    int nseg;                      // PCRD hull segments of the field
+    int ok;                        // decoder consistency flag
+    long long nbits;               // SPIHT stream length in bits
+    long long T;                   // truncation (bits) under evaluation
+    unsigned long long cnt[2];     // counters of the base loop and the truncation loop
+    unsigned long long nesc;       // escaped points
+    unsigned long long tot[2];     // base section: metadata bytes, payload bytes
+    long long refine_start[32];    // SPIHT: bit offset of each plane's refinement pass
+};
+
+struct SpihtWork {  // per-field device lists and maxima
+    uint32_t *maxd, *maxl;      // N each
+    uint32_t *lip, *lsp;        // N each
+    uint32_t *lis_a, *lis_b;    // 2N each (idx << 1 | type)
+    uint32_t *tmp;              // 2N
+};
+
+// One field of a batch as the kernels see it.  All pointers are device
+// pointers; the point planes hold ny * nx values in row-major order.
+struct FieldRun {
+    int ny, nx, L, nblk;           // shape, effective DWT levels, code-blocks
+    int blk0, pad0;                // first code-block of the field in the batch-wide block arrays
+    long long N;                   // ny * nx
+    double mn, range, inv_range;   // min-max normalisation
+    double E;                      // half-width of the acceptance test (eps_abs - guard), original units
+    const float *x;                // input field (original units)
+    float *W, *Abase, *R, *dst;    // coefficient / reconstruction planes; dst = caller's output
+    float2 *bounds;                // per-point acceptance interval of the normalised value
+    int32_t *qt, *s;               // base-layer quantised Mallat array; SPIHT integers
+    uint32_t *sig_pos, *lsp_idx;   // SPIHT trace
+    int8_t *plane8;                // decoder: lowest decoded plane per point
+    uint8_t *neg8;                 // decoder: sign per point
+    float *s1, *s2;                // DWT scratch (LL bands of odd / even levels)
+    const FieldGeom *geom;
+    SpihtWork sw;
+    uint8_t *sp;                   // SPIHT stream, sp_cap bytes (multiple of 4)
+    long long sp_cap;
+    uint32_t *esc;                 // escapes: (index, float bits) pairs, esc_cap of them
+    long long esc_cap;
+    uint8_t *out;                  // compressed stream of the field, out_cap bytes
+    long long out_cap;
+    const uint8_t *in;             // decoder: the stream, in_len bytes
+    long long in_len;
+    long long base_len, res_len, n_esc;  // decoder: section sizes from the header
+    FieldScal *sc;
+};
+
+// Which fields a launch covers: grid slot k serves table entry idx[k] while
+// k < *n.  A launch on a single field passes it by value (tab == nullptr;
+// slot 0 only).
+struct Live {
+    const FieldRun *tab;
+    const int *idx;
+    const int *n;
+};
+
+enum { PL_X = 0, PL_W = 1, PL_ABASE = 2, PL_R = 3, PL_DST = 4 };
+
+#ifdef __CUDACC__
+__device__ __forceinline__ const FieldRun *pick(const Live &lv, const FieldRun &one, int slot, int &f) {
+    if (!lv.tab) {
+        f = 0;
+        return slot == 0 ? &one : nullptr;
+    }
+    if (slot >= *lv.n) return nullptr;
+    f = lv.idx[slot];
+    return lv.tab + f;
+}
+__device__ __forceinline__ float *plane_ptr(const FieldRun &r, int p) {
+    switch (p) {
+    case PL_X: return const_cast<float *>(r.x);
+    case PL_W: return r.W;
+    case PL_ABASE: return r.Abase;
+    case PL_R: return r.R;
+    default: return r.dst;
+    }
+}
+#endif
+
+// largest per-level extents over the fields of a batch (grid sizes)
+struct BatchDims {
+    int maxL;
+    long long maxN;
+    int maxnblk;
+    int h[EBCC_MAX_LEVELS + 1], w[EBCC_MAX_LEVELS + 1];
+    bool any_L0;
+};
+void batch_dims_add(BatchDims &d, int ny, int nx, int L, int nblk);
+void batch_dims_init(BatchDims &d);
 
 // ------------------------------------------------------------ DWT
 struct InvFinal {
-    // -1: store into out; 0: store (+ base if set); 1: count points with the
-    // value inside bounds[i]; 2: count points with base + value outside
-    // bounds[i]; 3: store mn + (value (+ base)) * range (original units)
-    int mode;
-    const float2 *bounds;
-    const float *base;
-    unsigned long long *count;
+    // -1: store into plane `dst`; 0: store (+ Abase if add_base) into `dst`;
+    // 1: count points whose value lies inside bounds[i]; 2: count points with
+    // Abase + value outside bounds[i]; 3: store mn + (value (+ Abase)) * range
+    // (original units) into `dst`.  Counts add to sc->cnt[counter].
+    int mode, add_base, dst, counter;
 };
-// scratch s1 >= ceil(ny/2)*ceil(nx/2) floats, s2 >= ceil(ny/4)*ceil(nx/4)
+// forward: plane `src` (PL_X with normalisation when norm, or PL_R) -> W
+int dwt_forward_b(const Live &lv, const FieldRun &one, int nslots, const BatchDims &d, int src, int norm,
+                  cudaStream_t st);
+// inverse: plane `src` (W or R), finished per fin
+int dwt_inverse_b(const Live &lv, const FieldRun &one, int nslots, const BatchDims &d, int src, InvFinal fin,
+                  cudaStream_t st);
+// single-field forms on plain pointers (scratch s1 >= ceil(ny/2)*ceil(nx/2)+16
+// floats, s2 >= ceil(ny/4)*ceil(nx/4)+16)
 int dwt_forward(const float *in, float *coef, float *s1, float *s2, int ny, int nx, int L, double norm_min,
                 double norm_inv_range, cudaStream_t st);
-int dwt_inverse_ex(const float *coef, float *out, float *s1, float *s2, int ny, int nx, int L, InvFinal fin,
-                   double mn, double range, cudaStream_t st);
+int dwt_inverse_plain(const float *coef, float *out, float *s1, float *s2, int ny, int nx, int L, cudaStream_t st);
 
 // ------------------------------------------------------------ tier-1
 struct T1Out {
@@ -105,30 +215,36 @@ int t1_decode_blocks(const uint8_t *bytes, const int64_t *off, const int32_t *le
                      int32_t *mag, int8_t *plane, uint8_t *neg, long long nq, cudaStream_t st);
 
 // ------------------------------------------------------------ PCRD
+// Batch-wide arrays, indexed by global code-block (hull points) or by
+// blk * T1_MAXPASS + k (a field's sorted segments start at blk0 * T1_MAXPASS).
 struct Hulls {
     int maxpt;          // T1_MAXPASS + 1
     int32_t *nh;        // nblk
     int32_t *pt;        // nblk * maxpt   truncation point (passes)
     int32_t *rate;      // nblk * maxpt   bytes at the point
     uint64_t *key;      // nblk * maxpt   slope of the segment ending there (double bits)
-    // all hull segments of the field sorted by slope, highest first, with the
+    // all hull segments of a field sorted by slope, highest first, with the
     // running byte total: built once per field, then every budget is a search
     uint64_t *skey, *skey2;           // nblk * (maxpt - 1) each
     uint32_t *sdr, *sdr2;             // nblk * (maxpt - 1) each
     unsigned long long *cum;          // nblk * (maxpt - 1)
-    int *nseg;                        // device count of segments
 };
 int pcrd_hulls(const int32_t *npass, const int32_t *pass_len, const int64_t *dD, const int64_t *D0, int nblk,
                int maxpass, const Hulls &h, cudaStream_t st);
-int pcrd_prepare(const Hulls &h, int nblk, cudaStream_t st);
+// sorted segments of each field (sc->nseg); one CTA per field
+int pcrd_prepare_b(const Live &lv, const FieldRun &one, int nslots, const Hulls &h, cudaStream_t st);
 // selection for a byte budget: mode 0 = nothing, 1 = every segment with key >= thr
 struct Sel {
     unsigned long long thr;
     int mode;
     int pad;
 };
-int pcrd_select(const Hulls &h, int nblk, const double *budget_dev, Sel *sel_dev, cudaStream_t st);
-int pcrd_npass(const Hulls &h, int nblk, const Sel *sel_dev, int32_t *npass_out, cudaStream_t st);
+// passes kept per code-block for the selection of each field; the selection
+// of table entry f is at (const char *)sel + f * sel_stride
+int pcrd_npass_b(const Live &lv, const FieldRun &one, int nslots, int maxnblk, const Hulls &h, const void *sel,
+                 size_t sel_stride, int32_t *npass_out, cudaStream_t st);
+// single field (blocks 0..nblk-1): selection for a device budget
+int pcrd_select(const Hulls &h, const int *nseg_dev, const double *budget_dev, Sel *sel_dev, cudaStream_t st);
 #ifdef __CUDACC__
 // PCRD answer for budget B: whole equal-slope groups, highest slope first,
 // while the running total stays within B (binary searches over the sorted
@@ -161,33 +277,30 @@ __device__ __forceinline__ Sel select_for_budget(const uint64_t *skey, const uns
 #endif
 
 // ------------------------------------------------------------ pointwise kernels
-int minmax_finite(const float *x, size_t n, double *mm_dev /*[2]*/, int *nonfinite_dev, cudaStream_t st);
-int quantise_base(const float *coef, int32_t *qt, const FieldGeom &g, int sign_magnitude, cudaStream_t st);
-int base_recon(const int32_t *qt, const FieldGeom &g, const int32_t *K, const int32_t *npass, float *coef,
-               cudaStream_t st);
-int make_bounds(const float *x, size_t n, double mn, double range, double eps_abs, double guard, float2 *bounds,
-                cudaStream_t st);
-int residue(const float *x, const float *abase, size_t n, double mn, double inv_range, float *res,
-            cudaStream_t st);
-int spiht_quantise(const float *w, size_t n, int step_exp, int32_t *s, cudaStream_t st);
-int spiht_prefix_recon(const int32_t *s, const uint32_t *sig_pos, const uint32_t *lsp_idx, const int64_t *refine_start,
-                       const int64_t *nbits_dev, int64_t nbits_host, size_t n, int step_exp, float *out,
-                       cudaStream_t st);
+// min / max of the finite values and the non-finite flag -> sc
+int minmax_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, cudaStream_t st);
+int quantise_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, int sign_magnitude, cudaStream_t st);
+// W = base reconstruction for npass (batch-wide per-block arrays K, npass)
+int base_recon_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, const int32_t *K,
+                 const int32_t *npass, cudaStream_t st);
+int make_bounds_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, cudaStream_t st);
+// R = (x - mn) / range - Abase in FP64, rounded to float
+int residue_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, cudaStream_t st);
+// s = SPIHT integers of W with step 2^sc->es
+int spiht_quantise_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, cudaStream_t st);
+// R = coefficients a decoder gets from the first T bits (T = sc->T when
+// use_T, else the whole stream sc->nbits)
+int spiht_prefix_recon_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, int use_T,
+                         cudaStream_t st);
 
 // ------------------------------------------------------------ SPIHT
-struct SpihtWork {  // per-field device lists and maxima
-    uint32_t *maxd, *maxl;      // N each
-    uint32_t *lip, *lsp;        // N each
-    uint32_t *lis_a, *lis_b;    // 2N each (idx << 1 | type)
-    uint32_t *tmp;              // 2N
-};
 size_t spiht_work_bytes(size_t n);
 void spiht_work_carve(uint8_t *base, size_t n, SpihtWork *w);
-int spiht_encode(const int32_t *s, int ny, int nx, int L, uint8_t *out, size_t cap_bytes, int64_t *nbits_dev,
-                 int32_t *nmax_dev, uint32_t *sig_pos, uint32_t *lsp_idx, int64_t *refine_start, int32_t *status_dev,
-                 const SpihtWork &w, cudaStream_t st);
-int spiht_decode(const uint8_t *in, int64_t nbits, int ny, int nx, int L, int nmax, int32_t *mag, int8_t *plane,
-                 uint8_t *neg, float *coef_out, int step_exp, const SpihtWork &w, cudaStream_t st);
+// encode s -> sp (sc->nbits, nmax, spiht_status, refine_start; sig_pos, lsp_idx)
+int spiht_encode_b(const Live &lv, const FieldRun &one, int nslots, const BatchDims &d, cudaStream_t st);
+// decode in[HDR + base_len ..] (res_len bytes) with sc->nmax, sc->es -> R
+// (coef) when to_coef, else mag (qt) / plane8 / neg8
+int spiht_decode_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, int to_coef, cudaStream_t st);
 
 // ------------------------------------------------------------ diagnostics
 // Every guarded access checks its index; an index out of range is reported

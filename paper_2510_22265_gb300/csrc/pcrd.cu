@@ -57,16 +57,23 @@ __global__ void hull_kernel(const int32_t *__restrict__ npass, const int32_t *__
 
 constexpr int ST = 1024;
 
-// compact the hull segments of all blocks: (slope key, byte increment)
-__global__ void __launch_bounds__(ST) seg_build_kernel(Hulls h, int nblk) {
+// compact the hull segments of the field's blocks: (slope key, byte increment)
+__global__ void __launch_bounds__(ST) seg_build_kernel(Live lv, const __grid_constant__ FieldRun one, Hulls h) {
+    int f;
+    const FieldRun *r = pick(lv, one, blockIdx.x, f);
+    if (!r) return;
     __shared__ unsigned int ws[ST / 32];
     __shared__ unsigned int run;
+    const int nblk = r->nblk, blk0 = r->blk0;
+    const long long sbase = (long long)blk0 * T1_MAXPASS;
+    uint64_t *skey = h.skey + sbase;
+    uint32_t *sdr = h.sdr + sbase;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (threadIdx.x == 0) run = 0;
     __syncthreads();
     for (int b0 = 0; b0 < nblk; b0 += ST) {
         const int b = b0 + threadIdx.x;
-        const int cnt = b < nblk ? h.nh[b] - 1 : 0;
+        const int cnt = b < nblk ? h.nh[blk0 + b] - 1 : 0;
         unsigned int incl = cnt;
         for (int o = 1; o < 32; o <<= 1) {
             unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
@@ -78,11 +85,11 @@ __global__ void __launch_bounds__(ST) seg_build_kernel(Hulls h, int nblk) {
         for (int k = 0; k < wid; k++) off += ws[k];
         off += incl - cnt;
         if (b < nblk) {
-            const size_t base = (size_t)b * h.maxpt;
+            const size_t base = (size_t)(blk0 + b) * h.maxpt;
             for (int k = 1; k <= cnt; k++) {
                 if (!INB(off + k - 1, (long long)nblk * (h.maxpt - 1))) break;
-                h.skey[off + k - 1] = h.key[base + k];
-                h.sdr[off + k - 1] = (uint32_t)(h.rate[base + k] - h.rate[base + k - 1]);
+                skey[off + k - 1] = h.key[base + k];
+                sdr[off + k - 1] = (uint32_t)(h.rate[base + k] - h.rate[base + k - 1]);
             }
         }
         __syncthreads();
@@ -90,20 +97,24 @@ __global__ void __launch_bounds__(ST) seg_build_kernel(Hulls h, int nblk) {
             for (int k = 0; k < ST / 32; k++) run += ws[k];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *h.nseg = (int)run;
+    if (threadIdx.x == 0) r->sc->nseg = (int)run;
 }
 
-// stable LSD radix sort of the segments by key, descending (8 passes of 8
-// bits on the complemented key); one CTA, tiles of 1024 ranked with warp
+// stable LSD radix sort of the field's segments by key, descending (8 passes
+// of 8 bits on the complemented key); one CTA, tiles of 1024 ranked with warp
 // match-any and per-warp digit counts
-__global__ void __launch_bounds__(ST) seg_sort_kernel(Hulls h) {
+__global__ void __launch_bounds__(ST) seg_sort_kernel(Live lv, const __grid_constant__ FieldRun one, Hulls h) {
+    int f;
+    const FieldRun *r = pick(lv, one, blockIdx.x, f);
+    if (!r) return;
     __shared__ unsigned int base[256], tilecnt[256];
     __shared__ unsigned short wcnt[ST / 32][256];
-    const int m = *h.nseg;
+    const int m = r->sc->nseg;
+    const long long sbase = (long long)r->blk0 * T1_MAXPASS;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const unsigned int lt = (1u << lane) - 1;
-    uint64_t *ks = h.skey, *kd = h.skey2;
-    uint32_t *vs = h.sdr, *vd = h.sdr2;
+    uint64_t *ks = h.skey + sbase, *kd = h.skey2 + sbase;
+    uint32_t *vs = h.sdr + sbase, *vd = h.sdr2 + sbase;
     for (int pass = 0; pass < 8; pass++) {
         const int shift = 8 * pass;
         for (int i = tid; i < 256; i += ST) base[i] = 0;
@@ -151,16 +162,22 @@ __global__ void __launch_bounds__(ST) seg_sort_kernel(Hulls h) {
 }
 
 // running byte total over the sorted segments (inclusive)
-__global__ void __launch_bounds__(ST) seg_cum_kernel(Hulls h) {
+__global__ void __launch_bounds__(ST) seg_cum_kernel(Live lv, const __grid_constant__ FieldRun one, Hulls h) {
+    int f;
+    const FieldRun *r = pick(lv, one, blockIdx.x, f);
+    if (!r) return;
     __shared__ unsigned long long ws[ST / 32];
     __shared__ unsigned long long run;
-    const int m = *h.nseg;
+    const int m = r->sc->nseg;
+    const long long sbase = (long long)r->blk0 * T1_MAXPASS;
+    const uint32_t *sdr = h.sdr + sbase;
+    unsigned long long *cum = h.cum + sbase;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (threadIdx.x == 0) run = 0;
     __syncthreads();
     for (int b0 = 0; b0 < m; b0 += ST) {
         const int i = b0 + threadIdx.x;
-        const unsigned long long v = i < m ? h.sdr[i] : 0;
+        const unsigned long long v = i < m ? sdr[i] : 0;
         unsigned long long incl = v;
         for (int o = 1; o < 32; o <<= 1) {
             unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
@@ -170,7 +187,7 @@ __global__ void __launch_bounds__(ST) seg_cum_kernel(Hulls h) {
         __syncthreads();
         unsigned long long off = run;
         for (int k = 0; k < wid; k++) off += ws[k];
-        if (i < m) h.cum[i] = off + incl;
+        if (i < m) cum[i] = off + incl;
         __syncthreads();
         if (threadIdx.x == 0)
             for (int k = 0; k < ST / 32; k++) run += ws[k];
@@ -178,25 +195,30 @@ __global__ void __launch_bounds__(ST) seg_cum_kernel(Hulls h) {
     }
 }
 
-__global__ void select_kernel(Hulls h, const double *budget, Sel *out) {
+__global__ void select_kernel(Hulls h, const int *nseg, const double *budget, Sel *out) {
     if (threadIdx.x || blockIdx.x) return;
-    *out = select_for_budget(h.skey, h.cum, *h.nseg, *budget);
+    *out = select_for_budget(h.skey, h.cum, *nseg, *budget);
 }
 
-__global__ void npass_kernel(Hulls h, int nblk, const Sel *sel, int32_t *npass_out) {
-    const Sel s = *sel;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
-        const int nh = h.nh[b];
-        const size_t base = (size_t)b * h.maxpt;
-        int n = 0;
-        if (s.mode == 1)
-            for (int k = 1; k < nh; k++) {
-                if (!INB(k, h.maxpt)) break;
-                if (h.key[base + k] >= s.thr) n = h.pt[base + k];
-                else break;
-            }
-        npass_out[b] = n;
-    }
+__global__ void npass_kernel(Live lv, const __grid_constant__ FieldRun one, Hulls h, const char *sel_base,
+                             size_t sel_stride, int32_t *npass_out) {
+    int f;
+    const FieldRun *r = pick(lv, one, blockIdx.y, f);
+    if (!r) return;
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= r->nblk) return;
+    const Sel s = *(const Sel *)(sel_base + (size_t)f * sel_stride);
+    const int gb = r->blk0 + b;
+    const int nh = h.nh[gb];
+    const size_t base = (size_t)gb * h.maxpt;
+    int n = 0;
+    if (s.mode == 1)
+        for (int k = 1; k < nh; k++) {
+            if (!INB(k, h.maxpt)) break;
+            if (h.key[base + k] >= s.thr) n = h.pt[base + k];
+            else break;
+        }
+    npass_out[gb] = n;
 }
 
 unsigned grid1(int n, int t) {
@@ -214,24 +236,26 @@ int pcrd_hulls(const int32_t *npass, const int32_t *pass_len, const int64_t *dD,
     return EBCC_OK;
 }
 
-int pcrd_prepare(const Hulls &h, int nblk, cudaStream_t st) {
-    PROF("seg_build_kernel", st, 0.0, seg_build_kernel<<<1, ST, 0, st>>>(h, nblk));
-    PROF("seg_sort_kernel", st, 0.0, seg_sort_kernel<<<1, ST, 0, st>>>(h));
-    PROF("seg_cum_kernel", st, 0.0, seg_cum_kernel<<<1, ST, 0, st>>>(h));
+int pcrd_prepare_b(const Live &lv, const FieldRun &one, int nslots, const Hulls &h, cudaStream_t st) {
+    if (nslots <= 0) return EBCC_OK;
+    PROF("seg_build_kernel", st, 0.0, seg_build_kernel<<<nslots, ST, 0, st>>>(lv, one, h));
+    PROF("seg_sort_kernel", st, 0.0, seg_sort_kernel<<<nslots, ST, 0, st>>>(lv, one, h));
+    PROF("seg_cum_kernel", st, 0.0, seg_cum_kernel<<<nslots, ST, 0, st>>>(lv, one, h));
     CK(cudaGetLastError());
     return EBCC_OK;
 }
 
-int pcrd_select(const Hulls &h, int nblk, const double *budget_dev, Sel *sel_dev, cudaStream_t st) {
-    (void)nblk;
-    PROF("select_kernel", st, 0.0, select_kernel<<<1, 32, 0, st>>>(h, budget_dev, sel_dev));
+int pcrd_select(const Hulls &h, const int *nseg_dev, const double *budget_dev, Sel *sel_dev, cudaStream_t st) {
+    PROF("select_kernel", st, 0.0, select_kernel<<<1, 32, 0, st>>>(h, nseg_dev, budget_dev, sel_dev));
     CK(cudaGetLastError());
     return EBCC_OK;
 }
 
-int pcrd_npass(const Hulls &h, int nblk, const Sel *sel_dev, int32_t *npass_out, cudaStream_t st) {
-    if (nblk <= 0) return EBCC_OK;
-    PROF("npass_kernel", st, 0.0, npass_kernel<<<grid1(nblk, 128), 128, 0, st>>>(h, nblk, sel_dev, npass_out););
+int pcrd_npass_b(const Live &lv, const FieldRun &one, int nslots, int maxnblk, const Hulls &h, const void *sel,
+                 size_t sel_stride, int32_t *npass_out, cudaStream_t st) {
+    if (nslots <= 0 || maxnblk <= 0) return EBCC_OK;
+    dim3 grid((maxnblk + 127) / 128, nslots);
+    PROF("npass_kernel", st, 0.0, npass_kernel<<<grid, 128, 0, st>>>(lv, one, h, (const char *)sel, sel_stride, npass_out));
     CK(cudaGetLastError());
     return EBCC_OK;
 }

@@ -1,18 +1,24 @@
-// Algorithm 1 (EBCC compression process) and the decompressor on GB300.
+// Algorithm 1 (EBCC compression process) and the decompressor on GB300, run
+// on a batch of fields at once.
 //
-// Everything per point runs in this library's kernels; the host only orders
-// launches.  The two feedback loops of Algorithm 1 are device-side state
-// machines: after each evaluation (PCRD selection for the current ratio, base
-// reconstruction from the tier-1 trace, inverse DWT with the bound test fused
-// into its last level) a one-thread kernel advances the bracketing / bisection
-// exactly as printed and sets up the next evaluation.  The host launches
-// evaluations and reads the loop's done flag one evaluation behind, so the GPU
-// never waits on the host inside a loop.
+// Every step is one launch over all fields of the batch that take part in it
+// (grid slot -> field through a device list).  The two feedback loops of
+// Algorithm 1 are device-side state machines, one per field: after each
+// evaluation (PCRD selection for the current ratio, base reconstruction from
+// the tier-1 trace, inverse DWT with the bound test fused into its last level)
+// a one-CTA kernel advances every live field's bracketing / bisection exactly
+// as Algorithm 1 prints it, sets up its next evaluation, and compacts the list
+// of fields still iterating.  The host only launches: it learns the live count
+// one evaluation late (a pinned copy), so the GPU never waits on the host
+// inside a loop, and the grids shrink as fields finish.  A batch of one field
+// is the plain path.
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#include <algorithm>
 #include <mutex>
+#include <new>
 #include <vector>
 #include "ebcc_internal.cuh"
 
@@ -24,7 +30,6 @@ struct BaseLoop {
     int fallback, phase, iters, done;
     double r_low, r_high, r_mid, qA0, q_last, r_last, r_f, q_f, budget;
     Sel sel_eval, sel_A, sel_f;
-    unsigned long long count;
 };
 
 __device__ void bl_eval(BaseLoop &s, double r, int ph) {
@@ -58,12 +63,8 @@ __device__ void bl_down(BaseLoop &s) {
 
 // Algorithm 1: bracketing (halve r_low while q_A < q, double r_high while
 // q_A > q) and bisection keeping the last feasible encoding e_f
-__global__ void bl_update(BaseLoop *sp, Hulls h) {
-    BaseLoop s = *sp;
-    if (s.done) return;
-    const double qA = (double)s.count / s.N;
+__device__ void bl_step(BaseLoop &s, double qA) {
     s.iters++;
-    s.count = 0;
     switch (s.phase) {
     case 0:
         s.qA0 = qA; s.r_low = s.r0; s.r_high = s.r0;
@@ -86,14 +87,81 @@ __global__ void bl_update(BaseLoop *sp, Hulls h) {
         bl_bisect(s);
         break;
     }
-    if (!s.done) s.sel_eval = select_for_budget(h.skey, h.cum, *h.nseg, s.budget);  // next evaluation
-    *sp = s;
+}
+
+__device__ __forceinline__ Sel select_field(const Hulls &h, const FieldRun &r, double B) {
+    const long long sb = (long long)r.blk0 * T1_MAXPASS;
+    return select_for_budget(h.skey + sb, h.cum + sb, r.sc->nseg, B);
+}
+
+// Live lists: live[0] = count, live[1 + k] = table index of grid slot k.
+// One CTA runs `step` on every listed field and keeps, in order and in place,
+// those for which it returns true.
+template <typename F>
+__device__ void compact(int *live, F &&step) {
+    __shared__ int ws[32];
+    __shared__ int out;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int n = live[0];
+    if (tid == 0) out = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+        const int k = c0 + tid;
+        int f = -1;
+        bool keep = false;
+        if (k < n) {
+            f = live[1 + k];
+            keep = step(f);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) ws[wid] = __popc(m);
+        __syncthreads();
+        int off = out;
+        for (int q = 0; q < wid; q++) off += ws[q];
+        if (keep) live[1 + off + __popc(m & ((1u << lane) - 1))] = f;
+        __syncthreads();
+        if (tid == 0)
+            for (int q = 0; q < nw; q++) out += ws[q];
+        __syncthreads();
+    }
+    if (tid == 0) live[0] = out;
+}
+
+__global__ void bl_start(BaseLoop *bl, const FieldRun *tab, const int *list, int n, double q, int fallback, double r0,
+                         double tol, Hulls h, int *live) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int f = list[k];
+        const FieldRun &r = tab[f];
+        BaseLoop s;
+        memset(&s, 0, sizeof(s));
+        s.q = q; s.r0 = r0; s.tol = tol; s.N = (double)r.N; s.rmax = 4.0 * (double)r.N;
+        s.fallback = fallback; s.phase = 0; s.budget = 4.0 * (double)r.N / r0;
+        s.sel_eval = select_field(h, r, s.budget);
+        bl[f] = s;
+        r.sc->cnt[0] = 0;
+        live[1 + k] = f;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) live[0] = n;
+}
+
+__global__ void __launch_bounds__(1024) bl_update(BaseLoop *bl, const FieldRun *tab, Hulls h, int *live) {
+    compact(live, [&](int f) {
+        BaseLoop s = bl[f];
+        const FieldRun &r = tab[f];
+        if (!s.done) {
+            const double qA = (double)r.sc->cnt[0] / s.N;
+            r.sc->cnt[0] = 0;
+            bl_step(s, qA);
+            if (!s.done) s.sel_eval = select_field(h, r, s.budget);  // next evaluation
+            bl[f] = s;
+        }
+        return !s.done;
+    });
 }
 
 struct TruncLoop {
     long long lo, hi, mid, nbits, T;
     int iters, done;
-    unsigned long long count;
 };
 
 __device__ void tl_next(TruncLoop &t) {
@@ -104,37 +172,72 @@ __device__ void tl_next(TruncLoop &t) {
         t.done = 1;
     }
 }
-__global__ void tl_init(TruncLoop *tp, long long len_bytes, long long nbits) {
-    TruncLoop t;
-    t.lo = 0; t.hi = len_bytes; t.nbits = nbits; t.iters = 0; t.done = 0; t.count = 0; t.mid = 0; t.T = 0;
-    tl_next(t);
-    *tp = t;
+
+// binary search for the best feasible truncation point (Algorithm 1), over
+// the stream's bytes
+__global__ void __launch_bounds__(1024) tl_start(TruncLoop *tl, const FieldRun *tab, int *live) {
+    compact(live, [&](int f) {
+        const FieldRun &r = tab[f];
+        TruncLoop t;
+        t.nbits = r.sc->nbits;
+        t.lo = 0; t.hi = (t.nbits + 7) / 8; t.iters = 0; t.done = 0; t.mid = 0; t.T = 0;
+        tl_next(t);
+        tl[f] = t;
+        r.sc->T = t.T;
+        r.sc->cnt[1] = 0;
+        return !t.done;
+    });
 }
-// binary search for the best feasible truncation point (Algorithm 1)
-__global__ void tl_update(TruncLoop *tp) {
-    TruncLoop t = *tp;
-    if (t.done) return;
-    t.iters++;
-    if (t.count > 0) t.lo = t.mid; else t.hi = t.mid;
-    t.count = 0;
-    tl_next(t);
-    *tp = t;
+
+__global__ void __launch_bounds__(1024) tl_update(TruncLoop *tl, const FieldRun *tab, int *live) {
+    compact(live, [&](int f) {
+        TruncLoop t = tl[f];
+        const FieldRun &r = tab[f];
+        if (!t.done) {
+            t.iters++;
+            if (r.sc->cnt[1] > 0) t.lo = t.mid; else t.hi = t.mid;
+            r.sc->cnt[1] = 0;
+            tl_next(t);
+            r.sc->T = t.T;
+            tl[f] = t;
+        }
+        return !t.done;
+    });
 }
 
 // ------------------------------------------------------------ small kernels
-__global__ void escape_kernel(const float *abase, const float *ares, float2 *bounds, const float *x, size_t n,
-                              uint32_t *esc, unsigned long long *nesc, unsigned long long cap) {
-    // one CTA, ascending order: a block-wide ballot compaction per 1024 points
+// live list from a host-chosen list of table indices
+__global__ void set_live(const int *list, int n, int *live) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) live[1 + k] = list[k];
+    if (blockIdx.x == 0 && threadIdx.x == 0) live[0] = n;
+}
+
+// per listed field: SPIHT step exponent es[f] (when given); clear the
+// truncation-loop counter (when asked)
+__global__ void set_scalars(Live lv, const int *es, int zero_cnt1) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= *lv.n) return;
+    const int f = lv.idx[k];
+    if (es) lv.tab[f].sc->es = es[f];
+    if (zero_cnt1) lv.tab[f].sc->cnt[1] = 0;
+}
+
+// escapes: points whose full two-layer reconstruction Abase + W still misses
+// the bound keep their exact value; one CTA per field, ascending order
+__global__ void escape_kernel(Live lv) {
+    if ((int)blockIdx.x >= *lv.n) return;
+    const FieldRun &r = lv.tab[lv.idx[blockIdx.x]];
     __shared__ int wc[32];
     __shared__ unsigned long long base;
     if (threadIdx.x == 0) base = 0;
     __syncthreads();
-    for (size_t b0 = 0; b0 < n; b0 += blockDim.x) {
-        size_t i = b0 + threadIdx.x;
+    const long long n = r.N;
+    for (long long b0 = 0; b0 < n; b0 += blockDim.x) {
+        long long i = b0 + threadIdx.x;
         bool bad = false;
         if (i < n) {
-            float a = abase[i] + ares[i];
-            float2 bd = bounds[i];
+            float a = r.Abase[i] + r.W[i];
+            float2 bd = r.bounds[i];
             bad = !(a >= bd.x && a <= bd.y);
         }
         unsigned m = __ballot_sync(0xffffffffu, bad);
@@ -145,11 +248,11 @@ __global__ void escape_kernel(const float *abase, const float *ares, float2 *bou
         for (int k = 0; k < wid; k++) off += wc[k];
         if (bad) {
             unsigned long long pos = base + off + __popc(m & ((1u << lane) - 1));
-            if (pos < cap) {
-                esc[2 * pos] = (uint32_t)i;
-                esc[2 * pos + 1] = __float_as_uint(x[i]);
+            if (pos < (unsigned long long)r.esc_cap) {
+                r.esc[2 * pos] = (uint32_t)i;
+                r.esc[2 * pos + 1] = __float_as_uint(r.x[i]);
             }
-            bounds[i] = make_float2(-INFINITY, INFINITY);
+            r.bounds[i] = make_float2(-INFINITY, INFINITY);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -159,7 +262,7 @@ __global__ void escape_kernel(const float *abase, const float *ares, float2 *bou
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) *nesc = base;
+    if (threadIdx.x == 0) r.sc->nesc = base;
 }
 
 __device__ __forceinline__ int varint_len(uint32_t v) {
@@ -168,9 +271,14 @@ __device__ __forceinline__ int varint_len(uint32_t v) {
     return n;
 }
 
-// per-block sizes of the base section and their exclusive scans (one CTA)
-__global__ void base_sizes(const int32_t *np, const int32_t *pass_len, int maxpass, int nblk, uint32_t *meta_off,
-                           uint32_t *pay_off, unsigned long long *tot /*[2]*/) {
+// per-block sizes of the base section and their exclusive scans; one CTA per field
+__global__ void base_sizes(Live lv, const int32_t *npass, const int32_t *pass_len, uint32_t *meta_off_all,
+                           uint32_t *pay_off_all) {
+    if ((int)blockIdx.x >= *lv.n) return;
+    const FieldRun &r = lv.tab[lv.idx[blockIdx.x]];
+    const int nblk = r.nblk, b00 = r.blk0;
+    const int32_t *np = npass + b00;
+    uint32_t *meta_off = meta_off_all + b00, *pay_off = pay_off_all + b00;
     __shared__ unsigned long long ws[2][32];
     __shared__ unsigned long long run[2];
     if (threadIdx.x == 0) { run[0] = 0; run[1] = 0; }
@@ -181,7 +289,7 @@ __global__ void base_sizes(const int32_t *np, const int32_t *pass_len, int maxpa
         unsigned long long m = 0, p = 0;
         if (b < nblk) {
             int n = np[b];
-            uint32_t l = n > 0 ? (uint32_t)pass_len[(size_t)b * maxpass + n - 1] : 0;
+            uint32_t l = n > 0 ? (uint32_t)pass_len[(size_t)(b00 + b) * T1_MAXPASS + n - 1] : 0;
             m = 1 + (n > 0 ? 1 + varint_len(l) : 0);
             p = l;
         }
@@ -204,88 +312,151 @@ __global__ void base_sizes(const int32_t *np, const int32_t *pass_len, int maxpa
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) { tot[0] = run[0]; tot[1] = run[1]; }
+    if (threadIdx.x == 0) { r.sc->tot[0] = run[0]; r.sc->tot[1] = run[1]; }
 }
 
-// writes the base section at out (meta records, then payloads): warp per block
-__global__ void base_write(const int32_t *np, const int32_t *K, const int32_t *pass_len, const uint32_t *tail,
-                           const int32_t *tail_len, const uint8_t *bytes, int cap, int maxpass, int nblk,
-                           const uint32_t *meta_off, const uint32_t *pay_off, const unsigned long long *tot,
-                           uint8_t *out, long long out_cap) {
+// writes the base section after the header (meta records, then payloads):
+// warp per code-block, grid.y = field slot
+__global__ void base_write(Live lv, T1Out t1, const int32_t *npass, const uint32_t *meta_off_all,
+                           const uint32_t *pay_off_all) {
+    if ((int)blockIdx.y >= *lv.n) return;
+    const FieldRun &r = lv.tab[lv.idx[blockIdx.y]];
+    uint8_t *out = r.out + HDR_BYTES;
+    const long long out_cap = r.out_cap - HDR_BYTES;
     const int lane = threadIdx.x & 31;
-    const unsigned long long meta_total = tot[0];
-    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nblk; b += (gridDim.x * blockDim.x) >> 5) {
-        const int n = np[b];
-        uint8_t *m = out + meta_off[b];
-        if (!INB((long long)meta_off[b] + 6, out_cap + 6)) continue;
+    const unsigned long long meta_total = r.sc->tot[0];
+    const int maxpass = T1_MAXPASS, cap = t1.cap;
+    for (int bl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; bl < r.nblk; bl += (gridDim.x * blockDim.x) >> 5) {
+        const int b = r.blk0 + bl;
+        const int n = npass[b];
+        const uint32_t mo = meta_off_all[b], po = pay_off_all[b];
+        uint8_t *m = out + mo;
+        if (!INB((long long)mo + 6, out_cap + 6)) continue;
         if (n <= 0) {
             if (lane == 0) m[0] = 0;
             continue;
         }
         if (!INB(n - 1, maxpass)) continue;
         const size_t pi = (size_t)b * maxpass + n - 1;
-        const uint32_t l = (uint32_t)pass_len[pi];
-        const int tl = tail_len[pi];
+        const uint32_t l = (uint32_t)t1.pass_len[pi];
+        const int tl = t1.tail_len[pi];
         if (lane == 0) {
             m[0] = (uint8_t)n;
-            m[1] = (uint8_t)K[b];
+            m[1] = (uint8_t)t1.K[b];
             uint32_t v = l;
             int k = 2;
             while (v >= 128) { m[k++] = (uint8_t)(0x80 | (v & 0x7F)); v >>= 7; }
             m[k] = (uint8_t)v;
         }
-        uint8_t *p = out + meta_total + pay_off[b];
-        const uint8_t *src = bytes + (size_t)b * cap;
+        uint8_t *p = out + meta_total + po;
+        const uint8_t *src = t1.bytes + (size_t)b * cap;
         const uint32_t nf = l - tl;
         for (uint32_t k = lane; k < l; k += 32)
-            if (INB((long long)meta_total + pay_off[b] + k, out_cap) && INB(k < nf ? k : 0, cap))
-                p[k] = k < nf ? src[k] : (uint8_t)(tail[pi] >> (8 * (k - nf)));
+            if (INB((long long)meta_total + po + k, out_cap) && INB(k < nf ? k : 0, cap))
+                p[k] = k < nf ? src[k] : (uint8_t)(t1.tail[pi] >> (8 * (k - nf)));
     }
 }
 
+// what follows the base section of each field's stream, and its header
+struct PackPlan {
+    uint8_t hdr[HDR_BYTES];
+    long long base_len, res_len, n_esc;
+    int write_hdr, pad;
+};
+
+__global__ void pack_tail(Live lv, const PackPlan *plan) {
+    if ((int)blockIdx.y >= *lv.n) return;
+    const int f = lv.idx[blockIdx.y];
+    const FieldRun &r = lv.tab[f];
+    const PackPlan &P = plan[f];
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x, step = (long long)gridDim.x * blockDim.x;
+    if (P.write_hdr)
+        for (long long k = t; k < HDR_BYTES; k += step)
+            if (INB(k, r.out_cap)) r.out[k] = P.hdr[k];
+    uint8_t *dst = r.out + HDR_BYTES + P.base_len;
+    for (long long k = t; k < P.res_len; k += step)
+        if (INB(HDR_BYTES + P.base_len + k, r.out_cap) && INB(k, r.sp_cap)) dst[k] = r.sp[k];
+    const uint8_t *e = (const uint8_t *)r.esc;
+    dst += P.res_len;
+    for (long long k = t; k < 8 * P.n_esc; k += step)
+        if (INB(HDR_BYTES + P.base_len + P.res_len + k, r.out_cap) && INB(k, 8 * r.esc_cap)) dst[k] = e[k];
+}
+
+// ---- decompression
+__global__ void hdr_gather(const uint8_t *const *src, const long long *len, int n, uint8_t *dst) {
+    const int f = blockIdx.x;
+    if (f >= n) return;
+    for (int k = threadIdx.x; k < HDR_BYTES; k += blockDim.x)
+        dst[(size_t)f * HDR_BYTES + k] = len[f] >= HDR_BYTES ? src[f][k] : 0;
+}
+
 // sequential parse of the base metadata of one stream: per-block pass count,
-// K, payload length and absolute payload offset; *ok = 0 on inconsistency
-__global__ void base_parse(const uint8_t *s, long long base_off, long long base_len, int nblk, int32_t *np, int32_t *K,
-                           int32_t *len, int64_t *off, int *ok) {
-    if (threadIdx.x || blockIdx.x) return;
+// K, payload length and absolute payload address; sc->ok = 0 on inconsistency
+__global__ void base_parse(Live lv, int32_t *np_all, int32_t *K_all, int32_t *len_all, int64_t *addr_all) {
+    if ((int)blockIdx.x >= *lv.n || threadIdx.x) return;
+    const FieldRun &r = lv.tab[lv.idx[blockIdx.x]];
+    const uint8_t *s = r.in + HDR_BYTES;
+    const long long base_len = r.base_len;
+    const int nblk = r.nblk, b0 = r.blk0;
     long long pos = 0;
     int good = 1;
     for (int b = 0; b < nblk; b++) {
         if (pos >= base_len) { good = 0; break; }
-        int n = s[base_off + pos++];
-        np[b] = n; K[b] = 0; len[b] = 0;
+        int n = s[pos++];
+        np_all[b0 + b] = n; K_all[b0 + b] = 0; len_all[b0 + b] = 0;
         if (n > 0) {
             if (pos >= base_len) { good = 0; break; }
-            int k = s[base_off + pos++];
+            int k = s[pos++];
             uint32_t v = 0;
             int sh = 0, done = 0;
             for (int t = 0; t < 5 && pos < base_len; t++) {
-                uint8_t c = s[base_off + pos++];
+                uint8_t c = s[pos++];
                 v |= (uint32_t)(c & 0x7F) << sh;
                 sh += 7;
                 if (!(c & 0x80)) { done = 1; break; }
             }
             if (!done || k < 1 || k > 30 || n > 3 * k - 2) { good = 0; break; }
-            K[b] = k; len[b] = (int32_t)v;
+            K_all[b0 + b] = k; len_all[b0 + b] = (int32_t)v;
         }
     }
     long long p = pos;
     for (int b = 0; good && b < nblk; b++) {
-        off[b] = base_off + p;
-        p += len[b];
+        addr_all[b0 + b] = (int64_t)(uintptr_t)(s + p);
+        p += len_all[b0 + b];
     }
     if (p != base_len) good = 0;
-    *ok = good;
+    if (!good)
+        for (int b = 0; b < nblk; b++) { np_all[b0 + b] = 0; K_all[b0 + b] = 0; len_all[b0 + b] = 0; addr_all[b0 + b] = 0; }
+    r.sc->ok = good;
 }
 
-__global__ void scatter_escapes(const uint8_t *e, long long n, float *out, long long N, int *ok) {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+__global__ void scatter_escapes(Live lv) {
+    if ((int)blockIdx.y >= *lv.n) return;
+    const FieldRun &r = lv.tab[lv.idx[blockIdx.y]];
+    const uint8_t *e = r.in + HDR_BYTES + r.base_len + r.res_len;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < r.n_esc;
+         k += (long long)gridDim.x * blockDim.x) {
         uint32_t idx, v;
         memcpy(&idx, e + 8 * k, 4);
         memcpy(&v, e + 8 * k + 4, 4);
-        if (idx < N) out[idx] = __uint_as_float(v);
-        else *ok = 0;
+        if (idx < r.N) r.dst[idx] = __uint_as_float(v);
+        else r.sc->ok = 0;
     }
+}
+
+__global__ void fill_kernel(Live lv) {
+    if ((int)blockIdx.y >= *lv.n) return;
+    const FieldRun &r = lv.tab[lv.idx[blockIdx.y]];
+    const float v = (float)r.mn;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < r.N; i += (long long)gridDim.x * blockDim.x)
+        r.dst[i] = v;
+}
+
+unsigned cgrid(long long n, int nslots, int per = 256) {
+    long long g = (n + per - 1) / per;
+    long long cap = 2432 / (nslots > 0 ? nslots : 1);
+    if (cap < 4) cap = 4;
+    return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
 }  // namespace
@@ -309,116 +480,238 @@ namespace {
 size_t scratch1(size_t ny, size_t nx) { return ((ny + 1) / 2) * ((nx + 1) / 2) + 16; }
 size_t scratch2(size_t ny, size_t nx) { return ((ny + 3) / 4) * ((nx + 3) / 4) + 16; }
 
+// bump allocation in an arena; with a null base it only measures
 template <typename T>
 T *carve(Arena &a, size_t n) {
     size_t off = (a.used + 255) & ~(size_t)255;
     a.used = off + n * sizeof(T);
-    return (T *)(a.base + off);
+    return a.base ? (T *)(a.base + off) : nullptr;
 }
 
-struct FieldBufs {
-    float *x, *W, *Abase, *R;
-    float2 *bounds;
-    int32_t *qt, *s;
-    uint32_t *sig_pos, *lsp_idx;
-    float *s1, *s2;
-    uint8_t *t1bytes, *sp_stream, *spw;
-    size_t sp_cap;
-    T1Out t1;
-    Hulls hull;
-    BlockDesc *blk;
-    int32_t *npass;
-    uint32_t *meta_off, *pay_off;
-    unsigned long long *tot;
-    uint32_t *esc;
-    size_t esc_cap;
-    BaseLoop *bl;
-    TruncLoop *tl;
-    double *mm;
-    int *nonfinite;
-    int64_t *nbits, *refine_start;
-    int32_t *nmax, *status;
-    unsigned long long *nesc;
-    SpihtWork sw;
+// Pinned host staging for the uploads and downloads of one batch (bump
+// allocated; every region is used by one copy only, so no copy waits on
+// another).
+struct Engine {
+    Arena a;
+    uint8_t *stage = nullptr;
+    size_t stage_cap = 0, stage_used = 0;
+    cudaEvent_t ev[2];
+    bool ev_ok = false;
 };
 
-size_t field_bytes(const FieldGeom &g, int cap_per_blk) {
-    size_t N = (size_t)g.ny * g.nx, nb = g.nblocks;
-    size_t q = scratch1(g.ny, g.nx), q2 = scratch2(g.ny, g.nx);
-    size_t b = 0;
-    b += N * 4 * 4;          // x, W, Abase, R
-    b += N * 8;              // bounds
-    b += N * 4 * 4;          // qt, s, sig_pos, lsp_idx
-    b += (q + q2) * 4;
-    b += nb * (size_t)cap_per_blk;
-    b += 8 * N + 4096;       // SPIHT stream
-    b += spiht_work_bytes(N);
-    b += nb * T1_MAXPASS * (4 + 4 + 4 + 8) + nb * (4 * 4 + 8);
-    b += nb * (T1_MAXPASS + 1) * (4 + 4 + 8) + nb * 4;
-    b += nb * T1_MAXPASS * (8 + 8 + 4 + 4 + 8);  // sorted segments
-    b += nb * sizeof(BlockDesc) + nb * 4 * 3;
-    b += 2 * 4 * 4096 + 4096;  // escapes
-    b += 64 * 256;           // small structs and alignment
-    return b + 40 * 256;
+int engine_begin(Engine &e, size_t stage_bytes) {
+    if (!e.ev_ok) {
+        CK(cudaEventCreateWithFlags(&e.ev[0], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&e.ev[1], cudaEventDisableTiming));
+        e.ev_ok = true;
+    }
+    if (e.stage_cap < stage_bytes) {
+        if (e.stage) cudaFreeHost(e.stage);
+        e.stage = nullptr;
+        e.stage_cap = 0;
+        size_t cap = stage_bytes + stage_bytes / 4;
+        if (cudaHostAlloc((void **)&e.stage, cap, cudaHostAllocDefault) != cudaSuccess) return EBCC_ENOMEM;
+        e.stage_cap = cap;
+    }
+    e.stage_used = 0;
+    return EBCC_OK;
 }
 
-void carve_field(Arena &a, const FieldGeom &g, int cap_per_blk, FieldBufs &f) {
-    size_t N = (size_t)g.ny * g.nx, nb = g.nblocks;
-    size_t q = scratch1(g.ny, g.nx), q2 = scratch2(g.ny, g.nx);
-    f.x = carve<float>(a, N);
-    f.W = carve<float>(a, N);
-    f.Abase = carve<float>(a, N);
-    f.R = carve<float>(a, N);
-    f.bounds = carve<float2>(a, N);
-    f.qt = carve<int32_t>(a, N);
-    f.s = carve<int32_t>(a, N);
-    f.sig_pos = carve<uint32_t>(a, N);
-    f.lsp_idx = carve<uint32_t>(a, N);
-    f.s1 = carve<float>(a, q);
-    f.s2 = carve<float>(a, q2);
-    f.t1bytes = carve<uint8_t>(a, nb * (size_t)cap_per_blk);
-    f.sp_cap = 8 * N + 4096;
-    f.sp_stream = carve<uint8_t>(a, f.sp_cap);
-    f.spw = carve<uint8_t>(a, spiht_work_bytes(N));
-    spiht_work_carve(f.spw, N, &f.sw);
-    f.t1.bytes = f.t1bytes;
-    f.t1.cap = cap_per_blk;
-    f.t1.maxpass = T1_MAXPASS;
-    f.t1.K = carve<int32_t>(a, nb);
-    f.t1.npass = carve<int32_t>(a, nb);
-    f.t1.pass_len = carve<int32_t>(a, nb * T1_MAXPASS);
-    f.t1.tail = carve<uint32_t>(a, nb * T1_MAXPASS);
-    f.t1.tail_len = carve<int32_t>(a, nb * T1_MAXPASS);
-    f.t1.dD = carve<int64_t>(a, nb * T1_MAXPASS);
-    f.t1.D0 = carve<int64_t>(a, nb);
-    f.t1.status = carve<int32_t>(a, 4);
-    f.hull.maxpt = T1_MAXPASS + 1;
-    f.hull.nh = carve<int32_t>(a, nb);
-    f.hull.pt = carve<int32_t>(a, nb * (T1_MAXPASS + 1));
-    f.hull.rate = carve<int32_t>(a, nb * (T1_MAXPASS + 1));
-    f.hull.key = carve<uint64_t>(a, nb * (T1_MAXPASS + 1));
-    f.hull.skey = carve<uint64_t>(a, nb * T1_MAXPASS);
-    f.hull.skey2 = carve<uint64_t>(a, nb * T1_MAXPASS);
-    f.hull.sdr = carve<uint32_t>(a, nb * T1_MAXPASS);
-    f.hull.sdr2 = carve<uint32_t>(a, nb * T1_MAXPASS);
-    f.hull.cum = carve<unsigned long long>(a, nb * T1_MAXPASS);
-    f.hull.nseg = carve<int>(a, 4);
-    f.blk = carve<BlockDesc>(a, nb);
-    f.npass = carve<int32_t>(a, nb);
-    f.meta_off = carve<uint32_t>(a, nb);
-    f.pay_off = carve<uint32_t>(a, nb);
-    f.tot = carve<unsigned long long>(a, 2);
-    f.esc_cap = 4096;
-    f.esc = carve<uint32_t>(a, 2 * f.esc_cap);
-    f.bl = carve<BaseLoop>(a, 1);
-    f.tl = carve<TruncLoop>(a, 1);
-    f.mm = carve<double>(a, 4);
-    f.nonfinite = carve<int>(a, 4);
-    f.nbits = carve<int64_t>(a, 1);
-    f.refine_start = carve<int64_t>(a, 32);
-    f.nmax = carve<int32_t>(a, 1);
-    f.status = carve<int32_t>(a, 1);
-    f.nesc = carve<unsigned long long>(a, 1);
+template <typename T>
+T *stage_take(Engine &e, size_t n) {
+    size_t off = (e.stage_used + 255) & ~(size_t)255;
+    if (off + n * sizeof(T) > e.stage_cap) return nullptr;
+    e.stage_used = off + n * sizeof(T);
+    return (T *)(e.stage + off);
+}
+
+int upload(Engine &e, void *dst, const void *src, size_t bytes, cudaStream_t st) {
+    if (!bytes) return EBCC_OK;
+    uint8_t *p = stage_take<uint8_t>(e, bytes);
+    if (!p) return EBCC_ECAPACITY;
+    memcpy(p, src, bytes);
+    CK(cudaMemcpyAsync(dst, p, bytes, cudaMemcpyHostToDevice, st));
+    return EBCC_OK;
+}
+
+// device -> pinned staging, synchronous on st; returns the host copy
+template <typename T>
+int download(Engine &e, const T *src, size_t n, T **host, cudaStream_t st) {
+    T *p = stage_take<T>(e, n);
+    if (!p) return EBCC_ECAPACITY;
+    if (n) CK(cudaMemcpyAsync(p, src, n * sizeof(T), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *host = p;
+    return EBCC_OK;
+}
+
+// One batch on the device: the field table and the batch-wide arrays.
+struct Batch {
+    int F = 0;                      // table entries
+    std::vector<FieldRun> run;      // host copy of the table
+    std::vector<FieldGeom> geom;
+    std::vector<BlockDesc> blk;     // code-blocks of the fields taking part, in table order
+    FieldRun *d_run = nullptr;
+    FieldGeom *d_geom = nullptr;
+    FieldScal *d_sc = nullptr;
+    BlockDesc *d_blk = nullptr;
+    T1Out t1{};
+    Hulls hull{};
+    int32_t *npass = nullptr;
+    uint32_t *meta_off = nullptr, *pay_off = nullptr;
+    int64_t *addr = nullptr;        // decoder: payload address per block
+    BaseLoop *bl = nullptr;
+    TruncLoop *tl = nullptr;
+    int *live = nullptr;            // F + 1
+    int *list = nullptr;            // F
+    int *es = nullptr;              // F
+    Sel *sel = nullptr;             // F
+    PackPlan *plan = nullptr;       // F
+    BatchDims dims{};
+    long long Ntot = 0;
+    int Btot = 0;
+    int cap_blk = 0;
+};
+
+Live live_of(const Batch &b) { return Live{b.d_run, b.live + 1, b.live}; }
+
+// host list -> device live list
+int set_list(Engine &e, Batch &b, const std::vector<int> &lst, cudaStream_t st) {
+    RC(upload(e, b.list, lst.data(), lst.size() * sizeof(int), st));
+    set_live<<<1, 256, 0, st>>>(b.list, (int)lst.size(), b.live);
+    CK(cudaGetLastError());
+    return EBCC_OK;
+}
+
+const FieldRun kNone{};  // placeholder `one` argument of batched launches
+
+// Shapes of the fields of a compression batch: lays out every buffer (a dry
+// run with a null arena measures it) and fills the pointers of the table.
+// Geometry-dependent values (normalisation, steps) are filled later.
+void layout_compress(Arena &a, Batch &b, const std::vector<int> &ny, const std::vector<int> &nx,
+                     const std::vector<int> &L, const std::vector<int> &nblk, int cap_blk) {
+    const int F = (int)ny.size();
+    b.F = F;
+    b.run.assign(F, FieldRun{});
+    b.cap_blk = cap_blk;
+    long long Ntot = 0;
+    int Btot = 0;
+    std::vector<long long> pt(F);
+    for (int f = 0; f < F; f++) {
+        pt[f] = Ntot;
+        Ntot += ((long long)ny[f] * nx[f] + 63) / 64 * 64;
+        Btot += nblk[f];
+    }
+    b.Ntot = Ntot;
+    b.Btot = Btot;
+    float *W = carve<float>(a, Ntot), *Ab = carve<float>(a, Ntot), *R = carve<float>(a, Ntot);
+    float2 *bounds = carve<float2>(a, Ntot);
+    int32_t *qt = carve<int32_t>(a, Ntot), *s = carve<int32_t>(a, Ntot);
+    uint32_t *sig = carve<uint32_t>(a, Ntot), *lsp = carve<uint32_t>(a, Ntot);
+    const size_t nb = (size_t)Btot + 1;
+    b.t1.bytes = carve<uint8_t>(a, nb * cap_blk);
+    b.t1.cap = cap_blk;
+    b.t1.maxpass = T1_MAXPASS;
+    b.t1.K = carve<int32_t>(a, nb);
+    b.t1.npass = carve<int32_t>(a, nb);
+    b.t1.pass_len = carve<int32_t>(a, nb * T1_MAXPASS);
+    b.t1.tail = carve<uint32_t>(a, nb * T1_MAXPASS);
+    b.t1.tail_len = carve<int32_t>(a, nb * T1_MAXPASS);
+    b.t1.dD = carve<int64_t>(a, nb * T1_MAXPASS);
+    b.t1.D0 = carve<int64_t>(a, nb);
+    b.t1.status = carve<int32_t>(a, 4);
+    b.hull.maxpt = T1_MAXPASS + 1;
+    b.hull.nh = carve<int32_t>(a, nb);
+    b.hull.pt = carve<int32_t>(a, nb * (T1_MAXPASS + 1));
+    b.hull.rate = carve<int32_t>(a, nb * (T1_MAXPASS + 1));
+    b.hull.key = carve<uint64_t>(a, nb * (T1_MAXPASS + 1));
+    b.hull.skey = carve<uint64_t>(a, nb * T1_MAXPASS);
+    b.hull.skey2 = carve<uint64_t>(a, nb * T1_MAXPASS);
+    b.hull.sdr = carve<uint32_t>(a, nb * T1_MAXPASS);
+    b.hull.sdr2 = carve<uint32_t>(a, nb * T1_MAXPASS);
+    b.hull.cum = carve<unsigned long long>(a, nb * T1_MAXPASS);
+    b.npass = carve<int32_t>(a, nb);
+    b.meta_off = carve<uint32_t>(a, nb);
+    b.pay_off = carve<uint32_t>(a, nb);
+    b.d_blk = carve<BlockDesc>(a, nb);
+    b.d_run = carve<FieldRun>(a, F);
+    b.d_geom = carve<FieldGeom>(a, F);
+    b.d_sc = carve<FieldScal>(a, F);
+    b.bl = carve<BaseLoop>(a, F);
+    b.tl = carve<TruncLoop>(a, F);
+    b.live = carve<int>(a, F + 1);
+    b.list = carve<int>(a, F + 1);
+    b.es = carve<int>(a, F + 1);
+    b.sel = carve<Sel>(a, F + 1);
+    b.plan = carve<PackPlan>(a, F + 1);
+    for (int f = 0; f < F; f++) {
+        FieldRun &r = b.run[f];
+        const long long N = (long long)ny[f] * nx[f];
+        r.ny = ny[f]; r.nx = nx[f]; r.L = L[f]; r.N = N;
+        auto at = [&](auto *p) { return p ? p + pt[f] : p; };
+        r.W = at(W); r.Abase = at(Ab); r.R = at(R); r.bounds = at(bounds);
+        r.qt = at(qt); r.s = at(s); r.sig_pos = at(sig); r.lsp_idx = at(lsp);
+        r.s1 = carve<float>(a, scratch1(ny[f], nx[f]));
+        r.s2 = carve<float>(a, scratch2(ny[f], nx[f]));
+        uint8_t *spw = carve<uint8_t>(a, spiht_work_bytes(N));
+        if (spw) spiht_work_carve(spw, N, &r.sw);
+        r.sp_cap = (8 * N + 4096 + 15) / 16 * 16;
+        r.sp = carve<uint8_t>(a, r.sp_cap);
+        r.esc_cap = 4096;
+        r.esc = carve<uint32_t>(a, 2 * r.esc_cap);
+        r.geom = b.d_geom ? b.d_geom + f : nullptr;
+        r.sc = b.d_sc ? b.d_sc + f : nullptr;
+    }
+}
+
+// the same for a decompression batch
+void layout_decompress(Arena &a, Batch &b, const std::vector<int> &ny, const std::vector<int> &nx,
+                       const std::vector<int> &nblk) {
+    const int F = (int)ny.size();
+    b.F = F;
+    b.run.assign(F, FieldRun{});
+    long long Ntot = 0;
+    int Btot = 0;
+    std::vector<long long> pt(F);
+    for (int f = 0; f < F; f++) {
+        pt[f] = Ntot;
+        Ntot += ((long long)ny[f] * nx[f] + 63) / 64 * 64;
+        Btot += nblk[f];
+    }
+    b.Ntot = Ntot;
+    b.Btot = Btot;
+    float *W = carve<float>(a, Ntot), *Ab = carve<float>(a, Ntot), *R = carve<float>(a, Ntot);
+    int32_t *qt = carve<int32_t>(a, Ntot);
+    int8_t *pl = carve<int8_t>(a, Ntot);
+    uint8_t *ng = carve<uint8_t>(a, Ntot);
+    const size_t nb = (size_t)Btot + 1;
+    b.t1.K = carve<int32_t>(a, nb);
+    b.t1.pass_len = carve<int32_t>(a, nb);  // payload length per block
+    b.npass = carve<int32_t>(a, nb);
+    b.addr = carve<int64_t>(a, nb);
+    b.d_blk = carve<BlockDesc>(a, nb);
+    b.d_run = carve<FieldRun>(a, F);
+    b.d_geom = carve<FieldGeom>(a, F);
+    b.d_sc = carve<FieldScal>(a, F);
+    b.live = carve<int>(a, F + 1);
+    b.list = carve<int>(a, F + 1);
+    for (int f = 0; f < F; f++) {
+        FieldRun &r = b.run[f];
+        const long long N = (long long)ny[f] * nx[f];
+        r.ny = ny[f]; r.nx = nx[f]; r.N = N;
+        auto at = [&](auto *p) { return p ? p + pt[f] : p; };
+        r.W = at(W); r.Abase = at(Ab); r.R = at(R); r.qt = at(qt); r.plane8 = at(pl); r.neg8 = at(ng);
+        r.s1 = carve<float>(a, scratch1(ny[f], nx[f]));
+        r.s2 = carve<float>(a, scratch2(ny[f], nx[f]));
+        uint8_t *spw = carve<uint8_t>(a, spiht_work_bytes(N));
+        if (spw) spiht_work_carve(spw, N, &r.sw);
+        r.geom = b.d_geom ? b.d_geom + f : nullptr;
+        r.sc = b.d_sc ? b.d_sc + f : nullptr;
+    }
+}
+
+size_t stage_bytes_for(int F, int Btot) {
+    return ((size_t)4 << 20) + (size_t)F * 24576 + (size_t)Btot * 64;
 }
 
 int validate_params(const ebcc_params &p) {
@@ -429,288 +722,23 @@ int validate_params(const ebcc_params &p) {
     return EBCC_OK;
 }
 
-struct HostHeader {
-    uint8_t b[HDR_BYTES];
-};
-
-void write_header(HostHeader &h, int flags, int L, int cw, int ch, int P, int es, int nmax, int ny, int nx,
-                  uint32_t bl, uint32_t rl, uint32_t ne, double mn, double mx, double eps) {
-    memset(h.b, 0, HDR_BYTES);
-    h.b[0] = 'E'; h.b[1] = 'B'; h.b[2] = 'C'; h.b[3] = '1';
-    h.b[4] = 1;
-    h.b[5] = (uint8_t)flags;
-    h.b[6] = (uint8_t)L;
+void write_header(uint8_t *h, int flags, int L, int cw, int ch, int P, int es, int nmax, int ny, int nx, uint32_t bl,
+                  uint32_t rl, uint32_t ne, double mn, double mx, double eps) {
+    memset(h, 0, HDR_BYTES);
+    h[0] = 'E'; h[1] = 'B'; h[2] = 'C'; h[3] = '1';
+    h[4] = 1;
+    h[5] = (uint8_t)flags;
+    h[6] = (uint8_t)L;
     int lw = 0, lh = 0;
     while ((1 << lw) < cw) lw++;
     while ((1 << lh) < ch) lh++;
-    h.b[7] = (uint8_t)lw; h.b[8] = (uint8_t)lh; h.b[9] = (uint8_t)P;
-    h.b[10] = (uint8_t)(int8_t)es; h.b[11] = (uint8_t)(int8_t)nmax;
+    h[7] = (uint8_t)lw; h[8] = (uint8_t)lh; h[9] = (uint8_t)P;
+    h[10] = (uint8_t)(int8_t)es; h[11] = (uint8_t)(int8_t)nmax;
     uint32_t u[5] = {(uint32_t)ny, (uint32_t)nx, bl, rl, ne};
-    memcpy(h.b + 12, u, 20);
-    memcpy(h.b + 32, &mn, 8);
-    memcpy(h.b + 40, &mx, 8);
-    memcpy(h.b + 48, &eps, 8);
-}
-
-// runs one base loop to completion (Algorithm 1 bracketing + bisection)
-int run_base_loop(FieldBufs &f, const FieldGeom &g, double q, int fallback, const ebcc_params &p, BaseLoop &out,
-                  cudaStream_t st) {
-    const size_t N = (size_t)g.ny * g.nx;
-    BaseLoop init;
-    memset(&init, 0, sizeof(init));
-    init.q = q; init.r0 = p.r0; init.tol = p.tol; init.N = (double)N; init.rmax = 4.0 * (double)N;
-    init.fallback = fallback; init.phase = 0; init.budget = 4.0 * (double)N / p.r0;
-    CK(cudaMemcpyAsync(f.bl, &init, sizeof(init), cudaMemcpyHostToDevice, st));
-    int *hdone = nullptr;
-    CK(cudaMallocHost(&hdone, 2 * sizeof(int)));
-    cudaEvent_t ev[2];
-    CK(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
-    InvFinal fin{1, f.bounds, nullptr, &f.bl->count};
-    int rc = pcrd_select(f.hull, g.nblocks, &f.bl->budget, &f.bl->sel_eval, st);  // r0
-    for (int step = 0; step < 400 && !rc; step++) {
-        rc = pcrd_npass(f.hull, g.nblocks, &f.bl->sel_eval, f.npass, st);
-        if (!rc) rc = base_recon(f.qt, g, f.t1.K, f.npass, f.W, st);
-        if (!rc) rc = dwt_inverse_ex(f.W, nullptr, f.s1, f.s2, g.ny, g.nx, g.L, fin, 0.0, 1.0, st);
-        if (rc) break;
-        PROF("bl_update", st, 0.0, bl_update<<<1, 1, 0, st>>>(f.bl, f.hull));
-        if (ebcc_debug_sync_enabled() && ebcc_stage_check(st, "base eval", __LINE__)) { rc = EBCC_ECUDA; break; }
-        if (cudaMemcpyAsync(&hdone[step & 1], &f.bl->done, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaEventRecord(ev[step & 1], st) != cudaSuccess) { rc = EBCC_ECUDA; break; }
-        if (step >= 1) {
-            if (cudaEventSynchronize(ev[(step - 1) & 1]) != cudaSuccess) { rc = EBCC_ECUDA; break; }
-            if (hdone[(step - 1) & 1]) break;
-        }
-    }
-    if (!rc && cudaMemcpyAsync(&out, f.bl, sizeof(out), cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = EBCC_ECUDA;
-    if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = EBCC_ECUDA;
-    cudaEventDestroy(ev[0]);
-    cudaEventDestroy(ev[1]);
-    cudaFreeHost(hdone);
-    if (!rc && !out.done) rc = EBCC_ETIMEOUT;
-    return rc;
-}
-
-int pack_base_size(FieldBufs &f, const FieldGeom &g, const Sel *sel_dev, unsigned long long &bl, cudaStream_t st) {
-    RC(pcrd_npass(f.hull, g.nblocks, sel_dev, f.npass, st));
-    STAGE(st, "npass for pack");
-    PROF("base_sizes", st, 0.0, base_sizes<<<1, 1024, 0, st>>>(f.npass, f.t1.pass_len, T1_MAXPASS, g.nblocks, f.meta_off, f.pay_off, f.tot););
-    CK(cudaGetLastError());
-    unsigned long long t[2];
-    CK(cudaMemcpyAsync(t, f.tot, sizeof(t), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    bl = t[0] + t[1];
-    return EBCC_OK;
-}
-
-int pack_base_write(FieldBufs &f, const FieldGeom &g, uint8_t *out, long long out_cap, cudaStream_t st) {
-    // f.npass / meta_off / pay_off / tot are those of the last pack_base_size
-    PROF("base_write", st, 0.0, base_write<<<152 * 2, 256, 0, st>>>(f.npass, f.t1.K, f.t1.pass_len, f.t1.tail, f.t1.tail_len, f.t1.bytes,
-                                        f.t1.cap, T1_MAXPASS, g.nblocks, f.meta_off, f.pay_off, f.tot, out, out_cap););
-    CK(cudaGetLastError());
-    return EBCC_OK;
-}
-
-// Algorithm 1 on one device field; writes the stream to out (device, cap)
-int compress_field(FieldBufs &f, const float *x_dev, int ny, int nx, double bound, int kind, const ebcc_params &p,
-                   uint8_t *out, size_t cap, size_t *out_len, ebcc_stats *st_out, cudaStream_t st) {
-    ebcc_stats stt;
-    memset(&stt, 0, sizeof(stt));
-    const size_t N = (size_t)ny * nx;
-    // ---- min / max / finiteness (normalisation, Materials and Methods)
-    RC(minmax_finite(x_dev, N, f.mm, f.nonfinite, st));
-    double mm[2];
-    int nonfin = 0;
-    CK(cudaMemcpyAsync(mm, f.mm, sizeof(mm), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&nonfin, f.nonfinite, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (nonfin) return EBCC_ENONFINITE;
-    const double mn = mm[0], mx = mm[1], range = mx - mn;
-    const double eps_abs = kind == EBCC_BOUND_REL ? bound * range : bound;
-    HostHeader hh;
-    if (range == 0 || eps_abs >= range) {  // constant field, or a bound above the range: header only
-        if (cap < HDR_BYTES) return EBCC_ECAPACITY;
-        double fill = range == 0 ? mn : mn + 0.5 * range;
-        write_header(hh, 1, 0, p.cblk_w, p.cblk_h, 0, 0, -1, ny, nx, 0, 0, 0, fill, mx, eps_abs);
-        CK(cudaMemcpyAsync(out, hh.b, HDR_BYTES, cudaMemcpyHostToDevice, st));
-        CK(cudaStreamSynchronize(st));
-        *out_len = HDR_BYTES;
-        stt.total_bytes = HDR_BYTES;
-        if (st_out) *st_out = stt;
-        return EBCC_OK;
-    }
-    const double eps_n = eps_abs / range;
-    double guard = ldexp(range, -17);
-    if (guard > 0.25 * eps_abs) guard = 0.25 * eps_abs;
-    FieldGeom g;
-    make_geom(&g, ny, nx, p.levels, p.cblk_w, p.cblk_h, base_precision(eps_n));
-    const int L = g.L;
-    std::vector<BlockDesc> blk;
-    make_blocks(g, blk);
-    CK(cudaMemcpyAsync(f.blk, blk.data(), blk.size() * sizeof(BlockDesc), cudaMemcpyHostToDevice, st));
-    // ---- per-point acceptance intervals of the bound test (FP64, once)
-    RC(make_bounds(x_dev, N, mn, range, eps_abs, guard, f.bounds, st));
-    STAGE(st, "bounds");
-    // ---- base layer: DWT of the normalised field, quantise, tier-1, hulls
-    RC(dwt_forward(x_dev, f.W, f.s1, f.s2, ny, nx, L, mn, 1.0 / range, st));
-    STAGE(st, "dwt fwd");
-    RC(quantise_base(f.W, f.qt, g, 1, st));
-    STAGE(st, "quantise");
-    CK(cudaMemsetAsync(f.t1.status, 0, 4, st));
-    RC(t1_encode_blocks(f.qt, f.blk, g.nblocks, g.cw, g.ch, f.t1, 1, nullptr, (long long)N, st));
-    STAGE(st, "tier-1");
-    RC(pcrd_hulls(f.t1.npass, f.t1.pass_len, f.t1.dD, f.t1.D0, g.nblocks, T1_MAXPASS, f.hull, st));
-    RC(pcrd_prepare(f.hull, g.nblocks, st));
-    STAGE(st, "hulls");
-    // ---- base loop with q
-    BaseLoop b1;
-    RC(run_base_loop(f, g, p.q, 0, p, b1, st));
-    int t1st = 0;
-    CK(cudaMemcpyAsync(&t1st, f.t1.status, 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (t1st) return EBCC_ECAPACITY;
-    stt.r_base = b1.r_f; stt.iters_base = b1.iters; stt.q_base = b1.q_f;
-    // A_base = dec_base(e_f)
-    RC(pcrd_npass(f.hull, g.nblocks, &f.bl->sel_f, f.npass, st));
-    RC(base_recon(f.qt, g, f.t1.K, f.npass, f.W, st));
-    InvFinal store{0, nullptr, nullptr, nullptr};
-    RC(dwt_inverse_ex(f.W, f.Abase, f.s1, f.s2, ny, nx, L, store, 0.0, 1.0, st));
-    STAGE(st, "A_base");
-    Sel sel_two;
-    CK(cudaMemcpyAsync(&sel_two, &f.bl->sel_f, sizeof(Sel), cudaMemcpyDeviceToHost, st));
-    // ---- residual layer: A_residue (FP64), DWT, SPIHT with guard retries
-    RC(residue(x_dev, f.Abase, N, mn, 1.0 / range, f.R, st));
-    RC(dwt_forward(f.R, f.W, f.s1, f.s2, ny, nx, L, 0.0, 0.0, st));
-    STAGE(st, "residue dwt");
-    int G = p.spiht_guard_bits, es = 0, nmax = -1;
-    long long nbits = 0;
-    unsigned long long bad = 0;
-    InvFinal chk{2, f.bounds, f.Abase, &f.tl->count};
-    for (int attempt = 0; attempt < 3; attempt++) {
-        es = (int)floor(log2(eps_n)) - G;
-        RC(spiht_quantise(f.W, N, es, f.s, st));
-        STAGE(st, "spiht quantise");
-        CK(cudaMemsetAsync(f.status, 0, 4, st));
-        RC(spiht_encode(f.s, ny, nx, L, f.sp_stream, f.sp_cap, f.nbits, f.nmax, f.sig_pos, f.lsp_idx, f.refine_start,
-                        f.status, f.sw, st));
-        STAGE(st, "spiht encode");
-        int sstat = 0;
-        CK(cudaMemcpyAsync(&nbits, f.nbits, 8, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(&nmax, f.nmax, 4, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(&sstat, f.status, 4, cudaMemcpyDeviceToHost, st));
-        CK(cudaMemsetAsync(&f.tl->count, 0, 8, st));
-        RC(spiht_prefix_recon(f.s, f.sig_pos, f.lsp_idx, f.refine_start, f.nbits, 0, N, es, f.R, st));
-        STAGE(st, "prefix recon");
-        RC(dwt_inverse_ex(f.R, nullptr, f.s1, f.s2, ny, nx, L, chk, 0.0, 1.0, st));
-        STAGE(st, "full check");
-        CK(cudaMemcpyAsync(&bad, &f.tl->count, 8, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (sstat) return EBCC_ECAPACITY;
-        if (bad == 0 || attempt == 2) break;
-        G += 2;
-    }
-    stt.guard_bits = G;
-    const long long len = (nbits + 7) / 8;
-    unsigned long long nesc = 0;
-    if (bad > 0) {  // last resort: exact values of the points still outside the bound
-        InvFinal st0{0, nullptr, nullptr, nullptr};
-        RC(dwt_inverse_ex(f.R, f.W, f.s1, f.s2, ny, nx, L, st0, 0.0, 1.0, st));  // R holds the full-stream residual coefs
-        PROF("escape_kernel", st, 0.0, escape_kernel<<<1, 1024, 0, st>>>(f.Abase, f.W, f.bounds, x_dev, N, f.esc, f.nesc, f.esc_cap););
-        CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(&nesc, f.nesc, 8, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (nesc > f.esc_cap) return EBCC_ECAPACITY;
-    }
-    stt.n_escape = (int)nesc;
-    // ---- binary search for the truncation point
-    PROF("tl_init", st, 0.0, tl_init<<<1, 1, 0, st>>>(f.tl, len, nbits););
-    CK(cudaGetLastError());
-    {
-        int *hdone = nullptr;
-        CK(cudaMallocHost(&hdone, 2 * sizeof(int)));
-        cudaEvent_t ev[2];
-        cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
-        cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
-        int rc = EBCC_OK;
-        int hd0 = 0;
-        CK(cudaMemcpyAsync(&hd0, &f.tl->done, 4, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        for (int step = 0; !hd0 && step < 80; step++) {
-            rc = spiht_prefix_recon(f.s, f.sig_pos, f.lsp_idx, f.refine_start, (const int64_t *)&f.tl->T, 0, N, es,
-                                    f.R, st);
-            if (!rc) rc = dwt_inverse_ex(f.R, nullptr, f.s1, f.s2, ny, nx, L, chk, 0.0, 1.0, st);
-            if (rc) break;
-            PROF("tl_update", st, 0.0, tl_update<<<1, 1, 0, st>>>(f.tl););
-            if (ebcc_debug_sync_enabled() && ebcc_stage_check(st, "trunc eval", __LINE__)) { rc = EBCC_ECUDA; break; }
-            cudaMemcpyAsync(&hdone[step & 1], &f.tl->done, 4, cudaMemcpyDeviceToHost, st);
-            cudaEventRecord(ev[step & 1], st);
-            if (step >= 1) {
-                cudaEventSynchronize(ev[(step - 1) & 1]);
-                if (hdone[(step - 1) & 1]) break;
-            }
-        }
-        cudaStreamSynchronize(st);
-        cudaEventDestroy(ev[0]);
-        cudaEventDestroy(ev[1]);
-        cudaFreeHost(hdone);
-        if (rc) return rc;
-    }
-    TruncLoop tl;
-    CK(cudaMemcpyAsync(&tl, f.tl, sizeof(tl), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    const long long t_high = tl.hi;
-    stt.iters_trunc = tl.iters;
-    stt.spiht_len_bytes = len;
-    // ---- sizes of the two candidates; the fallback (q = 1) base loop
-    unsigned long long bl2 = 0;
-    RC(pack_base_size(f, g, &f.bl->sel_f, bl2, st));  // sel_f of the q loop is still in f.bl
-    const unsigned long long len2 = HDR_BYTES + bl2 + t_high + 8 * nesc;
-    stt.len_two = (long long)len2;
-    // escaped points had their acceptance interval opened up for the
-    // truncation search; the base-only candidate is judged on the true bound
-    if (nesc) RC(make_bounds(x_dev, N, mn, range, eps_abs, guard, f.bounds, st));
-    BaseLoop b2;
-    RC(run_base_loop(f, g, 1.0, 1, p, b2, st));
-    stt.r_base1 = b2.r_f; stt.iters_base1 = b2.iters;
-    bool use_one = false;
-    unsigned long long bl1 = 0;
-    if (b2.q_f >= 1.0) {
-        RC(pack_base_size(f, g, &f.bl->sel_f, bl1, st));
-        stt.len_one = (long long)(HDR_BYTES + bl1);
-        use_one = HDR_BYTES + bl1 < len2;
-    }
-    if (use_one) {
-        if (cap < HDR_BYTES + bl1) return EBCC_ECAPACITY;
-        write_header(hh, 0, L, g.cw, g.ch, g.P, 0, -1, ny, nx, (uint32_t)bl1, 0, 0, mn, mx, eps_abs);
-        RC(pack_base_write(f, g, out + HDR_BYTES, (long long)(cap - HDR_BYTES), st));
-        CK(cudaMemcpyAsync(out, hh.b, HDR_BYTES, cudaMemcpyHostToDevice, st));
-        *out_len = HDR_BYTES + bl1;
-        stt.used_fallback = 1;
-        stt.base_bytes = (long long)bl1;
-        stt.res_bytes = 0;
-        stt.n_escape = 0;
-    } else {
-        if (cap < len2) return EBCC_ECAPACITY;
-        // restore the q-loop selection and rebuild its sizes
-        CK(cudaMemcpyAsync(&f.bl->sel_f, &sel_two, sizeof(Sel), cudaMemcpyHostToDevice, st));
-        RC(pack_base_size(f, g, &f.bl->sel_f, bl2, st));
-        int flags = (t_high > 0 ? 2 : 0) | (nesc ? 4 : 0);
-        write_header(hh, flags, L, g.cw, g.ch, g.P, es, nmax, ny, nx, (uint32_t)bl2, (uint32_t)t_high,
-                     (uint32_t)nesc, mn, mx, eps_abs);
-        RC(pack_base_write(f, g, out + HDR_BYTES, (long long)(cap - HDR_BYTES), st));
-        if (t_high > 0)
-            CK(cudaMemcpyAsync(out + HDR_BYTES + bl2, f.sp_stream, t_high, cudaMemcpyDeviceToDevice, st));
-        if (nesc)
-            CK(cudaMemcpyAsync(out + HDR_BYTES + bl2 + t_high, f.esc, 8 * nesc, cudaMemcpyDeviceToDevice, st));
-        CK(cudaMemcpyAsync(out, hh.b, HDR_BYTES, cudaMemcpyHostToDevice, st));
-        *out_len = len2;
-        stt.base_bytes = (long long)bl2;
-        stt.res_bytes = t_high;
-    }
-    CK(cudaStreamSynchronize(st));
-    stt.total_bytes = (long long)*out_len;
-    if (st_out) *st_out = stt;
-    return EBCC_OK;
+    memcpy(h + 12, u, 20);
+    memcpy(h + 32, &mn, 8);
+    memcpy(h + 40, &mx, 8);
+    memcpy(h + 48, &eps, 8);
 }
 
 struct ParsedHeader {
@@ -740,126 +768,666 @@ int parse_header(const uint8_t *h, size_t len, ParsedHeader &o) {
     return EBCC_OK;
 }
 
-__global__ void fill_kernel(float *o, size_t n, float v) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) o[i] = v;
-}
-
-// decompress a device stream (whose header is already parsed) into out
-int decompress_field(const uint8_t *s_dev, size_t len, const ParsedHeader &h, float *out, Arena &a, cudaStream_t st) {
-    const size_t N = (size_t)h.ny * h.nx;
-    if (h.flags & 1) {
-        PROF("fill_kernel", st, 0.0, fill_kernel<<<152 * 4, 256, 0, st>>>(out, N, (float)h.mn););
-        CK(cudaGetLastError());
-        return EBCC_OK;
-    }
-    FieldGeom g;
-    make_geom(&g, h.ny, h.nx, h.L, h.cw, h.ch, h.P);
-    std::vector<BlockDesc> blk;
-    make_blocks(g, blk);
-    const size_t nb = g.nblocks;
-    size_t q = scratch1(h.ny, h.nx), q2 = scratch2(h.ny, h.nx);
-    size_t need = N * 4 * 3 + (q + q2) * 4 + nb * (sizeof(BlockDesc) + 4 * 3 + 8) + N * 6 +
-                  spiht_work_bytes(N) + 64 * 256;
-    RC(arena_reserve(a, need));
-    float *W = carve<float>(a, N), *Ab = carve<float>(a, N), *Wr = carve<float>(a, N);
-    float *s1 = carve<float>(a, q), *s2 = carve<float>(a, q2);
-    BlockDesc *bd = carve<BlockDesc>(a, nb);
-    int32_t *np = carve<int32_t>(a, nb), *K = carve<int32_t>(a, nb), *bl = carve<int32_t>(a, nb);
-    int64_t *off = carve<int64_t>(a, nb);
-    int32_t *mag = carve<int32_t>(a, N);
-    int8_t *plane = carve<int8_t>(a, N);
-    uint8_t *neg = carve<uint8_t>(a, N);
-    uint8_t *spw = carve<uint8_t>(a, spiht_work_bytes(N));
-    int *ok = carve<int>(a, 4);
-    SpihtWork sw;
-    spiht_work_carve(spw, N, &sw);
-    CK(cudaMemcpyAsync(bd, blk.data(), nb * sizeof(BlockDesc), cudaMemcpyHostToDevice, st));
-    PROF("base_parse", st, 0.0, base_parse<<<1, 1, 0, st>>>(s_dev, HDR_BYTES, h.bl, (int)nb, np, K, bl, off, ok););
-    CK(cudaGetLastError());
-    int hok = 0;
-    CK(cudaMemcpyAsync(&hok, ok, 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (!hok) return EBCC_ECORRUPT;
-    RC(t1_decode_blocks(s_dev, off, bl, bd, K, np, (int)nb, g.cw, g.ch, W, nullptr, nullptr, nullptr, (long long)N,
-                         st));
-    const double range = h.mx - h.mn;
-    if ((h.flags & 2) && h.rl > 0) {
-        InvFinal store{0, nullptr, nullptr, nullptr};
-        RC(dwt_inverse_ex(W, Ab, s1, s2, h.ny, h.nx, g.L, store, 0.0, 1.0, st));
-        RC(spiht_decode(s_dev + HDR_BYTES + h.bl, 8ll * h.rl, h.ny, h.nx, g.L, h.nmax, mag, plane, neg, Wr, h.es, sw,
-                        st));
-        InvFinal fin{3, nullptr, Ab, nullptr};
-        RC(dwt_inverse_ex(Wr, out, s1, s2, h.ny, h.nx, g.L, fin, h.mn, range, st));
-    } else {
-        InvFinal fin{3, nullptr, nullptr, nullptr};
-        RC(dwt_inverse_ex(W, out, s1, s2, h.ny, h.nx, g.L, fin, h.mn, range, st));
-    }
-    if (h.ne) {
-        CK(cudaMemsetAsync(ok, 0xFF, 4, st));
-        PROF("scatter_escapes", st, 0.0, scatter_escapes<<<64, 256, 0, st>>>(s_dev + HDR_BYTES + h.bl + h.rl, h.ne, out, (long long)N, ok););
-        CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(&hok, ok, 4, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (hok != -1) return EBCC_ECORRUPT;
-    }
-    return EBCC_OK;
-}
-
-std::mutex g_mu;
-Arena g_arena, g_dec_arena;
-
 int check_shape(size_t ny, size_t nx) {
     if (ny == 0 || nx == 0 || ny > (1u << 30) || nx > (1u << 30) || ny * nx >= 0x7FFFFFFFull) return EBCC_EINVAL;
     return EBCC_OK;
 }
 
-int compress_with(Arena &arena, const float *x_dev, size_t ny, size_t nx, double bound, int kind,
-                  const ebcc_params &p, uint8_t *out_dev, size_t cap, size_t *len, ebcc_stats *stats, cudaStream_t st,
-                  bool copy_input) {
-    FieldGeom g;
-    make_geom(&g, (int)ny, (int)nx, p.levels, p.cblk_w, p.cblk_h, 16);
-    const int cap_blk = 6 * p.cblk_w * p.cblk_h + 64;
-    RC(arena_reserve(arena, field_bytes(g, cap_blk)));
-    FieldBufs f;
-    carve_field(arena, g, cap_blk, f);
-    const float *x = x_dev;
-    if (copy_input) {
-        CK(cudaMemcpyAsync(f.x, x_dev, ny * nx * sizeof(float), cudaMemcpyHostToDevice, st));
-        x = f.x;
+// ------------------------------------------------------------ the two loops
+// Algorithm 1's base loop for the table entries in A (q, or q = 1 with the
+// fallback's upward condition); the final states are left in b.bl
+int run_base_loop(Engine &e, Batch &b, const std::vector<int> &A, double q, int fallback, const ebcc_params &p,
+                  cudaStream_t st) {
+    const int n = (int)A.size();
+    if (!n) return EBCC_OK;
+    RC(upload(e, b.list, A.data(), n * sizeof(int), st));
+    bl_start<<<(n + 255) / 256, 256, 0, st>>>(b.bl, b.d_run, b.list, n, q, fallback, p.r0, p.tol, b.hull, b.live);
+    CK(cudaGetLastError());
+    int *slot = stage_take<int>(e, 2);
+    if (!slot) return EBCC_ECAPACITY;
+    const Live lv = live_of(b);
+    const InvFinal fin{1, 0, 0, 0};
+    const Sel *sel = &b.bl[0].sel_eval;
+    int hn = n, rc = EBCC_OK;
+    for (int step = 0; step < 400; step++) {
+        rc = pcrd_npass_b(lv, kNone, hn, b.dims.maxnblk, b.hull, sel, sizeof(BaseLoop), b.npass, st);
+        if (!rc) rc = base_recon_b(lv, kNone, hn, b.dims.maxN, b.t1.K, b.npass, st);
+        if (!rc) rc = dwt_inverse_b(lv, kNone, hn, b.dims, PL_W, fin, st);
+        if (rc) break;
+        PROF("bl_update", st, 0.0, bl_update<<<1, 1024, 0, st>>>(b.bl, b.d_run, b.hull, b.live));
+        if (ebcc_debug_sync_enabled() && ebcc_stage_check(st, "base eval", __LINE__)) { rc = EBCC_ECUDA; break; }
+        if (cudaMemcpyAsync(&slot[step & 1], b.live, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaEventRecord(e.ev[step & 1], st) != cudaSuccess) { rc = EBCC_ECUDA; break; }
+        if (step >= 1) {
+            if (cudaEventSynchronize(e.ev[(step - 1) & 1]) != cudaSuccess) { rc = EBCC_ECUDA; break; }
+            hn = slot[(step - 1) & 1];
+            if (hn <= 0) break;
+        }
     }
-    return compress_field(f, x, (int)ny, (int)nx, bound, kind, p, out_dev, cap, len, stats, st);
+    if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = EBCC_ECUDA;
+    return rc;
 }
 
-int compress_dev_locked(const float *x_dev, size_t ny, size_t nx, double bound, int kind, const ebcc_params &p,
-                        uint8_t *out_dev, size_t cap, size_t *len, ebcc_stats *stats, cudaStream_t st,
-                        bool copy_input) {
-    return compress_with(g_arena, x_dev, ny, nx, bound, kind, p, out_dev, cap, len, stats, st, copy_input);
+// truncation bisection for the table entries in A; final states in b.tl
+int run_trunc_loop(Engine &e, Batch &b, const std::vector<int> &A, cudaStream_t st) {
+    const int n = (int)A.size();
+    if (!n) return EBCC_OK;
+    RC(set_list(e, b, A, st));
+    tl_start<<<1, 1024, 0, st>>>(b.tl, b.d_run, b.live);
+    CK(cudaGetLastError());
+    int *slot = stage_take<int>(e, 2);
+    if (!slot) return EBCC_ECAPACITY;
+    int *h0 = nullptr;
+    RC(download(e, b.live, 1, &h0, st));
+    const Live lv = live_of(b);
+    const InvFinal fin{2, 0, 0, 1};
+    int hn = *h0, rc = EBCC_OK;
+    for (int step = 0; hn > 0 && step < 200; step++) {
+        rc = spiht_prefix_recon_b(lv, kNone, hn, b.dims.maxN, 1, st);
+        if (!rc) rc = dwt_inverse_b(lv, kNone, hn, b.dims, PL_R, fin, st);
+        if (rc) break;
+        PROF("tl_update", st, 0.0, tl_update<<<1, 1024, 0, st>>>(b.tl, b.d_run, b.live));
+        if (ebcc_debug_sync_enabled() && ebcc_stage_check(st, "trunc eval", __LINE__)) { rc = EBCC_ECUDA; break; }
+        if (cudaMemcpyAsync(&slot[step & 1], b.live, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaEventRecord(e.ev[step & 1], st) != cudaSuccess) { rc = EBCC_ECUDA; break; }
+        if (step >= 1) {
+            if (cudaEventSynchronize(e.ev[(step - 1) & 1]) != cudaSuccess) { rc = EBCC_ECUDA; break; }
+            hn = slot[(step - 1) & 1];
+        }
+    }
+    if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = EBCC_ECUDA;
+    return rc;
+}
+
+// base-section sizes (sc->tot) of the fields in L for the selections sel
+// (stride bytes apart, by table index)
+int base_sizes_for(Engine &e, Batch &b, const std::vector<int> &L, const void *sel, size_t stride, cudaStream_t st) {
+    if (L.empty()) return EBCC_OK;
+    RC(set_list(e, b, L, st));
+    const Live lv = live_of(b);
+    RC(pcrd_npass_b(lv, kNone, (int)L.size(), b.dims.maxnblk, b.hull, sel, stride, b.npass, st));
+    PROF("base_sizes", st, 0.0, base_sizes<<<(int)L.size(), 1024, 0, st>>>(lv, b.npass, b.t1.pass_len, b.meta_off, b.pay_off));
+    CK(cudaGetLastError());
+    return EBCC_OK;
+}
+
+void remove_from(std::vector<int> &v, const std::vector<char> &drop) {
+    std::vector<int> o;
+    for (int f : v)
+        if (!drop[f]) o.push_back(f);
+    v.swap(o);
+}
+
+// ------------------------------------------------------------ compression
+// Algorithm 1 on the fields fd[0..n-1] (device pointers) into their outputs.
+// Per-field outcomes in od[i]; the return value reports whole-batch failures.
+int compress_batch(Engine &e, const ebcc_field_desc *fd, int n, ebcc_out_desc *od, const ebcc_params &p,
+                   cudaStream_t st) {
+    std::vector<int> vin;  // table entry -> input index
+    for (int i = 0; i < n; i++) {
+        memset(&od[i].stats, 0, sizeof(ebcc_stats));
+        od[i].len = 0;
+        int rc = check_shape(fd[i].ny, fd[i].nx);
+        if (!rc && (!(fd[i].bound > 0) || !isfinite(fd[i].bound) || (fd[i].bound_kind != 0 && fd[i].bound_kind != 1) ||
+                    !fd[i].field || !od[i].stream))
+            rc = EBCC_EINVAL;
+        od[i].status = rc;
+        if (!rc) vin.push_back(i);
+    }
+    const int F = (int)vin.size();
+    if (!F) return EBCC_OK;
+    const int cw = p.cblk_w, ch = p.cblk_h;
+    std::vector<int> ny(F), nx(F), L(F), nblk(F);
+    for (int f = 0; f < F; f++) {
+        ny[f] = (int)fd[vin[f]].ny; nx[f] = (int)fd[vin[f]].nx;
+        FieldGeom g;
+        make_geom(&g, ny[f], nx[f], p.levels, cw, ch, 16);
+        L[f] = g.L; nblk[f] = g.nblocks;
+    }
+    const int cap_blk = 6 * cw * ch + 64;
+    Batch b;
+    {
+        Arena dry;
+        layout_compress(dry, b, ny, nx, L, nblk, cap_blk);
+        RC(arena_reserve(e.a, dry.used + 4096));
+    }
+    layout_compress(e.a, b, ny, nx, L, nblk, cap_blk);
+    RC(engine_begin(e, stage_bytes_for(F, b.Btot)));
+    std::vector<int> status(F, EBCC_OK);
+    for (int f = 0; f < F; f++) {
+        b.run[f].x = fd[vin[f]].field;
+        b.run[f].out = od[vin[f]].stream;
+        b.run[f].out_cap = (long long)od[vin[f]].capacity;
+    }
+    // ---- min / max / finiteness of every field (Materials and Methods: min-max normalisation)
+    BatchDims all;
+    batch_dims_init(all);
+    for (int f = 0; f < F; f++) batch_dims_add(all, ny[f], nx[f], L[f], nblk[f]);
+    b.dims = all;
+    RC(upload(e, b.d_run, b.run.data(), F * sizeof(FieldRun), st));
+    CK(cudaMemsetAsync(b.d_sc, 0, F * sizeof(FieldScal), st));
+    std::vector<int> every(F);
+    for (int f = 0; f < F; f++) every[f] = f;
+    RC(set_list(e, b, every, st));
+    RC(minmax_b(live_of(b), kNone, F, all.maxN, st));
+    FieldScal *hs = nullptr;
+    RC(download(e, b.d_sc, F, &hs, st));
+    // ---- per-field geometry: trivial fields (constant, or a bound above the
+    // range) become a header; the others take part in Algorithm 1
+    std::vector<int> A, T;
+    std::vector<double> mn(F), mx(F), eps(F), eps_n(F);
+    std::vector<int> P(F, 0);
+    b.geom.assign(F, FieldGeom{});
+    b.blk.clear();
+    const int32_t *qt0 = b.run[0].qt;
+    int blk0 = 0;
+    batch_dims_init(b.dims);
+    for (int f = 0; f < F; f++) {
+        const ebcc_field_desc &d = fd[vin[f]];
+        if (hs[f].nonfinite) { status[f] = EBCC_ENONFINITE; continue; }
+        mn[f] = hs[f].mm[0]; mx[f] = hs[f].mm[1];
+        const double range = mx[f] - mn[f];
+        eps[f] = d.bound_kind == EBCC_BOUND_REL ? d.bound * range : d.bound;
+        FieldRun &r = b.run[f];
+        r.mn = mn[f]; r.range = range;
+        if (range == 0 || eps[f] >= range) { T.push_back(f); continue; }
+        eps_n[f] = eps[f] / range;
+        double guard = ldexp(range, -17);
+        if (guard > 0.25 * eps[f]) guard = 0.25 * eps[f];
+        P[f] = base_precision(eps_n[f]);
+        make_geom(&b.geom[f], ny[f], nx[f], p.levels, cw, ch, P[f]);
+        std::vector<BlockDesc> bd;
+        make_blocks(b.geom[f], bd);
+        const long long base = (long long)(r.qt - qt0);
+        for (BlockDesc &x : bd) { x.off += base; b.blk.push_back(x); }
+        r.inv_range = 1.0 / range;
+        r.E = eps[f] - guard;
+        r.blk0 = blk0;
+        r.nblk = b.geom[f].nblocks;
+        blk0 += r.nblk;
+        A.push_back(f);
+        batch_dims_add(b.dims, ny[f], nx[f], L[f], r.nblk);
+    }
+    const int Bact = blk0;
+    RC(upload(e, b.d_run, b.run.data(), F * sizeof(FieldRun), st));
+    RC(upload(e, b.d_geom, b.geom.data(), F * sizeof(FieldGeom), st));
+    RC(upload(e, b.d_blk, b.blk.data(), b.blk.size() * sizeof(BlockDesc), st));
+    std::vector<BaseLoop> hb1(F), hb2(F);
+    std::vector<TruncLoop> htl(F);
+    std::vector<int> G(F, p.spiht_guard_bits), esv(F, 0), nmaxv(F, -1);
+    std::vector<long long> nbitsv(F, 0), bl2(F, 0), bl1(F, 0), len2(F, 0);
+    std::vector<unsigned long long> bad(F, 0), nesc(F, 0);
+    std::vector<char> use_one(F, 0), drop(F, 0);
+    std::vector<Sel> sel_two(F), sel_fin(F);
+    if (!A.empty()) {
+        const int na = (int)A.size();
+        RC(set_list(e, b, A, st));
+        Live lv = live_of(b);
+        // ---- per-point acceptance intervals of the bound test (FP64, once)
+        RC(make_bounds_b(lv, kNone, na, b.dims.maxN, st));
+        // ---- base layer: DWT of the normalised field, quantise, tier-1, hulls
+        RC(dwt_forward_b(lv, kNone, na, b.dims, PL_X, 1, st));
+        RC(quantise_b(lv, kNone, na, b.dims.maxN, 1, st));
+        STAGE(st, "quantise");
+        CK(cudaMemsetAsync(b.t1.status, 0, 4, st));
+        RC(t1_encode_blocks(b.run[0].qt, b.d_blk, Bact, cw, ch, b.t1, 1, nullptr, b.Ntot, st));
+        STAGE(st, "tier-1");
+        RC(pcrd_hulls(b.t1.npass, b.t1.pass_len, b.t1.dD, b.t1.D0, Bact, T1_MAXPASS, b.hull, st));
+        RC(pcrd_prepare_b(lv, kNone, na, b.hull, st));
+        STAGE(st, "hulls");
+        // ---- base loop with q
+        RC(run_base_loop(e, b, A, p.q, 0, p, st));
+        BaseLoop *hb = nullptr;
+        RC(download(e, b.bl, F, &hb, st));
+        for (int f : A) hb1[f] = hb[f];
+        int32_t *t1st = nullptr;
+        RC(download(e, b.t1.status, 1, &t1st, st));
+        if (*t1st) {
+            for (int f : A) status[f] = EBCC_ECAPACITY;
+            A.clear();
+        }
+        for (int f : A)
+            if (!hb1[f].done) { status[f] = EBCC_ETIMEOUT; drop[f] = 1; }
+        remove_from(A, drop);
+    }
+    if (!A.empty()) {
+        const int na = (int)A.size();
+        RC(set_list(e, b, A, st));
+        Live lv = live_of(b);
+        // ---- A_base = dec_base(e_f), the residue in FP64, its DWT
+        RC(pcrd_npass_b(lv, kNone, na, b.dims.maxnblk, b.hull, &b.bl[0].sel_f, sizeof(BaseLoop), b.npass, st));
+        RC(base_recon_b(lv, kNone, na, b.dims.maxN, b.t1.K, b.npass, st));
+        RC(dwt_inverse_b(lv, kNone, na, b.dims, PL_W, InvFinal{0, 0, PL_ABASE, 0}, st));
+        RC(residue_b(lv, kNone, na, b.dims.maxN, st));
+        RC(dwt_forward_b(lv, kNone, na, b.dims, PL_R, 0, st));
+        STAGE(st, "residue dwt");
+        for (int f : A) sel_two[f] = hb1[f].sel_f;
+        // ---- SPIHT with guard retries: step 2^(floor(log2 eps_n) - G)
+        std::vector<int> S = A;
+        for (int attempt = 0; attempt < 3 && !S.empty(); attempt++) {
+            for (int f : S) esv[f] = (int)floor(log2(eps_n[f])) - G[f];
+            RC(upload(e, b.es, esv.data(), F * sizeof(int), st));
+            RC(set_list(e, b, S, st));
+            const int ns = (int)S.size();
+            set_scalars<<<(ns + 255) / 256, 256, 0, st>>>(lv, b.es, 1);
+            CK(cudaGetLastError());
+            RC(spiht_quantise_b(lv, kNone, ns, b.dims.maxN, st));
+            RC(spiht_encode_b(lv, kNone, ns, b.dims, st));
+            STAGE(st, "spiht encode");
+            RC(spiht_prefix_recon_b(lv, kNone, ns, b.dims.maxN, 0, st));
+            RC(dwt_inverse_b(lv, kNone, ns, b.dims, PL_R, InvFinal{2, 0, 0, 1}, st));
+            RC(download(e, b.d_sc, F, &hs, st));
+            std::vector<int> again;
+            for (int f : S) {
+                if (hs[f].spiht_status) { status[f] = EBCC_ECAPACITY; drop[f] = 1; continue; }
+                nbitsv[f] = hs[f].nbits;
+                nmaxv[f] = hs[f].nmax;
+                bad[f] = hs[f].cnt[1];
+                if (bad[f] > 0 && attempt < 2) { G[f] += 2; again.push_back(f); }
+            }
+            S.swap(again);
+        }
+        remove_from(A, drop);
+    }
+    std::vector<int> X;  // fields with escapes
+    if (!A.empty()) {
+        for (int f : A)
+            if (bad[f] > 0) X.push_back(f);
+        if (!X.empty()) {  // last resort: exact values of the points still outside the bound
+            RC(set_list(e, b, X, st));
+            Live lv = live_of(b);
+            RC(dwt_inverse_b(lv, kNone, (int)X.size(), b.dims, PL_R, InvFinal{0, 0, PL_W, 0}, st));
+            PROF("escape_kernel", st, 0.0, escape_kernel<<<(int)X.size(), 1024, 0, st>>>(lv));
+            CK(cudaGetLastError());
+            RC(download(e, b.d_sc, F, &hs, st));
+            for (int f : X) {
+                nesc[f] = hs[f].nesc;
+                if (nesc[f] > (unsigned long long)b.run[f].esc_cap) { status[f] = EBCC_ECAPACITY; drop[f] = 1; }
+            }
+            remove_from(A, drop);
+            remove_from(X, drop);
+        }
+    }
+    if (!A.empty()) {
+        // ---- binary search for the truncation point
+        RC(run_trunc_loop(e, b, A, st));
+        TruncLoop *ht = nullptr;
+        RC(download(e, b.tl, F, &ht, st));
+        for (int f : A) htl[f] = ht[f];
+        // ---- sizes of the two-layer candidates
+        RC(base_sizes_for(e, b, A, &b.bl[0].sel_f, sizeof(BaseLoop), st));
+        RC(download(e, b.d_sc, F, &hs, st));
+        for (int f : A) {
+            bl2[f] = (long long)(hs[f].tot[0] + hs[f].tot[1]);
+            len2[f] = HDR_BYTES + bl2[f] + htl[f].hi + 8 * (long long)nesc[f];
+        }
+        // escaped points had their acceptance interval opened up for the
+        // truncation search; the base-only candidate is judged on the true bound
+        if (!X.empty()) {
+            RC(set_list(e, b, X, st));
+            RC(make_bounds_b(live_of(b), kNone, (int)X.size(), b.dims.maxN, st));
+        }
+        // ---- the fallback (q = 1) base loop
+        RC(run_base_loop(e, b, A, 1.0, 1, p, st));
+        BaseLoop *hb = nullptr;
+        RC(download(e, b.bl, F, &hb, st));
+        std::vector<int> O;
+        for (int f : A) {
+            hb2[f] = hb[f];
+            if (hb2[f].done && hb2[f].q_f >= 1.0) O.push_back(f);
+        }
+        RC(base_sizes_for(e, b, O, &b.bl[0].sel_f, sizeof(BaseLoop), st));
+        if (!O.empty()) RC(download(e, b.d_sc, F, &hs, st));
+        for (int f : O) {
+            bl1[f] = (long long)(hs[f].tot[0] + hs[f].tot[1]);
+            use_one[f] = HDR_BYTES + bl1[f] < len2[f];
+        }
+        for (int f : A) {
+            sel_fin[f] = use_one[f] ? hb2[f].sel_f : sel_two[f];
+            const long long total = use_one[f] ? HDR_BYTES + bl1[f] : len2[f];
+            if (total > b.run[f].out_cap) { status[f] = EBCC_ECAPACITY; drop[f] = 1; }
+        }
+        remove_from(A, drop);
+    }
+    // ---- write the streams: base sections, then residual bytes, escapes, headers
+    std::vector<PackPlan> plan(F);
+    memset(plan.data(), 0, F * sizeof(PackPlan));
+    std::vector<int> Wl;
+    if (!A.empty()) {
+        RC(upload(e, b.sel, sel_fin.data(), F * sizeof(Sel), st));
+        RC(base_sizes_for(e, b, A, b.sel, sizeof(Sel), st));
+        const Live lv = live_of(b);
+        dim3 grid(cgrid((long long)b.dims.maxnblk * 32, (int)A.size()), (unsigned)A.size());
+        PROF("base_write", st, 0.0, base_write<<<grid, 256, 0, st>>>(lv, b.t1, b.npass, b.meta_off, b.pay_off));
+        CK(cudaGetLastError());
+        for (int f : A) {
+            PackPlan &pl = plan[f];
+            const FieldGeom &g = b.geom[f];
+            if (use_one[f]) {
+                write_header(pl.hdr, 0, g.L, cw, ch, g.P, 0, -1, ny[f], nx[f], (uint32_t)bl1[f], 0, 0, mn[f], mx[f], eps[f]);
+                pl.base_len = bl1[f];
+            } else {
+                const long long th = htl[f].hi;
+                const int flags = (th > 0 ? 2 : 0) | (nesc[f] ? 4 : 0);
+                write_header(pl.hdr, flags, g.L, cw, ch, g.P, esv[f], nmaxv[f], ny[f], nx[f], (uint32_t)bl2[f],
+                             (uint32_t)th, (uint32_t)nesc[f], mn[f], mx[f], eps[f]);
+                pl.base_len = bl2[f];
+                pl.res_len = th;
+                pl.n_esc = (long long)nesc[f];
+            }
+            pl.write_hdr = 1;
+            Wl.push_back(f);
+        }
+    }
+    for (int f : T) {
+        if (b.run[f].out_cap < HDR_BYTES) { status[f] = EBCC_ECAPACITY; continue; }
+        const double range = mx[f] - mn[f];
+        const double fill = range == 0 ? mn[f] : mn[f] + 0.5 * range;
+        write_header(plan[f].hdr, 1, 0, cw, ch, 0, 0, -1, ny[f], nx[f], 0, 0, 0, fill, mx[f], eps[f]);
+        plan[f].write_hdr = 1;
+        Wl.push_back(f);
+    }
+    if (!Wl.empty()) {
+        RC(upload(e, b.plan, plan.data(), F * sizeof(PackPlan), st));
+        RC(set_list(e, b, Wl, st));
+        long long mx_tail = HDR_BYTES;
+        for (int f : Wl) mx_tail = std::max(mx_tail, plan[f].res_len + 8 * plan[f].n_esc);
+        dim3 grid(cgrid(mx_tail, (int)Wl.size()), (unsigned)Wl.size());
+        PROF("pack_tail", st, 0.0, pack_tail<<<grid, 256, 0, st>>>(live_of(b), b.plan));
+        CK(cudaGetLastError());
+    }
+    CK(cudaStreamSynchronize(st));
+    // ---- outcomes
+    for (int f = 0; f < F; f++) {
+        ebcc_out_desc &o = od[vin[f]];
+        o.status = status[f];
+        if (status[f]) continue;
+        ebcc_stats &s = o.stats;
+        const bool trivial = std::find(T.begin(), T.end(), f) != T.end();
+        if (trivial) {
+            o.len = HDR_BYTES;
+            s.total_bytes = HDR_BYTES;
+            continue;
+        }
+        s.r_base = hb1[f].r_f; s.iters_base = hb1[f].iters; s.q_base = hb1[f].q_f;
+        s.r_base1 = hb2[f].r_f; s.iters_base1 = hb2[f].iters;
+        s.iters_trunc = htl[f].iters;
+        s.guard_bits = G[f];
+        s.spiht_len_bytes = (nbitsv[f] + 7) / 8;
+        s.len_two = len2[f];
+        s.len_one = (hb2[f].done && hb2[f].q_f >= 1.0) ? HDR_BYTES + bl1[f] : 0;
+        s.used_fallback = use_one[f];
+        if (use_one[f]) {
+            s.base_bytes = bl1[f]; s.res_bytes = 0; s.n_escape = 0;
+            o.len = (size_t)(HDR_BYTES + bl1[f]);
+        } else {
+            s.base_bytes = bl2[f]; s.res_bytes = htl[f].hi; s.n_escape = (int)nesc[f];
+            o.len = (size_t)len2[f];
+        }
+        s.total_bytes = (long long)o.len;
+    }
+    return EBCC_OK;
+}
+
+// ------------------------------------------------------------ decompression
+// decode streams sd[0..n-1] (device) into outs[i] (device, ny*nx float32);
+// per-stream status in status[i]
+int decompress_batch(Engine &e, const ebcc_stream_desc *sd, int n, float *const *outs, int *status,
+                     cudaStream_t st) {
+    for (int i = 0; i < n; i++) {
+        status[i] = EBCC_OK;
+        if (!sd[i].stream || !outs[i] || check_shape(sd[i].ny, sd[i].nx)) status[i] = EBCC_EINVAL;
+        else if (sd[i].len < HDR_BYTES) status[i] = EBCC_ECORRUPT;
+    }
+    // headers: gather every stream's first 64 bytes into one download
+    RC(engine_begin(e, stage_bytes_for(n, 0) + (size_t)n * (HDR_BYTES + 32)));
+    {
+        size_t need = (size_t)n * (HDR_BYTES + 16) + 1024;
+        RC(arena_reserve(e.a, need));
+    }
+    const uint8_t **hp = stage_take<const uint8_t *>(e, n);
+    long long *hl = stage_take<long long>(e, n);
+    if (!hp || !hl) return EBCC_ECAPACITY;
+    for (int i = 0; i < n; i++) {
+        hp[i] = status[i] ? nullptr : sd[i].stream;
+        hl[i] = status[i] ? 0 : (long long)sd[i].len;
+    }
+    {
+        const uint8_t **dp = carve<const uint8_t *>(e.a, n);
+        long long *dl = carve<long long>(e.a, n);
+        uint8_t *dh = carve<uint8_t>(e.a, (size_t)n * HDR_BYTES);
+        CK(cudaMemcpyAsync(dp, hp, n * sizeof(void *), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(dl, hl, n * sizeof(long long), cudaMemcpyHostToDevice, st));
+        hdr_gather<<<n, 64, 0, st>>>(dp, dl, n, dh);
+        CK(cudaGetLastError());
+        uint8_t *hh = nullptr;
+        RC(download(e, dh, (size_t)n * HDR_BYTES, &hh, st));
+        std::vector<ParsedHeader> H(n);
+        std::vector<int> vin;
+        for (int i = 0; i < n; i++) {
+            if (status[i]) continue;
+            ParsedHeader &h = H[i];
+            int rc = parse_header(hh + (size_t)i * HDR_BYTES, sd[i].len, h);
+            if (!rc && ((size_t)h.ny != sd[i].ny || (size_t)h.nx != sd[i].nx)) rc = EBCC_EINVAL;
+            status[i] = rc;
+            if (!rc) vin.push_back(i);
+        }
+        const int F = (int)vin.size();
+        if (!F) return EBCC_OK;
+        std::vector<int> ny(F), nx(F), nblk(F, 0);
+        Batch b;
+        b.geom.assign(F, FieldGeom{});
+        for (int f = 0; f < F; f++) {
+            const ParsedHeader &h = H[vin[f]];
+            ny[f] = h.ny; nx[f] = h.nx;
+            if (!(h.flags & 1)) {
+                make_geom(&b.geom[f], h.ny, h.nx, h.L, h.cw, h.ch, h.P);
+                nblk[f] = b.geom[f].nblocks;
+            }
+        }
+        {
+            Arena dry;
+            layout_decompress(dry, b, ny, nx, nblk);
+            RC(arena_reserve(e.a, dry.used + 4096));
+        }
+        layout_decompress(e.a, b, ny, nx, nblk);
+        RC(engine_begin(e, stage_bytes_for(F, b.Btot)));
+        std::vector<FieldScal> sc(F);
+        memset(sc.data(), 0, F * sizeof(FieldScal));
+        std::vector<int> D, T, B1, B2, E;
+        const float *W0 = b.run[0].W;
+        int blk0 = 0, maxw = 4, maxh = 4;
+        batch_dims_init(b.dims);
+        b.blk.clear();
+        for (int f = 0; f < F; f++) {
+            const ParsedHeader &h = H[vin[f]];
+            FieldRun &r = b.run[f];
+            r.in = sd[vin[f]].stream;
+            r.in_len = (long long)sd[vin[f]].len;
+            r.dst = outs[vin[f]];
+            r.mn = h.mn;
+            r.range = h.mx - h.mn;
+            if (h.flags & 1) { T.push_back(f); continue; }
+            r.L = h.L;
+            r.base_len = h.bl; r.res_len = h.rl; r.n_esc = h.ne;
+            r.sp = const_cast<uint8_t *>(r.in) + HDR_BYTES + h.bl;
+            r.blk0 = blk0;
+            r.nblk = nblk[f];
+            blk0 += nblk[f];
+            std::vector<BlockDesc> bd;
+            make_blocks(b.geom[f], bd);
+            const long long base = (long long)(r.W - W0);
+            for (BlockDesc &x : bd) { x.off += base; b.blk.push_back(x); }
+            maxw = std::max(maxw, h.cw);
+            maxh = std::max(maxh, h.ch);
+            sc[f].nbits = 8LL * h.rl;
+            sc[f].nmax = h.nmax;
+            sc[f].es = h.es;
+            batch_dims_add(b.dims, h.ny, h.nx, h.L, nblk[f]);
+            D.push_back(f);
+            if ((h.flags & 2) && h.rl > 0) B2.push_back(f); else B1.push_back(f);
+            if (h.ne) E.push_back(f);
+        }
+        for (int f : T) batch_dims_add(b.dims, ny[f], nx[f], 0, 0);
+        RC(upload(e, b.d_run, b.run.data(), F * sizeof(FieldRun), st));
+        RC(upload(e, b.d_geom, b.geom.data(), F * sizeof(FieldGeom), st));
+        RC(upload(e, b.d_sc, sc.data(), F * sizeof(FieldScal), st));
+        RC(upload(e, b.d_blk, b.blk.data(), b.blk.size() * sizeof(BlockDesc), st));
+        const Live lv = live_of(b);
+        std::vector<char> bad(F, 0);
+        if (!D.empty()) {
+            RC(set_list(e, b, D, st));
+            PROF("base_parse", st, 0.0, base_parse<<<(int)D.size(), 32, 0, st>>>(lv, b.npass, b.t1.K, b.t1.pass_len, b.addr));
+            CK(cudaGetLastError());
+            FieldScal *hs = nullptr;
+            RC(download(e, b.d_sc, F, &hs, st));
+            for (int f : D)
+                if (!hs[f].ok) { status[vin[f]] = EBCC_ECORRUPT; bad[f] = 1; }
+            remove_from(D, bad);
+            remove_from(B1, bad);
+            remove_from(B2, bad);
+            remove_from(E, bad);
+            // tier-1 of every code-block of the batch (failed fields decode nothing)
+            RC(t1_decode_blocks(nullptr, b.addr, b.t1.pass_len, b.d_blk, b.t1.K, b.npass, blk0, maxw, maxh,
+                                b.run[0].W, nullptr, nullptr, nullptr, b.Ntot, st));
+            STAGE(st, "tier-1 decode");
+        }
+        if (!B1.empty()) {  // base layer only: IDWT, denormalise
+            RC(set_list(e, b, B1, st));
+            RC(dwt_inverse_b(lv, kNone, (int)B1.size(), b.dims, PL_W, InvFinal{3, 0, PL_DST, 0}, st));
+        }
+        if (!B2.empty()) {  // A_base + IDWT(SPIHT decode), denormalised
+            RC(set_list(e, b, B2, st));
+            const int n2 = (int)B2.size();
+            RC(dwt_inverse_b(lv, kNone, n2, b.dims, PL_W, InvFinal{0, 0, PL_ABASE, 0}, st));
+            RC(spiht_decode_b(lv, kNone, n2, b.dims.maxN, 1, st));
+            RC(dwt_inverse_b(lv, kNone, n2, b.dims, PL_R, InvFinal{3, 1, PL_DST, 0}, st));
+        }
+        if (!E.empty()) {
+            RC(set_list(e, b, E, st));
+            long long mx_e = 1;
+            for (int f : E) mx_e = std::max(mx_e, b.run[f].n_esc);
+            dim3 grid(cgrid(mx_e, (int)E.size()), (unsigned)E.size());
+            PROF("scatter_escapes", st, 0.0, scatter_escapes<<<grid, 256, 0, st>>>(lv));
+            CK(cudaGetLastError());
+        }
+        if (!T.empty()) {
+            RC(set_list(e, b, T, st));
+            dim3 grid(cgrid(b.dims.maxN, (int)T.size()), (unsigned)T.size());
+            PROF("fill_kernel", st, 0.0, fill_kernel<<<grid, 256, 0, st>>>(lv));
+            CK(cudaGetLastError());
+        }
+        if (!E.empty()) {
+            FieldScal *hs = nullptr;
+            RC(download(e, b.d_sc, F, &hs, st));
+            for (int f : E)
+                if (!hs[f].ok) status[vin[f]] = EBCC_ECORRUPT;
+        }
+        CK(cudaStreamSynchronize(st));
+    }
+    return EBCC_OK;
+}
+
+// per-field device bytes of a compression batch (for splitting large batches)
+size_t compress_bytes(size_t ny, size_t nx, const ebcc_params &p) {
+    FieldGeom g;
+    make_geom(&g, (int)ny, (int)nx, p.levels, p.cblk_w, p.cblk_h, 16);
+    Arena dry;
+    Batch b;
+    layout_compress(dry, b, {(int)ny}, {(int)nx}, {g.L}, {g.nblocks}, 6 * p.cblk_w * p.cblk_h + 64);
+    return dry.used;
+}
+
+size_t batch_budget() {
+    static size_t v = 0;
+    if (!v) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = (size_t)8 << 30;
+        v = fr / 2;
+        if (v > ((size_t)64 << 30)) v = (size_t)64 << 30;
+        if (v < ((size_t)1 << 30)) v = (size_t)1 << 30;
+    }
+    return v;
 }
 
 }  // namespace
 
-size_t ebcc_compress_footprint(size_t ny, size_t nx, const ebcc_params &p) {
-    FieldGeom g;
-    make_geom(&g, (int)ny, (int)nx, p.levels, p.cblk_w, p.cblk_h, 16);
-    return field_bytes(g, 6 * p.cblk_w * p.cblk_h + 64) + ny * nx * 4;
+// ------------------------------------------------------------ engines
+struct EbccEngine {
+    Engine c, d;
+};
+
+EbccEngine *engine_create() { return new (std::nothrow) EbccEngine(); }
+
+void engine_destroy(EbccEngine *e) {
+    if (!e) return;
+    for (Engine *x : {&e->c, &e->d}) {
+        if (x->a.base) cudaFree(x->a.base);
+        if (x->stage) cudaFreeHost(x->stage);
+        if (x->ev_ok) { cudaEventDestroy(x->ev[0]); cudaEventDestroy(x->ev[1]); }
+    }
+    delete e;
 }
 
-int ebcc_compress_arena(Arena &a, const float *x_dev, size_t ny, size_t nx, double bound, int kind,
-                        const ebcc_params &p, uint8_t *out_dev, size_t cap, size_t *len, ebcc_stats *stats,
-                        cudaStream_t st) {
-    RC(check_shape(ny, nx));
-    if (!(bound > 0) || !isfinite(bound) || (kind != 0 && kind != 1)) return EBCC_EINVAL;
+size_t ebcc_compress_footprint(size_t ny, size_t nx, const ebcc_params &p) { return compress_bytes(ny, nx, p); }
+
+int engine_compress(EbccEngine *e, const ebcc_field_desc *fd, int n, ebcc_out_desc *od, const ebcc_params &p,
+                    cudaStream_t st) {
     RC(validate_params(p));
-    return compress_with(a, x_dev, ny, nx, bound, kind, p, out_dev, cap, len, stats, st, false);
+    // split into batches whose workspace fits the device budget
+    const size_t budget = batch_budget();
+    int i = 0;
+    while (i < n) {
+        size_t used = 0;
+        int j = i;
+        while (j < n) {
+            size_t fb = check_shape(fd[j].ny, fd[j].nx) ? 0 : compress_bytes(fd[j].ny, fd[j].nx, p);
+            if (j > i && used + fb > budget) break;
+            used += fb;
+            j++;
+        }
+        int rc = compress_batch(e->c, fd + i, j - i, od + i, p, st);
+        if (rc) {
+            for (int k = i; k < j; k++)
+                if (!od[k].status) od[k].status = rc;
+            return rc;
+        }
+        i = j;
+    }
+    return EBCC_OK;
 }
 
-int ebcc_decompress_arena(Arena &a, const uint8_t *s_dev, const uint8_t *s_host, size_t len, size_t ny, size_t nx,
-                          float *out_dev, cudaStream_t st) {
-    ParsedHeader h;
-    RC(parse_header(s_host, len, h));
-    if ((size_t)h.ny != ny || (size_t)h.nx != nx) return EBCC_EINVAL;
-    return decompress_field(s_dev, len, h, out_dev, a, st);
+int engine_decompress(EbccEngine *e, const ebcc_stream_desc *sd, int n, float *const *outs, int *status,
+                      cudaStream_t st) {
+    const size_t budget = batch_budget();
+    int i = 0;
+    while (i < n) {
+        size_t used = 0;
+        int j = i;
+        while (j < n) {
+            size_t fb = check_shape(sd[j].ny, sd[j].nx) ? 0 : sd[j].ny * sd[j].nx * 80 + sd[j].len;
+            if (j > i && used + fb > budget) break;
+            used += fb;
+            j++;
+        }
+        int rc = decompress_batch(e->d, sd + i, j - i, outs + i, status + i, st);
+        if (rc) {
+            for (int k = i; k < j; k++)
+                if (!status[k]) status[k] = rc;
+            return rc;
+        }
+        i = j;
+    }
+    return EBCC_OK;
 }
+
+namespace {
+std::mutex g_mu;
+EbccEngine *g_engine() {
+    static EbccEngine *e = engine_create();
+    return e;
+}
+}  // namespace
 
 extern "C" {
 
@@ -881,17 +1449,29 @@ int ebcc_compress(const float *field, size_t ny, size_t nx, double bound, int bo
     if (pp) p = *pp; else ebcc_params_default(&p);
     RC(validate_params(p));
     std::lock_guard<std::mutex> lk(g_mu);
-    size_t cap = ebcc_max_stream_bytes(ny, nx);
+    EbccEngine *eng = g_engine();
+    if (!eng) return EBCC_ENOMEM;
+    const size_t cap = ebcc_max_stream_bytes(ny, nx);
+    float *d_in = nullptr;
     uint8_t *d_out = nullptr;
-    CK(cudaMalloc(&d_out, cap));
-    size_t len = 0;
-    int rc = compress_dev_locked(field, ny, nx, bound, bound_kind, p, d_out, cap, &len, stats, 0, true);
-    if (rc == EBCC_OK) {
-        uint8_t *h = (uint8_t *)malloc(len);
+    CK(cudaMalloc(&d_in, ny * nx * sizeof(float)));
+    if (cudaMalloc(&d_out, cap) != cudaSuccess) { cudaFree(d_in); return EBCC_ENOMEM; }
+    int rc = EBCC_OK;
+    if (cudaMemcpy(d_in, field, ny * nx * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) rc = EBCC_ECUDA;
+    ebcc_field_desc fd{d_in, ny, nx, bound, bound_kind};
+    ebcc_out_desc od;
+    memset(&od, 0, sizeof(od));
+    od.stream = d_out;
+    od.capacity = cap;
+    if (!rc) rc = engine_compress(eng, &fd, 1, &od, p, 0);
+    if (!rc) rc = od.status;
+    if (!rc) {
+        uint8_t *h = (uint8_t *)malloc(od.len);
         if (!h) rc = EBCC_ENOMEM;
-        else if (cudaMemcpy(h, d_out, len, cudaMemcpyDeviceToHost) != cudaSuccess) { free(h); rc = EBCC_ECUDA; }
-        else { *out = h; *out_len = len; }
+        else if (cudaMemcpy(h, d_out, od.len, cudaMemcpyDeviceToHost) != cudaSuccess) { free(h); rc = EBCC_ECUDA; }
+        else { *out = h; *out_len = od.len; if (stats) *stats = od.stats; }
     }
+    cudaFree(d_in);
     cudaFree(d_out);
     return rc;
 }
@@ -913,13 +1493,17 @@ int ebcc_decompress(const uint8_t *stream, size_t len, float *out, size_t ny, si
     RC(parse_header(stream, len, h));
     if ((size_t)h.ny != ny || (size_t)h.nx != nx) return EBCC_EINVAL;
     std::lock_guard<std::mutex> lk(g_mu);
+    EbccEngine *eng = g_engine();
+    if (!eng) return EBCC_ENOMEM;
     uint8_t *d_s = nullptr;
     float *d_o = nullptr;
     CK(cudaMalloc(&d_s, len + 16));
     if (cudaMalloc(&d_o, ny * nx * sizeof(float)) != cudaSuccess) { cudaFree(d_s); return EBCC_ENOMEM; }
-    int rc = EBCC_OK;
+    int rc = EBCC_OK, s1 = EBCC_OK;
     if (cudaMemcpy(d_s, stream, len, cudaMemcpyHostToDevice) != cudaSuccess) rc = EBCC_ECUDA;
-    if (!rc) rc = decompress_field(d_s, len, h, d_o, g_dec_arena, 0);
+    ebcc_stream_desc sd{d_s, len, ny, nx};
+    if (!rc) rc = engine_decompress(eng, &sd, 1, &d_o, &s1, 0);
+    if (!rc) rc = s1;
     if (!rc && cudaMemcpy(out, d_o, ny * nx * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) rc = EBCC_ECUDA;
     cudaFree(d_s);
     cudaFree(d_o);
@@ -932,46 +1516,25 @@ int ebcc_compress_batch_dev(const ebcc_field_desc *fields, int n, ebcc_out_desc 
     ebcc_params p;
     if (pp) p = *pp; else ebcc_params_default(&p);
     RC(validate_params(p));
-    cudaStream_t st = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(g_mu);
-    int first = EBCC_OK;
-    for (int i = 0; i < n; i++) {
-        const ebcc_field_desc &d = fields[i];
-        int rc = check_shape(d.ny, d.nx);
-        if (!rc && (!(d.bound > 0) || !isfinite(d.bound) || (d.bound_kind != 0 && d.bound_kind != 1) || !d.field))
-            rc = EBCC_EINVAL;
-        size_t len = 0;
-        memset(&outs[i].stats, 0, sizeof(ebcc_stats));
-        if (!rc)
-            rc = compress_dev_locked(d.field, d.ny, d.nx, d.bound, d.bound_kind, p, outs[i].stream, outs[i].capacity,
-                                     &len, &outs[i].stats, st, false);
-        outs[i].status = rc;
-        outs[i].len = rc ? 0 : len;
-        if (rc && !first) first = rc;
-    }
-    return first;
+    EbccEngine *eng = g_engine();
+    if (!eng) return EBCC_ENOMEM;
+    RC(engine_compress(eng, fields, n, outs, p, (cudaStream_t)stream));
+    for (int i = 0; i < n; i++)
+        if (outs[i].status) return outs[i].status;
+    return EBCC_OK;
 }
 
 int ebcc_decompress_batch_dev(const ebcc_stream_desc *streams, int n, float **outs, void *stream) {
     if (n < 0 || (n > 0 && (!streams || !outs))) return EBCC_EINVAL;
-    cudaStream_t st = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(g_mu);
-    int first = EBCC_OK;
-    for (int i = 0; i < n; i++) {
-        HostHeader hb;
-        int rc = EBCC_OK;
-        if (streams[i].len < HDR_BYTES || !streams[i].stream) rc = EBCC_ECORRUPT;
-        if (!rc && cudaMemcpyAsync(hb.b, streams[i].stream, HDR_BYTES, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-            rc = EBCC_ECUDA;
-        if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = EBCC_ECUDA;
-        ParsedHeader h;
-        if (!rc) rc = parse_header(hb.b, streams[i].len, h);
-        if (!rc && ((size_t)h.ny != streams[i].ny || (size_t)h.nx != streams[i].nx)) rc = EBCC_EINVAL;
-        if (!rc) rc = decompress_field(streams[i].stream, streams[i].len, h, outs[i], g_dec_arena, st);
-        if (rc && !first) first = rc;
-    }
-    if (cudaStreamSynchronize(st) != cudaSuccess && !first) first = EBCC_ECUDA;
-    return first;
+    EbccEngine *eng = g_engine();
+    if (!eng) return EBCC_ENOMEM;
+    std::vector<int> status(n, EBCC_OK);
+    RC(engine_decompress(eng, streams, n, outs, status.data(), (cudaStream_t)stream));
+    for (int i = 0; i < n; i++)
+        if (status[i]) return status[i];
+    return EBCC_OK;
 }
 
 }  // extern "C"

@@ -14,12 +14,6 @@ namespace {
 
 constexpr int NT = 256;
 
-unsigned grid_for(size_t n) {
-    size_t g = (n + NT - 1) / NT;
-    const size_t cap = 152 * 8;
-    return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
-}
-
 __device__ __forceinline__ uint32_t f2key(float f) {
     uint32_t b = __float_as_uint(f);
     return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
@@ -28,16 +22,26 @@ __device__ __forceinline__ float key2f(uint32_t k) {
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
 }
 
-__global__ void mm_init(uint32_t *keys, int *nonfinite) {
-    keys[0] = 0xFFFFFFFFu;
-    keys[1] = 0;
-    *nonfinite = 0;
+__global__ void mm_init(Live lv, const __grid_constant__ FieldRun one, int nslots) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nslots; k += gridDim.x * blockDim.x) {
+        int f;
+        const FieldRun *r = pick(lv, one, k, f);
+        if (!r) continue;
+        r->sc->mmkey[0] = 0xFFFFFFFFu;
+        r->sc->mmkey[1] = 0;
+        r->sc->nonfinite = 0;
+    }
 }
 
-__global__ void __launch_bounds__(NT) mm_kernel(const float *__restrict__ x, size_t n, uint32_t *keys, int *nonfinite) {
+__global__ void __launch_bounds__(NT) mm_kernel(Live lv, const __grid_constant__ FieldRun one) {
+    int f;
+    const FieldRun *r = pick(lv, one, blockIdx.y, f);
+    if (!r) return;
+    const float *__restrict__ x = r->x;
+    const long long n = r->N;
     uint32_t lo = 0xFFFFFFFFu, hi = 0;
     int bad = 0;
-    for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT) {
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
         float v = x[i];
         if (!isfinite(v)) { bad = 1; continue; }
         uint32_t k = f2key(v);
@@ -50,22 +54,42 @@ __global__ void __launch_bounds__(NT) mm_kernel(const float *__restrict__ x, siz
         bad |= __shfl_xor_sync(0xffffffffu, bad, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        atomicMin(&keys[0], lo);
-        atomicMax(&keys[1], hi);
-        if (bad) atomicOr(nonfinite, 1);
+        atomicMin(&r->sc->mmkey[0], lo);
+        atomicMax(&r->sc->mmkey[1], hi);
+        if (bad) atomicOr(&r->sc->nonfinite, 1);
     }
 }
 
-__global__ void mm_final(const uint32_t *keys, double *mm) {
-    mm[0] = (double)key2f(keys[0]);
-    mm[1] = (double)key2f(keys[1]);
+__global__ void mm_final(Live lv, const __grid_constant__ FieldRun one, int nslots) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nslots; k += gridDim.x * blockDim.x) {
+        int f;
+        const FieldRun *r = pick(lv, one, k, f);
+        if (!r) continue;
+        r->sc->mm[0] = (double)key2f(r->sc->mmkey[0]);
+        r->sc->mm[1] = (double)key2f(r->sc->mmkey[1]);
+    }
 }
 
-__global__ void __launch_bounds__(NT) quant_kernel(const float *__restrict__ coef, int32_t *__restrict__ qt, FieldGeom g,
-                                                   int sm) {
-    const size_t n = (size_t)g.ny * g.nx;
-    for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT) {
-        int y = (int)(i / g.nx), x = (int)(i - (size_t)y * g.nx);
+// the field's geometry, staged in shared memory for per-point band lookups
+__device__ __forceinline__ void stage_geom(FieldGeom &dst, const FieldGeom *src) {
+    const int nw = (int)(sizeof(FieldGeom) / 4);
+    const uint32_t *s = (const uint32_t *)src;
+    uint32_t *d = (uint32_t *)&dst;
+    for (int k = threadIdx.x; k < nw; k += blockDim.x) d[k] = s[k];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(NT) quant_kernel(Live lv, const __grid_constant__ FieldRun one, int sm) {
+    int f;
+    const FieldRun *r = pick(lv, one, blockIdx.y, f);
+    if (!r) return;
+    __shared__ FieldGeom g;
+    stage_geom(g, r->geom);
+    const float *__restrict__ coef = r->W;
+    int32_t *__restrict__ qt = r->qt;
+    const long long n = r->N;
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
+        int y = (int)(i / g.nx), x = (int)(i - (long long)y * g.nx);
         float c = coef[i];
         float d = g.band[band_of(g, y, x)].delta;
         float m = floorf(__fdiv_rn(fabsf(c), d));
@@ -76,12 +100,19 @@ __global__ void __launch_bounds__(NT) quant_kernel(const float *__restrict__ coe
 }
 
 // coefficient value implied by npass passes of its block, from the trace flag
-__global__ void __launch_bounds__(NT) recon_kernel(const int32_t *__restrict__ qt, FieldGeom g,
-                                                   const int32_t *__restrict__ Kb, const int32_t *__restrict__ npb,
-                                                   float *__restrict__ coef) {
-    const size_t n = (size_t)g.ny * g.nx;
-    for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT) {
-        int y = (int)(i / g.nx), x = (int)(i - (size_t)y * g.nx);
+__global__ void __launch_bounds__(NT) recon_kernel(Live lv, const __grid_constant__ FieldRun one,
+                                                   const int32_t *__restrict__ Kb, const int32_t *__restrict__ npb) {
+    int f;
+    const FieldRun *r = pick(lv, one, blockIdx.y, f);
+    if (!r) return;
+    __shared__ FieldGeom g;
+    stage_geom(g, r->geom);
+    const int32_t *__restrict__ qt = r->qt;
+    float *__restrict__ coef = r->W;
+    const long long n = r->N;
+    const int blk0 = r->blk0;
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
+        int y = (int)(i / g.nx), x = (int)(i - (long long)y * g.nx);
         uint32_t v = (uint32_t)qt[i];
         uint32_t m = v & 0x3FFFFFFFu;
         float out = 0.0f;
@@ -89,7 +120,7 @@ __global__ void __launch_bounds__(NT) recon_kernel(const int32_t *__restrict__ q
             const BandGeom &B = g.band[band_of(g, y, x)];
             int blk = B.blk0 + ((y - B.y0) / g.ch) * B.nbx + (x - B.x0) / g.cw;
             if (!INB(blk, g.nblocks)) blk = 0;
-            int K = Kb[blk], np = npb[blk];
+            int K = Kb[blk0 + blk], np = npb[blk0 + blk];
             int s = 31 - __clz(m);
             int spp = (v >> 30) & 1;
             int psig = (s == K - 1) ? 0 : (spp ? 3 * (K - 1 - s) - 2 : 3 * (K - 1 - s));
@@ -142,10 +173,16 @@ __device__ int32_t edge(int32_t in, int32_t guess, int dir, double x, double mn,
     return good;
 }
 
-__global__ void __launch_bounds__(NT) bounds_kernel(const float *__restrict__ xs, size_t n, double mn, double range,
-                                                    double E, float2 *__restrict__ bounds) {
+__global__ void __launch_bounds__(NT) bounds_kernel(Live lv, const __grid_constant__ FieldRun one) {
+    int f;
+    const FieldRun *r = pick(lv, one, blockIdx.y, f);
+    if (!r) return;
+    const float *__restrict__ xs = r->x;
+    float2 *__restrict__ bounds = r->bounds;
+    const double mn = r->mn, range = r->range, E = r->E;
     const double inv = 1.0 / range;
-    for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT) {
+    const long long n = r->N;
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
         const double x = xs[i];
         float a0 = __double2float_rn((x - mn) * inv);
         int32_t o0 = f2o(a0);
@@ -165,14 +202,28 @@ __global__ void __launch_bounds__(NT) bounds_kernel(const float *__restrict__ xs
     }
 }
 
-__global__ void __launch_bounds__(NT) residue_kernel(const float *__restrict__ x, const float *__restrict__ ab, size_t n,
-                                                     double mn, double inv, float *__restrict__ res) {
-    for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT)
+__global__ void __launch_bounds__(NT) residue_kernel(Live lv, const __grid_constant__ FieldRun one) {
+    int f;
+    const FieldRun *r = pick(lv, one, blockIdx.y, f);
+    if (!r) return;
+    const float *__restrict__ x = r->x;
+    const float *__restrict__ ab = r->Abase;
+    float *__restrict__ res = r->R;
+    const double mn = r->mn, inv = r->inv_range;
+    const long long n = r->N;
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT)
         res[i] = __double2float_rn(__dsub_rn(__dmul_rn(__dsub_rn((double)x[i], mn), inv), (double)ab[i]));
 }
 
-__global__ void __launch_bounds__(NT) squant_kernel(const float *__restrict__ w, size_t n, int e, int32_t *__restrict__ s) {
-    for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT) {
+__global__ void __launch_bounds__(NT) squant_kernel(Live lv, const __grid_constant__ FieldRun one) {
+    int f;
+    const FieldRun *r = pick(lv, one, blockIdx.y, f);
+    if (!r) return;
+    const float *__restrict__ w = r->W;
+    int32_t *__restrict__ s = r->s;
+    const int e = r->sc->es;
+    const long long n = r->N;
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
         float v = w[i];
         float m = floorf(ldexpf(fabsf(v), -e));
         int32_t mi = m >= 1073741823.0f ? 0x3FFFFFFF : (int32_t)m;
@@ -180,16 +231,22 @@ __global__ void __launch_bounds__(NT) squant_kernel(const float *__restrict__ w,
     }
 }
 
-__global__ void __launch_bounds__(NT) sprefix_kernel(const int32_t *__restrict__ s, const uint32_t *__restrict__ sig_pos,
-                                                     const uint32_t *__restrict__ lsp_idx, const int64_t *refine_start,
-                                                     const int64_t *nbits_dev, int64_t nbits_host, size_t n, int e,
-                                                     float *__restrict__ out) {
+__global__ void __launch_bounds__(NT) sprefix_kernel(Live lv, const __grid_constant__ FieldRun one, int use_T) {
+    int f;
+    const FieldRun *r = pick(lv, one, blockIdx.y, f);
+    if (!r) return;
     __shared__ long long rs[32];
-    if (threadIdx.x < 32) rs[threadIdx.x] = refine_start[threadIdx.x];
+    if (threadIdx.x < 32) rs[threadIdx.x] = r->sc->refine_start[threadIdx.x];
     __syncthreads();
-    const long long T = nbits_dev ? *nbits_dev : nbits_host;
+    const long long T = use_T ? r->sc->T : r->sc->nbits;
+    const int e = r->sc->es;
     const float step = ldexpf(1.0f, e);
-    for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT) {
+    const int32_t *__restrict__ s = r->s;
+    const uint32_t *__restrict__ sig_pos = r->sig_pos;
+    const uint32_t *__restrict__ lsp_idx = r->lsp_idx;
+    float *__restrict__ out = r->R;
+    const long long n = r->N;
+    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
         int32_t v = s[i];
         uint32_t m = (uint32_t)(v < 0 ? -v : v);
         float o = 0.0f;
@@ -205,55 +262,68 @@ __global__ void __launch_bounds__(NT) sprefix_kernel(const int32_t *__restrict__
     }
 }
 
+unsigned pgrid(long long maxN, int nslots) {
+    long long g = (maxN + NT - 1) / NT;
+    long long cap = 2432 / (nslots > 0 ? nslots : 1);
+    if (cap < 8) cap = 8;
+    return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+unsigned sgrid(int nslots) { return (unsigned)((nslots + 255) / 256); }
+
 }  // namespace
 
-int minmax_finite(const float *x, size_t n, double *mm_dev, int *nonfinite_dev, cudaStream_t st) {
-    // the two uint32 keys live right after the two doubles
-    uint32_t *keys = (uint32_t *)(mm_dev + 2);
-    mm_init<<<1, 1, 0, st>>>(keys, nonfinite_dev);
-    PROF("mm_kernel", st, 4.0 * n, mm_kernel<<<grid_for(n), NT, 0, st>>>(x, n, keys, nonfinite_dev););
-    mm_final<<<1, 1, 0, st>>>(keys, mm_dev);
+#define PGRID dim3(pgrid(maxN, nslots), nslots)
+
+int minmax_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, cudaStream_t st) {
+    if (nslots <= 0) return EBCC_OK;
+    mm_init<<<sgrid(nslots), 256, 0, st>>>(lv, one, nslots);
+    PROF("mm_kernel", st, 4.0 * maxN * nslots, mm_kernel<<<PGRID, NT, 0, st>>>(lv, one));
+    mm_final<<<sgrid(nslots), 256, 0, st>>>(lv, one, nslots);
     CK(cudaGetLastError());
     return EBCC_OK;
 }
 
-int quantise_base(const float *coef, int32_t *qt, const FieldGeom &g, int sign_magnitude, cudaStream_t st) {
-    PROF("quant_kernel", st, 8.0 * g.ny * g.nx, quant_kernel<<<grid_for((size_t)g.ny * g.nx), NT, 0, st>>>(coef, qt, g, sign_magnitude););
+int quantise_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, int sign_magnitude, cudaStream_t st) {
+    if (nslots <= 0) return EBCC_OK;
+    PROF("quant_kernel", st, 8.0 * maxN * nslots, quant_kernel<<<PGRID, NT, 0, st>>>(lv, one, sign_magnitude));
     CK(cudaGetLastError());
     return EBCC_OK;
 }
 
-int base_recon(const int32_t *qt, const FieldGeom &g, const int32_t *K, const int32_t *npass, float *coef,
-               cudaStream_t st) {
-    PROF("recon_kernel", st, 8.0 * g.ny * g.nx, recon_kernel<<<grid_for((size_t)g.ny * g.nx), NT, 0, st>>>(qt, g, K, npass, coef););
+int base_recon_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, const int32_t *K,
+                 const int32_t *npass, cudaStream_t st) {
+    if (nslots <= 0) return EBCC_OK;
+    PROF("recon_kernel", st, 8.0 * maxN * nslots, recon_kernel<<<PGRID, NT, 0, st>>>(lv, one, K, npass));
     CK(cudaGetLastError());
     return EBCC_OK;
 }
 
-int make_bounds(const float *x, size_t n, double mn, double range, double eps_abs, double guard, float2 *bounds,
-                cudaStream_t st) {
-    PROF("bounds_kernel", st, 12.0 * n, bounds_kernel<<<grid_for(n), NT, 0, st>>>(x, n, mn, range, eps_abs - guard, bounds););
+int make_bounds_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, cudaStream_t st) {
+    if (nslots <= 0) return EBCC_OK;
+    PROF("bounds_kernel", st, 12.0 * maxN * nslots, bounds_kernel<<<PGRID, NT, 0, st>>>(lv, one));
     CK(cudaGetLastError());
     return EBCC_OK;
 }
 
-int residue(const float *x, const float *abase, size_t n, double mn, double inv_range, float *res, cudaStream_t st) {
-    PROF("residue_kernel", st, 12.0 * n, residue_kernel<<<grid_for(n), NT, 0, st>>>(x, abase, n, mn, inv_range, res););
+int residue_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, cudaStream_t st) {
+    if (nslots <= 0) return EBCC_OK;
+    PROF("residue_kernel", st, 12.0 * maxN * nslots, residue_kernel<<<PGRID, NT, 0, st>>>(lv, one));
     CK(cudaGetLastError());
     return EBCC_OK;
 }
 
-int spiht_quantise(const float *w, size_t n, int step_exp, int32_t *s, cudaStream_t st) {
-    PROF("squant_kernel", st, 8.0 * n, squant_kernel<<<grid_for(n), NT, 0, st>>>(w, n, step_exp, s););
+int spiht_quantise_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, cudaStream_t st) {
+    if (nslots <= 0) return EBCC_OK;
+    PROF("squant_kernel", st, 8.0 * maxN * nslots, squant_kernel<<<PGRID, NT, 0, st>>>(lv, one));
     CK(cudaGetLastError());
     return EBCC_OK;
 }
 
-int spiht_prefix_recon(const int32_t *s, const uint32_t *sig_pos, const uint32_t *lsp_idx, const int64_t *refine_start,
-                       const int64_t *nbits_dev, int64_t nbits_host, size_t n, int step_exp, float *out,
-                       cudaStream_t st) {
-    PROF("sprefix_kernel", st, 16.0 * n, sprefix_kernel<<<grid_for(n), NT, 0, st>>>(s, sig_pos, lsp_idx, refine_start, nbits_dev, nbits_host, n, step_exp,
-                                               out););
+int spiht_prefix_recon_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, int use_T,
+                         cudaStream_t st) {
+    if (nslots <= 0) return EBCC_OK;
+    PROF("sprefix_kernel", st, 16.0 * maxN * nslots, sprefix_kernel<<<PGRID, NT, 0, st>>>(lv, one, use_T));
     CK(cudaGetLastError());
     return EBCC_OK;
 }

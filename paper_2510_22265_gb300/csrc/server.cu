@@ -2,11 +2,13 @@
 // decompress requests with admission by an HBM budget.
 //
 // Requests are copied at submit time and queued FIFO.  Two worker threads, each
-// with its own CUDA stream and device workspace, take the oldest requests that
-// fit the budget (up to max_batch per group), run them, and complete their
-// tickets; a request that arrives while groups are on the GPU is admitted as
-// soon as budget and a worker free up, so the two streams keep the device
-// busy with overlapping work.  Latency is measured from submit to completion.
+// with its own CUDA stream and engine (device workspace), take the oldest
+// requests that fit the budget (up to max_batch per group) and run the group's
+// compressions as one batch and its decompressions as another (every kernel
+// covers all fields of the batch); a request that arrives while groups are on
+// the GPU is admitted as soon as budget and a worker free up, so the two
+// streams keep the device busy with overlapping work.  Latency is measured
+// from submit to completion.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -50,54 +52,89 @@ namespace {
 
 size_t footprint(const ebcc_request &r, const ebcc_params &p) {
     size_t n = r.ny * r.nx;
-    if (r.kind == EBCC_REQ_COMPRESS) return ebcc_compress_footprint(r.ny, r.nx, p) + ebcc_max_stream_bytes(r.ny, r.nx);
-    return n * 4 * 6 + r.stream_len + spiht_work_bytes(n) + (1 << 20);
+    if (r.kind == EBCC_REQ_COMPRESS) return ebcc_compress_footprint(r.ny, r.nx, p) + ebcc_max_stream_bytes(r.ny, r.nx) + n * 4;
+    return n * 4 * 21 + r.stream_len + spiht_work_bytes(n) + (1 << 20);
 }
 
-void run_job(ebcc_server *s, Job &j, Arena &arena, cudaStream_t st) {
-    ebcc_result &res = j.res;
-    memset(&res, 0, sizeof(res));
-    const size_t n = j.req.ny * j.req.nx;
-    if (j.req.kind == EBCC_REQ_COMPRESS) {
-        float *dx = nullptr;
-        uint8_t *dout = nullptr;
-        size_t cap = ebcc_max_stream_bytes(j.req.ny, j.req.nx), len = 0;
+// One admitted group: its compress requests run as one batch, its decompress
+// requests as another, on this worker's stream and engine.
+void run_group(ebcc_server *s, const std::vector<Job *> &jobs, EbccEngine *eng, cudaStream_t st) {
+    std::vector<Job *> cj, dj;
+    for (Job *j : jobs) {
+        memset(&j->res, 0, sizeof(j->res));
+        (j->req.kind == EBCC_REQ_COMPRESS ? cj : dj).push_back(j);
+    }
+    if (!cj.empty()) {
+        const int n = (int)cj.size();
+        std::vector<float *> dx(n, nullptr);
+        std::vector<uint8_t *> dout(n, nullptr);
+        std::vector<ebcc_field_desc> fd(n);
+        std::vector<ebcc_out_desc> od(n);
         int rc = EBCC_OK;
-        if (cudaMalloc(&dx, n * 4) != cudaSuccess || cudaMalloc(&dout, cap) != cudaSuccess) rc = EBCC_ENOMEM;
-        if (!rc && cudaMemcpyAsync(dx, j.in.data(), n * 4, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = EBCC_ECUDA;
-        if (!rc)
-            rc = ebcc_compress_arena(arena, dx, j.req.ny, j.req.nx, j.req.bound, j.req.bound_kind, s->p, dout, cap,
-                                     &len, nullptr, st);
-        if (!rc) {
-            res.stream = (uint8_t *)malloc(len);
-            if (!res.stream) rc = EBCC_ENOMEM;
-            else if (cudaMemcpyAsync(res.stream, dout, len, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                     cudaStreamSynchronize(st) != cudaSuccess) rc = EBCC_ECUDA;
-            res.stream_len = len;
+        for (int k = 0; k < n && !rc; k++) {
+            const ebcc_request &q = cj[k]->req;
+            const size_t cap = ebcc_max_stream_bytes(q.ny, q.nx);
+            if (cudaMalloc(&dx[k], q.ny * q.nx * 4) != cudaSuccess || cudaMalloc(&dout[k], cap) != cudaSuccess) {
+                rc = EBCC_ENOMEM;
+                break;
+            }
+            if (cudaMemcpyAsync(dx[k], cj[k]->in.data(), q.ny * q.nx * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
+                rc = EBCC_ECUDA;
+            fd[k] = ebcc_field_desc{dx[k], q.ny, q.nx, q.bound, q.bound_kind};
+            memset(&od[k], 0, sizeof(od[k]));
+            od[k].stream = dout[k];
+            od[k].capacity = cap;
         }
-        if (rc && res.stream) { free(res.stream); res.stream = nullptr; res.stream_len = 0; }
-        cudaFree(dx);
-        cudaFree(dout);
-        res.status = rc;
-    } else {
-        uint8_t *ds = nullptr;
-        float *dout = nullptr;
+        if (!rc) rc = engine_compress(eng, fd.data(), n, od.data(), s->p, st);
+        for (int k = 0; k < n; k++) {
+            ebcc_result &res = cj[k]->res;
+            int r = rc ? rc : od[k].status;
+            if (!r) {
+                res.stream = (uint8_t *)malloc(od[k].len ? od[k].len : 1);
+                if (!res.stream) r = EBCC_ENOMEM;
+                else if (cudaMemcpyAsync(res.stream, dout[k], od[k].len, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                         cudaStreamSynchronize(st) != cudaSuccess) r = EBCC_ECUDA;
+                res.stream_len = od[k].len;
+            }
+            if (r && res.stream) { free(res.stream); res.stream = nullptr; res.stream_len = 0; }
+            res.status = r;
+            cudaFree(dx[k]);
+            cudaFree(dout[k]);
+        }
+    }
+    if (!dj.empty()) {
+        const int n = (int)dj.size();
+        std::vector<uint8_t *> ds(n, nullptr);
+        std::vector<float *> dout(n, nullptr);
+        std::vector<ebcc_stream_desc> sd(n);
+        std::vector<int> status(n, EBCC_OK);
         int rc = EBCC_OK;
-        if (cudaMalloc(&ds, j.in.size() + 16) != cudaSuccess || cudaMalloc(&dout, n * 4) != cudaSuccess)
-            rc = EBCC_ENOMEM;
-        if (!rc && cudaMemcpyAsync(ds, j.in.data(), j.in.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
-            rc = EBCC_ECUDA;
-        if (!rc) rc = ebcc_decompress_arena(arena, ds, j.in.data(), j.in.size(), j.req.ny, j.req.nx, dout, st);
-        if (!rc) {
-            res.field = (float *)malloc(n * 4);
-            if (!res.field) rc = EBCC_ENOMEM;
-            else if (cudaMemcpyAsync(res.field, dout, n * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                     cudaStreamSynchronize(st) != cudaSuccess) rc = EBCC_ECUDA;
+        for (int k = 0; k < n && !rc; k++) {
+            const ebcc_request &q = dj[k]->req;
+            if (cudaMalloc(&ds[k], dj[k]->in.size() + 16) != cudaSuccess || cudaMalloc(&dout[k], q.ny * q.nx * 4) != cudaSuccess) {
+                rc = EBCC_ENOMEM;
+                break;
+            }
+            if (cudaMemcpyAsync(ds[k], dj[k]->in.data(), dj[k]->in.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+                rc = EBCC_ECUDA;
+            sd[k] = ebcc_stream_desc{ds[k], dj[k]->in.size(), q.ny, q.nx};
         }
-        if (rc && res.field) { free(res.field); res.field = nullptr; }
-        cudaFree(ds);
-        cudaFree(dout);
-        res.status = rc;
+        if (!rc) rc = engine_decompress(eng, sd.data(), n, dout.data(), status.data(), st);
+        for (int k = 0; k < n; k++) {
+            ebcc_result &res = dj[k]->res;
+            const ebcc_request &q = dj[k]->req;
+            int r = rc ? rc : status[k];
+            if (!r) {
+                res.field = (float *)malloc(q.ny * q.nx * 4);
+                if (!res.field) r = EBCC_ENOMEM;
+                else if (cudaMemcpyAsync(res.field, dout[k], q.ny * q.nx * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                         cudaStreamSynchronize(st) != cudaSuccess) r = EBCC_ECUDA;
+            }
+            if (r && res.field) { free(res.field); res.field = nullptr; }
+            res.status = r;
+            cudaFree(ds[k]);
+            cudaFree(dout[k]);
+        }
     }
 }
 
@@ -105,7 +142,7 @@ void worker(ebcc_server *s) {
     cudaSetDevice(s->device);
     cudaStream_t st;
     cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-    Arena arena;
+    EbccEngine *eng = engine_create();
     for (;;) {
         std::vector<uint64_t> group;
         {
@@ -126,26 +163,28 @@ void worker(ebcc_server *s) {
                 s->queue.pop_front();
             }
         }
-        for (uint64_t t : group) {
-            Job *jp;
-            {
-                std::lock_guard<std::mutex> lk(s->mu);
-                jp = &s->jobs[t];
-            }
-            run_job(s, *jp, arena, st);
+        std::vector<Job *> jp;
+        {
             std::lock_guard<std::mutex> lk(s->mu);
-            auto now = clk::now();
-            jp->res.latency_s = std::chrono::duration<double>(now - jp->t_submit).count();
-            jp->res.queue_s = std::chrono::duration<double>(jp->t_start - jp->t_submit).count();
-            jp->state = 2;
-            s->in_use -= jp->footprint;
-            jp->in.clear();
-            jp->in.shrink_to_fit();
-            s->cv_done.notify_all();
-            s->cv_work.notify_all();
+            for (uint64_t t : group) jp.push_back(&s->jobs[t]);
         }
+        if (eng) run_group(s, jp, eng, st);
+        else
+            for (Job *j : jp) { memset(&j->res, 0, sizeof(j->res)); j->res.status = EBCC_ENOMEM; }
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto now = clk::now();
+        for (Job *j : jp) {
+            j->res.latency_s = std::chrono::duration<double>(now - j->t_submit).count();
+            j->res.queue_s = std::chrono::duration<double>(j->t_start - j->t_submit).count();
+            j->state = 2;
+            s->in_use -= j->footprint;
+            j->in.clear();
+            j->in.shrink_to_fit();
+        }
+        s->cv_done.notify_all();
+        s->cv_work.notify_all();
     }
-    if (arena.base) cudaFree(arena.base);
+    engine_destroy(eng);
     cudaStreamDestroy(st);
 }
 

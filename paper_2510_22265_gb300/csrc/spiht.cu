@@ -32,14 +32,16 @@ struct SG {
     int h[EBCC_MAX_LEVELS + 1], w[EBCC_MAX_LEVELS + 1];
 };
 
-SG make_sg(int ny, int nx, int L) {
-    SG g;
-    g.ny = ny; g.nx = nx; g.L = L;
-    for (int l = 0; l <= L; l++) {
-        g.h[l] = (int)(((long)ny + (1L << l) - 1) >> l);
-        g.w[l] = (int)(((long)nx + (1L << l) - 1) >> l);
+// the field's SPIHT geometry in shared memory (all threads call; barrier inside)
+__device__ __forceinline__ void load_sg(SG &g, const FieldRun &r) {
+    if (threadIdx.x == 0) {
+        g.ny = r.ny; g.nx = r.nx; g.L = r.L;
+        for (int l = 0; l <= EBCC_MAX_LEVELS; l++) {
+            g.h[l] = (int)(((long long)r.ny + (1LL << l) - 1) >> l);
+            g.w[l] = (int)(((long long)r.nx + (1LL << l) - 1) >> l);
+        }
     }
-    return g;
+    __syncthreads();
 }
 
 __device__ __forceinline__ void band_box(const SG &g, int l, int o, int &y0, int &x0, int &bh, int &bw) {
@@ -95,7 +97,15 @@ __device__ __forceinline__ bool has_L(const SG &g, uint32_t idx) {
 __device__ __forceinline__ uint32_t absi(int32_t v) { return (uint32_t)(v < 0 ? -v : v); }
 
 // maxima of one level's nodes (level l detail bands, or the LL band when l = 0)
-__global__ void maxima_kernel(SG g, int l, const int32_t *__restrict__ s, uint32_t *maxd, uint32_t *maxl) {
+__global__ void maxima_kernel(Live lv, const __grid_constant__ FieldRun one, int l) {
+    int f;
+    const FieldRun *r = pick(lv, one, blockIdx.y, f);
+    if (!r) return;
+    if (r->L < 1 || (l > 0 && (l < 2 || l > r->L))) return;
+    __shared__ SG g;
+    load_sg(g, *r);
+    const int32_t *__restrict__ s = r->s;
+    uint32_t *maxd = r->sw.maxd, *maxl = r->sw.maxl;
     int nb = l == 0 ? 1 : 3;
     int y0s[3], x0s[3], bhs[3], bws[3];
     long cnt[4] = {0, 0, 0, 0};
@@ -195,13 +205,26 @@ __device__ __forceinline__ void win_flush(EncShared &sh, uint32_t *out32, unsign
     }
 }
 
-__global__ void __launch_bounds__(ET) encode_kernel(SG g, const int32_t *__restrict__ s, const uint32_t *__restrict__ maxd,
-                                                    const uint32_t *__restrict__ maxl, uint32_t *out32,
-                                                    unsigned long long cap_words, long long *nbits_out, int *nmax_out,
-                                                    uint32_t *sig_pos, uint32_t *lsp_idx, long long *refine_start,
-                                                    int *status, uint32_t *lip, uint32_t *lsp, uint32_t *lis,
-                                                    uint32_t *lis_new, uint32_t *wave_a, uint32_t *wave_b) {
+__global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_constant__ FieldRun one) {
+    int f;
+    const FieldRun *r = pick(lv, one, blockIdx.x, f);
+    if (!r) return;
     __shared__ EncShared sh;
+    __shared__ SG g;
+    load_sg(g, *r);
+    const int32_t *__restrict__ s = r->s;
+    const uint32_t *__restrict__ maxd = r->sw.maxd;
+    const uint32_t *__restrict__ maxl = r->sw.maxl;
+    uint32_t *out32 = (uint32_t *)r->sp;
+    const unsigned long long cap_words = (unsigned long long)r->sp_cap / 4;
+    long long *nbits_out = &r->sc->nbits;
+    int *nmax_out = &r->sc->nmax;
+    uint32_t *sig_pos = r->sig_pos, *lsp_idx = r->lsp_idx;
+    long long *refine_start = r->sc->refine_start;
+    int *status = &r->sc->spiht_status;
+    const long long N = r->N;
+    uint32_t *lip = r->sw.lip, *lsp = r->sw.lsp, *lis = r->sw.lis_a, *lis_new = r->sw.lis_a + N;
+    uint32_t *wave_a = r->sw.lis_b, *wave_b = r->sw.lis_b + N;
     const int tid = threadIdx.x;
     const long long NN = (long long)g.ny * g.nx;
     (void)NN;
@@ -424,10 +447,22 @@ struct BitR {
     }
 };
 
-__global__ void decode_kernel(SG g, const uint8_t *in, long long nbits, int nmax, int32_t *mag, int8_t *plane,
-                              uint8_t *neg, float *coef, int e, uint32_t *lip, uint32_t *lsp, uint32_t *lis,
-                              long long lis_cap) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void decode_kernel(Live lv, const __grid_constant__ FieldRun one) {
+    int f;
+    const FieldRun *rr = pick(lv, one, blockIdx.x, f);
+    if (!rr) return;
+    __shared__ SG g;
+    load_sg(g, *rr);
+    if (threadIdx.x != 0) return;
+    const uint8_t *in = rr->sp;
+    const long long nbits = rr->sc->nbits;
+    const int nmax = rr->sc->nmax;
+    if (nmax < 0 || nbits <= 0) return;
+    int32_t *mag = rr->qt;
+    int8_t *plane = rr->plane8;
+    uint8_t *neg = rr->neg8;
+    uint32_t *lip = rr->sw.lip, *lsp = rr->sw.lsp, *lis = rr->sw.lis_a;
+    const long long lis_cap = 4 * rr->N;
     const int hL = g.h[g.L], wL = g.w[g.L];
     long long nlip = 0, nlsp = 0, nlis = 0;
     uint32_t c[9];
@@ -493,14 +528,55 @@ done:
     return;
 }
 
-__global__ void dequant_kernel(const int32_t *mag, const int8_t *plane, const uint8_t *neg, size_t n, int e,
-                               float *coef) {
-    const float step = ldexpf(1.0f, e);
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        int p = plane[i];
-        float v = p >= 0 ? deq((uint32_t)mag[i], p, step) : 0.0f;
-        coef[i] = neg[i] && p >= 0 ? -v : v;
+// decoder: zero magnitudes, no plane, positive signs
+__global__ void dec_reset_kernel(Live lv, const __grid_constant__ FieldRun one) {
+    int f;
+    const FieldRun *r = pick(lv, one, blockIdx.y, f);
+    if (!r) return;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < r->N; i += (long long)gridDim.x * blockDim.x) {
+        r->qt[i] = 0;
+        r->plane8[i] = -1;
+        r->neg8[i] = 0;
     }
+}
+
+__global__ void dequant_kernel(Live lv, const __grid_constant__ FieldRun one) {
+    int f;
+    const FieldRun *r = pick(lv, one, blockIdx.y, f);
+    if (!r) return;
+    const float step = ldexpf(1.0f, r->sc->es);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < r->N; i += (long long)gridDim.x * blockDim.x) {
+        int p = r->plane8[i];
+        float v = p >= 0 ? deq((uint32_t)r->qt[i], p, step) : 0.0f;
+        r->R[i] = r->neg8[i] && p >= 0 ? -v : v;
+    }
+}
+
+// encoder: zero maxima, stream and plane table; no sign positions yet
+__global__ void enc_reset_kernel(Live lv, const __grid_constant__ FieldRun one) {
+    int f;
+    const FieldRun *r = pick(lv, one, blockIdx.y, f);
+    if (!r) return;
+    const long long n = r->N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        r->sw.maxd[i] = 0;
+        r->sw.maxl[i] = 0;
+        r->sig_pos[i] = 0xFFFFFFFFu;
+        r->lsp_idx[i] = 0xFFFFFFFFu;
+    }
+    uint32_t *o = (uint32_t *)r->sp;
+    const long long nw = r->sp_cap / 4;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nw; i += (long long)gridDim.x * blockDim.x)
+        o[i] = 0;
+    if (blockIdx.x == 0 && threadIdx.x < 32) r->sc->refine_start[threadIdx.x] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) r->sc->spiht_status = 0;
+}
+
+unsigned pg(long long maxN, int nslots) {
+    long long g = (maxN + 255) / 256;
+    long long cap = 2432 / (nslots > 0 ? nslots : 1);
+    if (cap < 8) cap = 8;
+    return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
 }  // namespace
@@ -518,46 +594,33 @@ void spiht_work_carve(uint8_t *base, size_t n, SpihtWork *w) {
     w->tmp = w->lis_a;
 }
 
-int spiht_encode(const int32_t *s, int ny, int nx, int L, uint8_t *out, size_t cap_bytes, int64_t *nbits_dev,
-                 int32_t *nmax_dev, uint32_t *sig_pos, uint32_t *lsp_idx, int64_t *refine_start, int32_t *status_dev,
-                 const SpihtWork &w, cudaStream_t st) {
-    const size_t n = (size_t)ny * nx;
-    if (n >= 0x7FFFFFFFu) return EBCC_EINVAL;
-    SG g = make_sg(ny, nx, L);
-    CK(cudaMemsetAsync(w.maxd, 0, 2 * n * sizeof(uint32_t), st));
-    CK(cudaMemsetAsync(sig_pos, 0xFF, n * sizeof(uint32_t), st));
-    CK(cudaMemsetAsync(lsp_idx, 0xFF, n * sizeof(uint32_t), st));
-    CK(cudaMemsetAsync(refine_start, 0, 32 * sizeof(int64_t), st));
-    CK(cudaMemsetAsync(out, 0, cap_bytes & ~(size_t)3, st));
-    for (int l = 2; l <= L; l++) {
-        PROF("maxima_kernel", st, 0.0, maxima_kernel<<<152 * 4, 256, 0, st>>>(g, l, s, w.maxd, w.maxl););
+int spiht_encode_b(const Live &lv, const FieldRun &one, int nslots, const BatchDims &d, cudaStream_t st) {
+    if (nslots <= 0) return EBCC_OK;
+    if (d.maxN >= 0x7FFFFFFFLL) return EBCC_EINVAL;
+    PROF("enc_reset_kernel", st, 0.0, enc_reset_kernel<<<dim3(pg(d.maxN, nslots), nslots), 256, 0, st>>>(lv, one));
+    CK(cudaGetLastError());
+    for (int l = 2; l <= d.maxL; l++) {
+        long long nb = 3LL * d.h[l] * d.w[l];
+        unsigned gx = pg(nb, nslots);
+        PROF("maxima_kernel", st, 0.0, maxima_kernel<<<dim3(gx, nslots), 256, 0, st>>>(lv, one, l));
         CK(cudaGetLastError());
     }
-    if (L >= 1) {
-        PROF("maxima_kernel", st, 0.0, maxima_kernel<<<152, 256, 0, st>>>(g, 0, s, w.maxd, w.maxl););
+    if (d.maxL >= 1) {
+        PROF("maxima_kernel", st, 0.0, maxima_kernel<<<dim3(pg((long long)d.h[d.maxL] * d.w[d.maxL] * 4, nslots), nslots), 256, 0, st>>>(lv, one, 0));
         CK(cudaGetLastError());
     }
-    PROF("encode_kernel", st, 0.0, encode_kernel<<<1, ET, 0, st>>>(g, s, w.maxd, w.maxl, (uint32_t *)out, cap_bytes / 4, (long long *)nbits_dev,
-                                    nmax_dev, sig_pos, lsp_idx, (long long *)refine_start, status_dev, w.lip, w.lsp,
-                                    w.lis_a, w.lis_a + n, w.lis_b, w.lis_b + n););
+    PROF("encode_kernel", st, 0.0, encode_kernel<<<nslots, ET, 0, st>>>(lv, one));
     CK(cudaGetLastError());
     return EBCC_OK;
 }
 
-int spiht_decode(const uint8_t *in, int64_t nbits, int ny, int nx, int L, int nmax, int32_t *mag, int8_t *plane,
-                 uint8_t *neg, float *coef_out, int step_exp, const SpihtWork &w, cudaStream_t st) {
-    const size_t n = (size_t)ny * nx;
-    SG g = make_sg(ny, nx, L);
-    CK(cudaMemsetAsync(mag, 0, n * sizeof(int32_t), st));
-    CK(cudaMemsetAsync(plane, 0xFF, n, st));
-    CK(cudaMemsetAsync(neg, 0, n, st));
-    if (nmax >= 0 && nbits > 0) {
-        PROF("decode_kernel", st, 0.0, decode_kernel<<<1, 32, 0, st>>>(g, in, nbits, nmax, mag, plane, neg, coef_out, step_exp, w.lip, w.lsp,
-                                        w.lis_a, (long long)(4 * n)););
-        CK(cudaGetLastError());
-    }
-    if (coef_out) {
-        PROF("dequant_kernel", st, 0.0, dequant_kernel<<<152 * 4, 256, 0, st>>>(mag, plane, neg, n, step_exp, coef_out););
+int spiht_decode_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, int to_coef, cudaStream_t st) {
+    if (nslots <= 0) return EBCC_OK;
+    PROF("dec_reset_kernel", st, 0.0, dec_reset_kernel<<<dim3(pg(maxN, nslots), nslots), 256, 0, st>>>(lv, one));
+    PROF("decode_kernel", st, 0.0, decode_kernel<<<nslots, 32, 0, st>>>(lv, one));
+    CK(cudaGetLastError());
+    if (to_coef) {
+        PROF("dequant_kernel", st, 0.0, dequant_kernel<<<dim3(pg(maxN, nslots), nslots), 256, 0, st>>>(lv, one));
         CK(cudaGetLastError());
     }
     return EBCC_OK;

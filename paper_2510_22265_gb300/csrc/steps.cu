@@ -2,6 +2,7 @@
 // path on caller-owned device buffers so it can be checked against the CPU
 // oracle on its own.  Temporary scratch is allocated per call.
 #include <math.h>
+#include <string.h>
 #include <vector>
 #include "ebcc_internal.cuh"
 
@@ -20,6 +21,16 @@ struct Tmp {
         return EBCC_OK;
     }
 };
+
+const Live kSingle{nullptr, nullptr, nullptr};
+
+// a single field passed by value to the batched kernels
+FieldRun single(int ny, int nx, int L) {
+    FieldRun r;
+    memset(&r, 0, sizeof(r));
+    r.ny = ny; r.nx = nx; r.L = L; r.N = (long long)ny * nx;
+    return r;
+}
 
 int shape_ok(size_t ny, size_t nx) {
     return (ny == 0 || nx == 0 || ny > (1u << 30) || nx > (1u << 30) || ny * nx >= 0x7FFFFFFFull) ? EBCC_EINVAL
@@ -52,8 +63,7 @@ int ebcc_dwt_inv_dev(const float *in, float *out, size_t ny, size_t nx, int leve
     float *s1, *s2;
     RC(t.get(&s1, ((ny + 1) / 2) * ((nx + 1) / 2) + 16));
     RC(t.get(&s2, ((ny + 3) / 4) * ((nx + 3) / 4) + 16));
-    InvFinal fin{-1, nullptr, nullptr, nullptr};
-    RC(dwt_inverse_ex(in, out, s1, s2, (int)ny, (int)nx, L, fin, 0.0, 1.0, (cudaStream_t)stream));
+    RC(dwt_inverse_plain(in, out, s1, s2, (int)ny, (int)nx, L, (cudaStream_t)stream));
     CK(cudaStreamSynchronize((cudaStream_t)stream));
     return EBCC_OK;
 }
@@ -61,10 +71,19 @@ int ebcc_dwt_inv_dev(const float *in, float *out, size_t ny, size_t nx, int leve
 int ebcc_quantise_dev(const float *coef, int32_t *q, size_t ny, size_t nx, int levels, int P, void *stream) {
     RC(shape_ok(ny, nx));
     if (levels < 0 || P < 1 || P > 30 || !coef || !q) return EBCC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
     FieldGeom g;
     make_geom(&g, (int)ny, (int)nx, levels, 32, 32, P);
-    RC(quantise_base(coef, q, g, 0, (cudaStream_t)stream));
-    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    Tmp t;
+    FieldGeom *dg;
+    RC(t.get(&dg, 1));
+    CK(cudaMemcpy(dg, &g, sizeof(g), cudaMemcpyHostToDevice));
+    FieldRun one = single((int)ny, (int)nx, g.L);
+    one.W = const_cast<float *>(coef);
+    one.qt = q;
+    one.geom = dg;
+    RC(quantise_b(kSingle, one, 1, one.N, 0, st));
+    CK(cudaStreamSynchronize(st));
     return EBCC_OK;
 }
 
@@ -128,6 +147,7 @@ int ebcc_pcrd_dev(const int32_t *npass, const int32_t *pass_len, const int64_t *
     hl.maxpt = T1_MAXPASS + 1;
     double *db;
     Sel *sel;
+    FieldScal *sc;
     RC(t.get(&hl.nh, nblk + 1));
     RC(t.get(&hl.pt, (size_t)(nblk + 1) * hl.maxpt));
     RC(t.get(&hl.rate, (size_t)(nblk + 1) * hl.maxpt));
@@ -137,14 +157,18 @@ int ebcc_pcrd_dev(const int32_t *npass, const int32_t *pass_len, const int64_t *
     RC(t.get(&hl.sdr, (size_t)(nblk + 1) * T1_MAXPASS));
     RC(t.get(&hl.sdr2, (size_t)(nblk + 1) * T1_MAXPASS));
     RC(t.get(&hl.cum, (size_t)(nblk + 1) * T1_MAXPASS));
-    RC(t.get(&hl.nseg, 4));
     RC(t.get(&db, 1));
     RC(t.get(&sel, 1));
+    RC(t.get(&sc, 1));
+    CK(cudaMemsetAsync(sc, 0, sizeof(FieldScal), st));
     CK(cudaMemcpyAsync(db, &budget, 8, cudaMemcpyHostToDevice, st));
+    FieldRun one = single(1, 1, 0);
+    one.nblk = nblk;
+    one.sc = sc;
     RC(pcrd_hulls(npass, pass_len, dD, D0, nblk, maxpass, hl, st));
-    RC(pcrd_prepare(hl, nblk, st));
-    RC(pcrd_select(hl, nblk, db, sel, st));
-    RC(pcrd_npass(hl, nblk, sel, npass_out, st));
+    RC(pcrd_prepare_b(kSingle, one, 1, hl, st));
+    RC(pcrd_select(hl, &sc->nseg, db, sel, st));
+    RC(pcrd_npass_b(kSingle, one, 1, nblk, hl, sel, 0, npass_out, st));
     CK(cudaStreamSynchronize(st));
     return EBCC_OK;
 }
@@ -153,39 +177,63 @@ int ebcc_spiht_encode_dev(const int32_t *s, size_t ny, size_t nx, int levels, ui
                           int64_t *nbits_out, int32_t *nmax_out, uint32_t *sig_pos, uint32_t *lsp_idx,
                           int64_t *refine_start, void *stream) {
     RC(shape_ok(ny, nx));
-    if (levels < 0 || !s || !out) return EBCC_EINVAL;
+    if (levels < 0 || !s || !out || !nbits_out || !nmax_out || !sig_pos || !lsp_idx || !refine_start)
+        return EBCC_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = ny * nx;
     int L = effective_levels((int)ny, (int)nx, levels);
     Tmp t;
     uint8_t *w;
-    int32_t *status;
+    FieldScal *sc;
     RC(t.get(&w, spiht_work_bytes(n)));
-    RC(t.get(&status, 4));
-    SpihtWork sw;
-    spiht_work_carve(w, n, &sw);
-    CK(cudaMemsetAsync(status, 0, 4, st));
-    RC(spiht_encode(s, (int)ny, (int)nx, L, out, cap_bytes, nbits_out, nmax_out, sig_pos, lsp_idx, refine_start,
-                    status, sw, st));
-    int hs = 0;
-    CK(cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, st));
+    RC(t.get(&sc, 1));
+    CK(cudaMemsetAsync(sc, 0, sizeof(FieldScal), st));
+    FieldRun one = single((int)ny, (int)nx, L);
+    spiht_work_carve(w, n, &one.sw);
+    one.s = const_cast<int32_t *>(s);
+    one.sp = out;
+    one.sp_cap = (long long)(cap_bytes & ~(size_t)3);
+    one.sig_pos = sig_pos;
+    one.lsp_idx = lsp_idx;
+    one.sc = sc;
+    BatchDims d;
+    batch_dims_init(d);
+    batch_dims_add(d, (int)ny, (int)nx, L, 0);
+    RC(spiht_encode_b(kSingle, one, 1, d, st));
+    FieldScal h;
+    CK(cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    return hs ? EBCC_ECAPACITY : EBCC_OK;
+    CK(cudaMemcpy(nbits_out, &h.nbits, 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(nmax_out, &h.nmax, 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(refine_start, h.refine_start, 32 * 8, cudaMemcpyHostToDevice));
+    return h.spiht_status ? EBCC_ECAPACITY : EBCC_OK;
 }
 
 int ebcc_spiht_decode_dev(const uint8_t *in, int64_t nbits, size_t ny, size_t nx, int levels, int nmax, int32_t *mag,
                           int8_t *plane, uint8_t *neg, void *stream) {
     RC(shape_ok(ny, nx));
-    if (levels < 0 || nbits < 0 || nmax > 30) return EBCC_EINVAL;
+    if (levels < 0 || nbits < 0 || nmax > 30 || !mag || !plane || !neg || (nbits > 0 && !in)) return EBCC_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = ny * nx;
     int L = effective_levels((int)ny, (int)nx, levels);
     Tmp t;
     uint8_t *w;
+    FieldScal *sc;
     RC(t.get(&w, spiht_work_bytes(n)));
-    SpihtWork sw;
-    spiht_work_carve(w, n, &sw);
-    RC(spiht_decode(in, nbits, (int)ny, (int)nx, L, nmax, mag, plane, neg, nullptr, 0, sw, st));
+    RC(t.get(&sc, 1));
+    FieldScal h;
+    memset(&h, 0, sizeof(h));
+    h.nbits = nbits;
+    h.nmax = nmax;
+    CK(cudaMemcpy(sc, &h, sizeof(h), cudaMemcpyHostToDevice));
+    FieldRun one = single((int)ny, (int)nx, L);
+    spiht_work_carve(w, n, &one.sw);
+    one.sp = const_cast<uint8_t *>(in);
+    one.qt = mag;
+    one.plane8 = plane;
+    one.neg8 = neg;
+    one.sc = sc;
+    RC(spiht_decode_b(kSingle, one, 1, (long long)n, 0, st));
     CK(cudaStreamSynchronize(st));
     return EBCC_OK;
 }
@@ -193,23 +241,55 @@ int ebcc_spiht_decode_dev(const uint8_t *in, int64_t nbits, size_t ny, size_t nx
 int ebcc_spiht_prefix_recon_dev(const int32_t *s, const uint32_t *sig_pos, const uint32_t *lsp_idx,
                                 const int64_t *refine_start, int64_t nbits, size_t n, int step_exp, float *out,
                                 void *stream) {
-    if (!s || !sig_pos || !lsp_idx || !refine_start || !out || nbits < 0) return EBCC_EINVAL;
-    RC(spiht_prefix_recon(s, sig_pos, lsp_idx, refine_start, nullptr, nbits, n, step_exp, out, (cudaStream_t)stream));
-    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    if (!s || !sig_pos || !lsp_idx || !refine_start || !out || nbits < 0 || n == 0 || n >= 0x7FFFFFFFull)
+        return EBCC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    Tmp t;
+    FieldScal *sc;
+    RC(t.get(&sc, 1));
+    FieldScal h;
+    memset(&h, 0, sizeof(h));
+    h.nbits = nbits;
+    h.es = step_exp;
+    CK(cudaMemcpy(sc, &h, sizeof(h), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(sc->refine_start, refine_start, 32 * 8, cudaMemcpyDeviceToDevice));
+    FieldRun one = single(1, (int)n, 0);
+    one.s = const_cast<int32_t *>(s);
+    one.sig_pos = const_cast<uint32_t *>(sig_pos);
+    one.lsp_idx = const_cast<uint32_t *>(lsp_idx);
+    one.R = out;
+    one.sc = sc;
+    RC(spiht_prefix_recon_b(kSingle, one, 1, (long long)n, 0, st));
+    CK(cudaStreamSynchronize(st));
     return EBCC_OK;
 }
 
 int ebcc_count_within_dev(const float *x, const float *an_hat, size_t n, double mn, double range, double eps_abs,
                           double guard, int64_t *count_out, void *stream) {
-    if (!x || !an_hat || !count_out || !(range > 0) || !(eps_abs > guard)) return EBCC_EINVAL;
+    if (!x || !an_hat || !count_out || !(range > 0) || !(eps_abs > guard) || n == 0 || n >= 0x7FFFFFFFull)
+        return EBCC_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     Tmp t;
     float2 *b;
+    FieldScal *sc;
     RC(t.get(&b, n + 1));
-    RC(make_bounds(x, n, mn, range, eps_abs, guard, b, st));
-    CK(cudaMemsetAsync(count_out, 0, 8, st));
-    InvFinal fin{1, b, nullptr, (unsigned long long *)count_out};
-    RC(dwt_inverse_ex(an_hat, nullptr, nullptr, nullptr, 1, (int)n, 0, fin, 0.0, 1.0, st));
+    RC(t.get(&sc, 1));
+    CK(cudaMemsetAsync(sc, 0, sizeof(FieldScal), st));
+    FieldRun one = single(1, (int)n, 0);
+    one.x = x;
+    one.mn = mn;
+    one.range = range;
+    one.inv_range = 1.0 / range;
+    one.E = eps_abs - guard;
+    one.bounds = b;
+    one.W = const_cast<float *>(an_hat);
+    one.sc = sc;
+    BatchDims d;
+    batch_dims_init(d);
+    batch_dims_add(d, 1, (int)n, 0, 0);
+    RC(make_bounds_b(kSingle, one, 1, (long long)n, st));
+    RC(dwt_inverse_b(kSingle, one, 1, d, PL_W, InvFinal{1, 0, 0, 0}, st));
+    CK(cudaMemcpyAsync(count_out, &sc->cnt[0], 8, cudaMemcpyDeviceToDevice, st));
     CK(cudaStreamSynchronize(st));
     return EBCC_OK;
 }

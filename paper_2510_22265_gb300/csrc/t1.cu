@@ -406,7 +406,8 @@ __global__ void __launch_bounds__(WARPS * 32) t1_decode_kernel(const uint8_t *by
         if (lane == 0 && np > 0 && np <= 3 * K - 2) {
             reset_ctx(I, M);
             MQDec dc;
-            dc.init(bytes + off[b], len[b]);
+            // bytes == nullptr: off[] holds absolute payload addresses
+            dc.init(bytes ? bytes + off[b] : (const uint8_t *)(uintptr_t)off[b], len[b]);
             const int orient = d.orient;
             const uint64_t full = w == 64 ? ~0ull : ((1ull << w) - 1);
             int pass = 0;
