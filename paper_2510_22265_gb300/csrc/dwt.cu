@@ -27,6 +27,7 @@ constexpr int EX = TX + 2 * HALO, EY = TY + 2 * HALO;
 constexpr int NT = 256;
 
 __device__ __forceinline__ int reflect(int i, int n) {
+    if ((unsigned)i < (unsigned)n) return i;
     if (n == 1) return 0;
     int p = 2 * (n - 1);
     i %= p;
@@ -125,14 +126,15 @@ __global__ void __launch_bounds__(NT) fwd_level(Live lv, const __grid_constant__
     }
 }
 
+template <int NTH = NT>
 __device__ __forceinline__ void block_count_add(unsigned long long v, unsigned long long *dst) {
-    __shared__ unsigned long long red[NT / 32];
+    __shared__ unsigned long long red[NTH / 32];
     for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long s = 0;
-        for (int i = 0; i < NT / 32; i++) s += red[i];
+        for (int i = 0; i < NTH / 32; i++) s += red[i];
         if (s) atomicAdd(dst, s);
     }
 }
@@ -157,11 +159,15 @@ __device__ __forceinline__ void finish_point(const InvFinal &fin, const FieldRun
     }
 }
 
+constexpr int IT = 96;  // threads of an inverse-level CTA (72 stage the tile's columns)
+
 // inverse level l of the field in grid slot blockIdx.z: LL (the Mallat array
 // at the top level, else the scratch of level l + 1) + detail bands of plane
 // `src` -> the level-(l-1) region: the scratch of level l, or at level 1 the
-// finished output per fin
-__global__ void __launch_bounds__(NT) inv_level(Live lv, const __grid_constant__ FieldRun one, int l, int src_plane,
+// finished output per fin.  Thread c < EX stages column c of the extended
+// tile (its source column is fixed, rows step down), then each row and each
+// column is lifted in registers by one thread.
+__global__ void __launch_bounds__(IT) inv_level(Live lv, const __grid_constant__ FieldRun one, int l, int src_plane,
                                                 InvFinal fin) {
     int f;
     const FieldRun *r = pick(lv, one, blockIdx.z, f);
@@ -171,51 +177,113 @@ __global__ void __launch_bounds__(NT) inv_level(Live lv, const __grid_constant__
     const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
     if (ty0 >= hp || tx0 >= wp) return;
     const float *__restrict__ coef = plane_ptr(*r, src_plane);
-    const float *__restrict__ ll = l == L ? coef : (((l + 1) & 1) ? r->s2 : r->s1);
-    const int ls = l == L ? nx : ceil_sh(nx, l);
+    const float *__restrict__ ll = l < L ? (((l + 1) & 1) ? r->s2 : r->s1) : coef;
+    const int ls = l < L ? ceil_sh(nx, l) : nx;
     float *__restrict__ dst = l == 1 ? plane_ptr(*r, fin.dst) : ((l & 1) ? r->s2 : r->s1);
     const int ds = l == 1 ? nx : wp;
     const int mode = l == 1 ? fin.mode : -1;
-    const long long ncoef = r->N;
+    const int ncoef = (int)r->N;
     const int hl = (hp + 1) >> 1, wl = (wp + 1) >> 1;
+    const int tid = threadIdx.x;
     __shared__ float t[EY][EX + 1];
-    for (int k = threadIdx.x; k < EY * EX; k += NT) {
-        int ly = k / EX, lx = k % EX;
-        int gy = reflect(ty0 - HALO + ly, hp), gx = reflect(tx0 - HALO + lx, wp);
-        int pv = gy & 1, ph = gx & 1;
-        int sy = gy >> 1, sx = gx >> 1;
-        float v;
-        if (!pv && !ph) v = INB((long long)sy * ls + sx, (long long)hl * ls) ? ll[(size_t)sy * ls + sx] : 0.0f;
-        else {
-            long long ci = (long long)(sy + (pv ? hl : 0)) * nx + sx + (ph ? wl : 0);
-            v = INB(ci, ncoef) ? coef[ci] : 0.0f;
+    if (tid < EX) {  // all EY loads of the column in flight, then the stores
+        const int gx = reflect(tx0 - HALO + tid, wp);
+        const int ph = gx & 1, sx = gx >> 1;
+        const int cx = sx + (ph ? wl : 0);  // column of the coefficient in the Mallat array
+        const int lim_ll = hl * ls;
+        float v[EY];
+#pragma unroll
+        for (int ly = 0; ly < EY; ly++) {
+            const int gy = reflect(ty0 - HALO + ly, hp);
+            const int pv = gy & 1, sy = gy >> 1;
+            const bool from_ll = !pv && !ph;
+            const int i = from_ll ? sy * ls + sx : (sy + (pv ? hl : 0)) * nx + cx;
+            const bool ok = from_ll ? INBQ(i, lim_ll) : INBQ(i, ncoef);
+            const float *src = from_ll ? ll : coef;
+            v[ly] = ok ? src[i] : 0.0f;
         }
-        t[ly][lx] = v;
+#pragma unroll
+        for (int ly = 0; ly < EY; ly++) t[ly][tid] = v[ly];
     }
     __syncthreads();
-    scale<false>(t, KAPPA, INV_KAPPA, 0, EY); __syncthreads();
-    lift<false>(t, 0, -DELTA, 0, EY); __syncthreads();
-    lift<false>(t, 1, -GAMMA, 0, EY); __syncthreads();
-    lift<false>(t, 0, -BETA, 0, EY); __syncthreads();
-    lift<false>(t, 1, -ALPHA, 0, EY); __syncthreads();
-    scale<true>(t, KAPPA, INV_KAPPA, HALO, HALO + TX); __syncthreads();
-    lift<true>(t, 0, -DELTA, HALO, HALO + TX); __syncthreads();
-    lift<true>(t, 1, -GAMMA, HALO, HALO + TX); __syncthreads();
-    lift<true>(t, 0, -BETA, HALO, HALO + TX); __syncthreads();
-    lift<true>(t, 1, -ALPHA, HALO, HALO + TX); __syncthreads();
+    if (tid < EY) {  // rows: scale, then the four lifting steps backwards
+        float v[EX];
+#pragma unroll
+        for (int i = 0; i < EX; i++) v[i] = t[tid][i];
+#pragma unroll
+        for (int i = 0; i < EX; i++) v[i] *= (i & 1) ? INV_KAPPA : KAPPA;
+#pragma unroll
+        for (int i = 2; i <= EX - 2; i += 2) v[i] += -DELTA * (v[i - 1] + v[i + 1]);
+#pragma unroll
+        for (int i = 1; i <= EX - 2; i += 2) v[i] += -GAMMA * (v[i - 1] + v[i + 1]);
+#pragma unroll
+        for (int i = 2; i <= EX - 2; i += 2) v[i] += -BETA * (v[i - 1] + v[i + 1]);
+#pragma unroll
+        for (int i = 1; i <= EX - 2; i += 2) v[i] += -ALPHA * (v[i - 1] + v[i + 1]);
+#pragma unroll
+        for (int i = 0; i < EX; i++) t[tid][i] = v[i];
+    }
+    __syncthreads();
     unsigned long long cnt = 0;
-    for (int k = threadIdx.x; k < TY * TX; k += NT) {
-        int rr = k / TX, c = k % TX;
-        int gy = ty0 + rr, gx = tx0 + c;
-        if (gy >= hp || gx >= wp) continue;
-        float v = t[HALO + rr][HALO + c];
-        if (mode < 0) {
-            if (INB((long long)gy * ds + gx, l == 1 ? ncoef : (long long)hp * ds)) dst[(size_t)gy * ds + gx] = v;
-        } else {
-            finish_point(fin, *r, dst, v, (long long)gy * nx + gx, cnt);
+    if (tid < TX) {  // columns: thread c lifts column HALO + c and finishes its TY outputs
+        float w[EY];
+#pragma unroll
+        for (int i = 0; i < EY; i++) w[i] = t[i][HALO + tid];
+#pragma unroll
+        for (int i = 0; i < EY; i++) w[i] *= (i & 1) ? INV_KAPPA : KAPPA;
+#pragma unroll
+        for (int i = 2; i <= EY - 2; i += 2) w[i] += -DELTA * (w[i - 1] + w[i + 1]);
+#pragma unroll
+        for (int i = 1; i <= EY - 2; i += 2) w[i] += -GAMMA * (w[i - 1] + w[i + 1]);
+#pragma unroll
+        for (int i = 2; i <= EY - 2; i += 2) w[i] += -BETA * (w[i - 1] + w[i + 1]);
+#pragma unroll
+        for (int i = 1; i <= EY - 2; i += 2) w[i] += -ALPHA * (w[i - 1] + w[i + 1]);
+        const int gx = tx0 + tid;
+        if (gx < wp) {
+            const int nr = hp - ty0 < TY ? hp - ty0 : TY;
+            if (mode < 0) {
+                const int lim = l == 1 ? ncoef : hp * ds;
+#pragma unroll
+                for (int rr = 0; rr < TY; rr++) {
+                    const int i = (ty0 + rr) * ds + gx;
+                    if (rr < nr && INBQ(i, lim)) dst[i] = w[HALO + rr];
+                }
+            } else if (mode == 1 || mode == 2) {  // counts: loads of a group in flight together
+                const float2 *__restrict__ bnd = r->bounds;
+                const float *__restrict__ ab = r->Abase;
+#pragma unroll
+                for (int g0 = 0; g0 < TY; g0 += 8) {
+                    float2 bb[8];
+                    float av[8];
+#pragma unroll
+                    for (int u = 0; u < 8; u++) {
+                        const int rr = g0 + u;
+                        const int i = (ty0 + rr) * nx + gx;
+                        const bool ok = rr < nr && INBQ(i, ncoef);
+                        bb[u] = ok ? bnd[i] : make_float2(1.0f, 0.0f);
+                        av[u] = (mode == 2 && ok) ? ab[i] : 0.0f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; u++) {
+                        const int rr = g0 + u;
+                        if (mode == 1) {
+                            const float v = w[HALO + rr];
+                            cnt += (v >= bb[u].x && v <= bb[u].y);
+                        } else if (rr < nr) {
+                            const float s2 = av[u] + w[HALO + rr];
+                            cnt += !(s2 >= bb[u].x && s2 <= bb[u].y);
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int rr = 0; rr < TY; rr++)
+                    if (rr < nr) finish_point(fin, *r, dst, w[HALO + rr], (long long)(ty0 + rr) * nx + gx, cnt);
+            }
         }
     }
-    if (mode == 1 || mode == 2) block_count_add(cnt, &r->sc->cnt[fin.counter]);
+    if (mode == 1 || mode == 2) block_count_add<IT>(cnt, &r->sc->cnt[fin.counter]);
 }
 
 // fields with no DWT level: the transform is the identity
@@ -306,7 +374,7 @@ int dwt_inverse_b(const Live &lv, const FieldRun &one, int nslots, const BatchDi
         else if (fin.mode == 1) per += 8.0;
         else if (fin.mode == 2) per += 12.0;
         else per += fin.add_base ? 8.0 : 4.0;
-        PROF("inv_level", st, per * hp * wp * nslots, inv_level<<<grid, NT, 0, st>>>(lv, one, l, src, fin));
+        PROF("inv_level", st, per * hp * wp * nslots, inv_level<<<grid, IT, 0, st>>>(lv, one, l, src, fin));
         CK(cudaGetLastError());
     }
     return EBCC_OK;

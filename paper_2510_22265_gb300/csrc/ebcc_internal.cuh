@@ -280,9 +280,11 @@ __device__ __forceinline__ Sel select_for_budget(const uint64_t *skey, const uns
 // min / max of the finite values and the non-finite flag -> sc
 int minmax_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, cudaStream_t st);
 int quantise_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, int sign_magnitude, cudaStream_t st);
-// W = base reconstruction for npass (batch-wide per-block arrays K, npass)
-int base_recon_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, const int32_t *K,
-                 const int32_t *npass, cudaStream_t st);
+// W = base reconstruction for npass (batch-wide per-block arrays K, npass);
+// one warp per code-block of the listed fields (blocks from blk, absolute
+// offsets into the batch-wide planes starting at qt0 / W0)
+int base_recon_b(const Live &lv, int nslots, int maxnblk, const BlockDesc *blk, const int32_t *qt0, float *W0,
+                 const int32_t *K, const int32_t *npass, long long ntot, cudaStream_t st);
 int make_bounds_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, cudaStream_t st);
 // R = (x - mn) / range - Abase in FP64, rounded to float
 int residue_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, cudaStream_t st);
@@ -343,6 +345,9 @@ __device__ __forceinline__ bool ebcc_inb(long long i, long long n, int line) {
 #else
 #define INB(i, n) true
 #endif
+// quiet form for hot loops (no report, so loads around it can be batched):
+// the caller skips or zero-fills the access when it is false
+#define INBQ(i, n) ((unsigned long long)(long long)(i) < (unsigned long long)(long long)(n))
 #endif
 
 // ------------------------------------------------------------ device helpers

@@ -774,6 +774,12 @@ int check_shape(size_t ny, size_t nx) {
 }
 
 // ------------------------------------------------------------ the two loops
+// inverse DWT of the base reconstruction for the kept passes b.npass
+int base_eval(Batch &b, const Live &lv, int nslots, InvFinal fin, cudaStream_t st) {
+    RC(base_recon_b(lv, nslots, b.dims.maxnblk, b.d_blk, b.run[0].qt, b.run[0].W, b.t1.K, b.npass, b.Ntot, st));
+    return dwt_inverse_b(lv, kNone, nslots, b.dims, PL_W, fin, st);
+}
+
 // Algorithm 1's base loop for the table entries in A (q, or q = 1 with the
 // fallback's upward condition); the final states are left in b.bl
 int run_base_loop(Engine &e, Batch &b, const std::vector<int> &A, double q, int fallback, const ebcc_params &p,
@@ -791,8 +797,7 @@ int run_base_loop(Engine &e, Batch &b, const std::vector<int> &A, double q, int 
     int hn = n, rc = EBCC_OK;
     for (int step = 0; step < 400; step++) {
         rc = pcrd_npass_b(lv, kNone, hn, b.dims.maxnblk, b.hull, sel, sizeof(BaseLoop), b.npass, st);
-        if (!rc) rc = base_recon_b(lv, kNone, hn, b.dims.maxN, b.t1.K, b.npass, st);
-        if (!rc) rc = dwt_inverse_b(lv, kNone, hn, b.dims, PL_W, fin, st);
+        if (!rc) rc = base_eval(b, lv, hn, fin, st);
         if (rc) break;
         PROF("bl_update", st, 0.0, bl_update<<<1, 1024, 0, st>>>(b.bl, b.d_run, b.hull, b.live));
         if (ebcc_debug_sync_enabled() && ebcc_stage_check(st, "base eval", __LINE__)) { rc = EBCC_ECUDA; break; }
@@ -996,8 +1001,7 @@ int compress_batch(Engine &e, const ebcc_field_desc *fd, int n, ebcc_out_desc *o
         Live lv = live_of(b);
         // ---- A_base = dec_base(e_f), the residue in FP64, its DWT
         RC(pcrd_npass_b(lv, kNone, na, b.dims.maxnblk, b.hull, &b.bl[0].sel_f, sizeof(BaseLoop), b.npass, st));
-        RC(base_recon_b(lv, kNone, na, b.dims.maxN, b.t1.K, b.npass, st));
-        RC(dwt_inverse_b(lv, kNone, na, b.dims, PL_W, InvFinal{0, 0, PL_ABASE, 0}, st));
+        RC(base_eval(b, lv, na, InvFinal{0, 0, PL_ABASE, 0}, st));
         RC(residue_b(lv, kNone, na, b.dims.maxN, st));
         RC(dwt_forward_b(lv, kNone, na, b.dims, PL_R, 0, st));
         STAGE(st, "residue dwt");

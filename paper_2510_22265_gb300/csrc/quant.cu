@@ -99,39 +99,54 @@ __global__ void __launch_bounds__(NT) quant_kernel(Live lv, const __grid_constan
     }
 }
 
-// coefficient value implied by npass passes of its block, from the trace flag
-__global__ void __launch_bounds__(NT) recon_kernel(Live lv, const __grid_constant__ FieldRun one,
-                                                   const int32_t *__restrict__ Kb, const int32_t *__restrict__ npb) {
-    int f;
-    const FieldRun *r = pick(lv, one, blockIdx.y, f);
-    if (!r) return;
-    __shared__ FieldGeom g;
-    stage_geom(g, r->geom);
-    const int32_t *__restrict__ qt = r->qt;
-    float *__restrict__ coef = r->W;
-    const long long n = r->N;
-    const int blk0 = r->blk0;
-    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
-        int y = (int)(i / g.nx), x = (int)(i - (long long)y * g.nx);
-        uint32_t v = (uint32_t)qt[i];
-        uint32_t m = v & 0x3FFFFFFFu;
-        float out = 0.0f;
-        if (m) {
-            const BandGeom &B = g.band[band_of(g, y, x)];
-            int blk = B.blk0 + ((y - B.y0) / g.ch) * B.nbx + (x - B.x0) / g.cw;
-            if (!INB(blk, g.nblocks)) blk = 0;
-            int K = Kb[blk0 + blk], np = npb[blk0 + blk];
-            int s = 31 - __clz(m);
-            int spp = (v >> 30) & 1;
-            int psig = (s == K - 1) ? 0 : (spp ? 3 * (K - 1 - s) - 2 : 3 * (K - 1 - s));
-            if (np > 0 && psig < np) {
-                int p = K - 1 - np / 3;  // lowest plane whose refinement pass is included
-                p = p < 0 ? 0 : (p > s ? s : p);
-                float val = deq((m >> p) << p, p, B.delta);
-                out = (v & 0x80000000u) ? -val : val;
+// base-layer coefficient from its quantised value (sign bit 31, trace flag
+// bit 30, magnitude below) and its code-block's K and kept passes: the
+// midpoint of the interval the kept passes leave, as a decoder reconstructs it
+__device__ __forceinline__ float recon_value(uint32_t v, float delta, int Kb, int npb) {
+    const uint32_t m = v & 0x3FFFFFFFu;
+    if (!m) return 0.0f;
+    const int s = 31 - __clz(m);
+    const int spp = (v >> 30) & 1;
+    const int psig = (s == Kb - 1) ? 0 : (spp ? 3 * (Kb - 1 - s) - 2 : 3 * (Kb - 1 - s));
+    if (npb > 0 && psig < npb) {
+        int p = Kb - 1 - npb / 3;  // lowest plane whose refinement pass is included
+        p = p < 0 ? 0 : (p > s ? s : p);
+        const float val = deq((m >> p) << p, p, delta);
+        return (v & 0x80000000u) ? -val : val;
+    }
+    return 0.0f;
+}
+
+constexpr int RW = 8;  // warps (code-blocks) per reconstruction CTA
+
+// coefficients implied by the kept passes of each code-block, from the trace
+// flags: one warp per code-block of the listed fields, rows coalesced
+__global__ void __launch_bounds__(RW * 32) recon_kernel(Live lv, const BlockDesc *__restrict__ blk,
+                                                        const int32_t *__restrict__ qt0, float *__restrict__ W0,
+                                                        const int32_t *__restrict__ Kb, const int32_t *__restrict__ npb,
+                                                        long long ntot) {
+    if ((int)blockIdx.y >= *lv.n) return;
+    const FieldRun &r = lv.tab[lv.idx[blockIdx.y]];
+    const int lb = blockIdx.x * RW + (threadIdx.x >> 5);
+    if (lb >= r.nblk) return;
+    const int b = r.blk0 + lb;
+    const BlockDesc d = blk[b];
+    const int K = Kb[b], np = npb[b];
+    const int lane = threadIdx.x & 31;
+    for (int c = lane; c < d.w; c += 32) {
+        for (int r0 = 0; r0 < d.h; r0 += 8) {  // eight loads in flight per lane
+            uint32_t q[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const long long i = d.off + (long long)(r0 + u) * d.stride + c;
+                q[u] = (r0 + u < d.h && INBQ(i, ntot)) ? (uint32_t)qt0[i] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const long long i = d.off + (long long)(r0 + u) * d.stride + c;
+                if (r0 + u < d.h && INBQ(i, ntot)) W0[i] = recon_value(q[u], d.delta, K, np);
             }
         }
-        coef[i] = out;
     }
 }
 
@@ -147,10 +162,12 @@ __device__ __forceinline__ bool point_ok(float a, double x, double mn, double ra
     return fabs(__dsub_rn(x, (double)xr)) <= E;
 }
 
-// largest (dir=+1) or smallest (dir=-1) ordinal ok, given ok at `in` and a guess
+// largest (dir=+1) or smallest (dir=-1) ordinal ok, given ok at `in` and a
+// guess; the ok ordinals form one interval (the test is monotone in the
+// value), so a galloping search from the guess and a bisection find its edge
 __device__ int32_t edge(int32_t in, int32_t guess, int dir, double x, double mn, double range, double E) {
     const int32_t lim = dir > 0 ? f2o(__int_as_float(0x7F800000)) : f2o(__int_as_float(0xFF800000));
-    if ((long long)(guess - in) * dir < 0) guess = in;
+    if (((long long)guess - (long long)in) * dir < 0) guess = in;
     int32_t good, bad;
     if (point_ok(o2f(guess), x, mn, range, E)) {
         good = guess;
@@ -162,11 +179,18 @@ __device__ int32_t edge(int32_t in, int32_t guess, int dir, double x, double mn,
             good = (int32_t)probe;
             step *= 2;
         }
-    } else {
-        good = in;
+    } else {  // the guess lies outside: step back towards `in` (which is ok)
         bad = guess;
+        long long step = 1;
+        for (;;) {
+            long long probe = (long long)bad - dir * step;
+            if ((probe - (long long)in) * dir <= 0) { good = in; break; }
+            if (point_ok(o2f((int32_t)probe), x, mn, range, E)) { good = (int32_t)probe; break; }
+            bad = (int32_t)probe;
+            step *= 2;
+        }
     }
-    while ((long long)(bad - good) * dir > 1) {  // bisect: good ok, bad not ok
+    while (((long long)bad - (long long)good) * dir > 1) {  // bisect: good ok, bad not ok
         int32_t mid = (int32_t)(((long long)good + (long long)bad) / 2);
         if (point_ok(o2f(mid), x, mn, range, E)) good = mid; else bad = mid;
     }
@@ -291,10 +315,11 @@ int quantise_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, 
     return EBCC_OK;
 }
 
-int base_recon_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, const int32_t *K,
-                 const int32_t *npass, cudaStream_t st) {
-    if (nslots <= 0) return EBCC_OK;
-    PROF("recon_kernel", st, 8.0 * maxN * nslots, recon_kernel<<<PGRID, NT, 0, st>>>(lv, one, K, npass));
+int base_recon_b(const Live &lv, int nslots, int maxnblk, const BlockDesc *blk, const int32_t *qt0, float *W0,
+                 const int32_t *K, const int32_t *npass, long long ntot, cudaStream_t st) {
+    if (nslots <= 0 || maxnblk <= 0) return EBCC_OK;
+    dim3 grid((maxnblk + RW - 1) / RW, nslots);
+    PROF("recon_kernel", st, 0.0, recon_kernel<<<grid, RW * 32, 0, st>>>(lv, blk, qt0, W0, K, npass, ntot));
     CK(cudaGetLastError());
     return EBCC_OK;
 }
