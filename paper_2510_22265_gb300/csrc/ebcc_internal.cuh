@@ -207,7 +207,16 @@ struct T1Out {
     int64_t *dD;         // nblk * maxpass
     int64_t *D0;         // nblk
     int32_t *status;     // bit 0 byte overflow, bit 1 too many passes
+    // modelled symbols of blocks up to 32 x 32 (byte (ctx << 1) | bit), sym_cap
+    // per block, and the symbol count at each pass end; null: serial coder
+    uint8_t *sym;
+    long long sym_cap;
+    int32_t *pass_sym;   // nblk * maxpass
 };
+// symbol capacity per coefficient of a block: per bit-plane at most 1.5
+// symbols per coefficient (a run-length hit at the first row costs three for
+// one coefficient), planes K <= 26, plus one sign per coefficient
+#define SYM_PER_COEF 40
 int t1_encode_blocks(int32_t *qt, const BlockDesc *blk, int nblk, int maxw, int maxh, const T1Out &o,
                      int sign_magnitude_q, uint8_t *spp_out, long long nq, cudaStream_t st);
 int t1_decode_blocks(const uint8_t *bytes, const int64_t *off, const int32_t *len, const BlockDesc *blk,

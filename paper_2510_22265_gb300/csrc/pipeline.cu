@@ -589,7 +589,7 @@ const FieldRun kNone{};  // placeholder `one` argument of batched launches
 // run with a null arena measures it) and fills the pointers of the table.
 // Geometry-dependent values (normalisation, steps) are filled later.
 void layout_compress(Arena &a, Batch &b, const std::vector<int> &ny, const std::vector<int> &nx,
-                     const std::vector<int> &L, const std::vector<int> &nblk, int cap_blk) {
+                     const std::vector<int> &L, const std::vector<int> &nblk, int cw, int ch, int cap_blk) {
     const int F = (int)ny.size();
     b.F = F;
     b.run.assign(F, FieldRun{});
@@ -620,6 +620,14 @@ void layout_compress(Arena &a, Batch &b, const std::vector<int> &ny, const std::
     b.t1.dD = carve<int64_t>(a, nb * T1_MAXPASS);
     b.t1.D0 = carve<int64_t>(a, nb);
     b.t1.status = carve<int32_t>(a, 4);
+    b.t1.sym = nullptr;
+    b.t1.sym_cap = 0;
+    b.t1.pass_sym = nullptr;
+    if (cw <= 32 && ch <= 32) {  // the split (model, then MQ) coder
+        b.t1.sym_cap = (long long)SYM_PER_COEF * cw * ch;
+        b.t1.sym = carve<uint8_t>(a, nb * b.t1.sym_cap);
+        b.t1.pass_sym = carve<int32_t>(a, nb * T1_MAXPASS);
+    }
     b.hull.maxpt = T1_MAXPASS + 1;
     b.hull.nh = carve<int32_t>(a, nb);
     b.hull.pt = carve<int32_t>(a, nb * (T1_MAXPASS + 1));
@@ -893,10 +901,10 @@ int compress_batch(Engine &e, const ebcc_field_desc *fd, int n, ebcc_out_desc *o
     Batch b;
     {
         Arena dry;
-        layout_compress(dry, b, ny, nx, L, nblk, cap_blk);
+        layout_compress(dry, b, ny, nx, L, nblk, cw, ch, cap_blk);
         RC(arena_reserve(e.a, dry.used + 4096));
     }
-    layout_compress(e.a, b, ny, nx, L, nblk, cap_blk);
+    layout_compress(e.a, b, ny, nx, L, nblk, cw, ch, cap_blk);
     RC(engine_begin(e, stage_bytes_for(F, b.Btot)));
     std::vector<int> status(F, EBCC_OK);
     for (int f = 0; f < F; f++) {
@@ -1338,7 +1346,7 @@ size_t compress_bytes(size_t ny, size_t nx, const ebcc_params &p) {
     make_geom(&g, (int)ny, (int)nx, p.levels, p.cblk_w, p.cblk_h, 16);
     Arena dry;
     Batch b;
-    layout_compress(dry, b, {(int)ny}, {(int)nx}, {g.L}, {g.nblocks}, 6 * p.cblk_w * p.cblk_h + 64);
+    layout_compress(dry, b, {(int)ny}, {(int)nx}, {g.L}, {g.nblocks}, p.cblk_w, p.cblk_h, 6 * p.cblk_w * p.cblk_h + 64);
     return dry.used;
 }
 

@@ -377,6 +377,357 @@ __global__ void __launch_bounds__(WARPS * 32) t1_encode_kernel(int32_t *qt, cons
     }
 }
 
+// ------------------------------------------------------------ warp-parallel encoder
+// Code-blocks of at most 32 x 32: lane j owns column j -- its magnitudes in
+// registers, and significance, coded-in-this-plane, refined, sign and
+// bit-plane states as bit masks over rows.  Every pass is decided for all
+// coefficients at once: a coefficient's neighbours count as significant when
+// they were significant before the pass, or became significant earlier in the
+// pass's stripe order (previous stripes; left column of the same stripe;
+// rows above in the same column).  In the significance propagation pass that
+// set depends on itself, so it is solved as the least fixpoint: lanes exchange
+// their new-significance masks with shuffles until nothing changes, and the
+// chain down a column is closed in one step with a carry (a run of
+// "insignificant with bit 1" rows is filled from its first enabled row by an
+// addition).  Each lane then emits its column's symbols stripe by stripe in
+// scan order, a warp scan places them in a shared buffer, and lane 0 runs the
+// MQ coder over the pass.  The results are identical to the serial coder.
+constexpr uint64_t kStripeEnd = 0x8888888888888888ull;    // rows r with r % 4 == 3
+constexpr uint64_t kStripeStart = 0x1111111111111111ull;  // rows r with r % 4 == 0
+constexpr int PW = 4;          // warps per CTA
+
+struct PWShared {
+    uint8_t sig[4][256];
+    uint8_t sgn[256];
+};
+
+// one column's view of its neighbours' significance, row-aligned (bit r is
+// the neighbour of the coefficient at row r)
+struct View {
+    uint64_t Lup, Lmid, Ldn, Mup, Mdn, Rup, Rmid, Rdn;
+    __device__ __forceinline__ uint32_t pat(int r) const {
+        return (uint32_t)(((Lup >> r) & 1) | (((Mup >> r) & 1) << 1) | (((Rup >> r) & 1) << 2) |
+                          (((Lmid >> r) & 1) << 3) | (((Rmid >> r) & 1) << 4) | (((Ldn >> r) & 1) << 5) |
+                          (((Mdn >> r) & 1) << 6) | (((Rdn >> r) & 1) << 7));
+    }
+    __device__ __forceinline__ uint64_t any() const { return Lup | Lmid | Ldn | Mup | Mdn | Rup | Rmid | Rdn; }
+};
+
+// S*: significance before the pass; N*: new significance of the pass (L / M / R
+// = left, own, right column)
+__device__ __forceinline__ View make_view(uint64_t SL, uint64_t NL, uint64_t SM, uint64_t NM, uint64_t SR, uint64_t NR) {
+    View v;
+    v.Lup = (SL | NL) << 1;
+    v.Lmid = SL | NL;
+    v.Ldn = (SL >> 1) | ((NL >> 1) & ~kStripeEnd);
+    v.Mup = (SM | NM) << 1;
+    v.Mdn = SM >> 1;
+    v.Rup = (SR << 1) | ((NR << 1) & kStripeStart);
+    v.Rmid = SR;
+    v.Rdn = SR >> 1;
+    return v;
+}
+
+// sign-coding pattern (sigL negL sigR negR sigU negU sigD negD) of row r
+__device__ __forceinline__ uint32_t sign_pat(const View &v, uint64_t NGL, uint64_t NGM, uint64_t NGR, int r) {
+    return (uint32_t)(((v.Lmid >> r) & 1) | (((NGL >> r) & 1) << 1) | (((v.Rmid >> r) & 1) << 2) |
+                      (((NGR >> r) & 1) << 3) | (((v.Mup >> r) & 1) << 4) | ((((NGM << 1) >> r) & 1) << 5) |
+                      (((v.Mdn >> r) & 1) << 6) | ((((NGM >> 1) >> r) & 1) << 7));
+}
+
+struct SymBuf {  // up to 16 symbols of one column in one stripe, byte k = (ctx << 1) | bit
+    uint64_t lo = 0, hi = 0;
+    int n = 0;
+    __device__ __forceinline__ void put(int cx, int d) {
+        const uint64_t b = (uint64_t)((cx << 1) | d);
+        if (n < 8) lo |= b << (8 * n); else hi |= b << (8 * (n - 8));
+        n++;
+    }
+};
+
+// place every lane's symbols of a stripe in scan order (lane = column)
+__device__ __forceinline__ void emit(uint8_t *buf, int cap, int &base, const SymBuf &sb, int lane, int32_t *status) {
+    int incl = sb.n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+    const int at = base + incl - sb.n;
+    for (int k = 0; k < sb.n; k++) {
+        if (at + k < cap) buf[at + k] = (uint8_t)((k < 8 ? sb.lo >> (8 * k) : sb.hi >> (8 * (k - 8))) & 0xFF);
+        else atomicOr(status, 1);
+    }
+    base += tot;
+}
+
+__device__ __forceinline__ int64_t warp_sum64(int64_t v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(PW * 32) t1_model_warp(int32_t *qt, const BlockDesc *blk, int nblk, T1Out o,
+                                                         int mark_spp_in_q, uint8_t *spp_out, long long nq) {
+    __shared__ PWShared tb;
+    for (int k = threadIdx.x; k < 4 * 256; k += blockDim.x) tb.sig[k >> 8][k & 255] = c_sigctx[k >> 8][k & 255];
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) tb.sgn[k] = c_signctx[k];
+    __syncthreads();
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int b = blockIdx.x * PW + wid; b < nblk; b += gridDim.x * PW) {
+        const BlockDesc d = blk[b];
+        const int w = d.w, h = d.h;
+        const uint64_t VALID = lane < w ? ((1ull << h) - 1) : 0ull;  // rows of my column (none past the width)
+        // my column: magnitudes (registers) and signs
+        uint32_t m[32];
+        uint64_t NGM = 0;
+        uint32_t mx = 0;
+        int64_t d0 = 0;
+#pragma unroll
+        for (int r = 0; r < 32; r++) {
+            m[r] = 0;
+            if (lane < w && r < h) {
+                const long long at = d.off + (long long)r * d.stride + lane;
+                const int32_t v = INBQ(at, nq) ? qt[at] : 0;
+                m[r] = mark_spp_in_q ? ((uint32_t)v & 0x3FFFFFFFu) : (uint32_t)(v < 0 ? -v : v);
+                NGM |= (uint64_t)(v < 0) << r;
+                mx = max(mx, m[r]);
+                const int64_t t = 2 * (int64_t)m[r] + 1;
+                d0 += t * t;
+            }
+        }
+#pragma unroll
+        for (int s2 = 16; s2; s2 >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, s2));
+        d0 = warp_sum64(d0);
+        const int K = mx ? 32 - __clz(mx) : 0;
+        int np = K ? 3 * K - 2 : 0;
+        if (lane == 0) {
+            o.D0[b] = d0;
+            o.K[b] = K;
+            if (np > o.maxpass) { atomicOr(o.status, 2); np = 0; }
+            o.npass[b] = np;
+        }
+        np = __shfl_sync(0xffffffffu, np, 0);
+        const uint64_t NGL = __shfl_up_sync(0xffffffffu, NGM, 1) * (lane > 0);
+        const uint64_t NGR = __shfl_down_sync(0xffffffffu, NGM, 1) * (lane < 31);
+        uint64_t SIG = 0, REF = 0, SPPF = 0;
+        if (np) {
+            const int orient = d.orient;
+            const uint8_t *sigt = tb.sig[orient];
+            uint8_t *buf = o.sym + (size_t)b * o.sym_cap;
+            const int cap = (int)o.sym_cap;
+            int pass = 0, base = 0;
+            const size_t pb = (size_t)b * o.maxpass;
+            // record the pass's end in the symbol stream and its distortion decrease
+            auto code_pass = [&](int64_t dd) {
+                if (lane == 0 && pass < o.maxpass) {
+                    o.pass_sym[pb + pass] = base;
+                    o.dD[pb + pass] = dd;
+                }
+                pass++;
+            };
+            auto sign_sym = [&](SymBuf &sb, const View &v, int r) {
+                const uint32_t sc = tb.sgn[sign_pat(v, NGL, NGM, NGR, r)];
+                sb.put(sc & 15, (int)((NGM >> r) & 1) ^ (int)(sc >> 4));
+            };
+            for (int p = K - 1; p >= 0; p--) {
+                uint64_t B = 0;
+#pragma unroll
+                for (int r = 0; r < 32; r++) B |= (uint64_t)((m[r] >> p) & 1) << r;
+                const uint64_t SL = __shfl_up_sync(0xffffffffu, SIG, 1) * (lane > 0);
+                const uint64_t SR = __shfl_down_sync(0xffffffffu, SIG, 1) * (lane < 31);
+                uint64_t S1 = SIG, VIS = 0;
+                if (p < K - 1) {
+                    // ---- significance propagation: least fixpoint of the new-significance masks
+                    const uint64_t G = ~SIG & B & VALID;
+                    uint64_t N = 0;
+                    View v;
+                    for (int it = 0; it < 4 * 64 * 32; it++) {
+                        const uint64_t NL = __shfl_up_sync(0xffffffffu, N, 1) * (lane > 0);
+                        const uint64_t NR = __shfl_down_sync(0xffffffffu, N, 1) * (lane < 31);
+                        v = make_view(SL, NL, SIG, 0, SR, NR);
+                        const uint64_t st = G & v.any();
+                        const uint64_t Nn = (((G + st) ^ G ^ st) >> 1) & G;
+                        const bool ch = Nn != N;
+                        N = Nn;
+                        if (!__any_sync(0xffffffffu, ch)) break;
+                    }
+                    {
+                        const uint64_t NL = __shfl_up_sync(0xffffffffu, N, 1) * (lane > 0);
+                        const uint64_t NR = __shfl_down_sync(0xffffffffu, N, 1) * (lane < 31);
+                        v = make_view(SL, NL, SIG, N, SR, NR);
+                    }
+                    const uint64_t coded = ~SIG & VALID & v.any();
+                    int64_t dd = 0;
+#pragma unroll
+                    for (int r = 0; r < 32; r++)
+                        if ((N >> r) & 1) {
+                            const int64_t t = 2 * (int64_t)m[r] + 1, q = t - rec2(m[r], p);
+                            dd += t * t - q * q;
+                        }
+                    dd = warp_sum64(dd);
+                    for (int s0 = 0; s0 < h; s0 += 4) {
+                        SymBuf sb;
+                        for (int r = s0; r < s0 + 4 && r < h; r++) {
+                            if (!((coded >> r) & 1)) continue;
+                            const int bit = (int)((B >> r) & 1);
+                            sb.put(sigt[v.pat(r)], bit);
+                            if (bit) sign_sym(sb, v, r);
+                        }
+                        emit(buf, cap, base, sb, lane, o.status);
+                    }
+                    code_pass(dd);
+                    SPPF |= N;
+                    S1 = SIG | N;
+                    VIS = coded;
+                    // ---- magnitude refinement of the coefficients significant before this plane
+                    const uint64_t S1L = __shfl_up_sync(0xffffffffu, S1, 1) * (lane > 0);
+                    const uint64_t S1R = __shfl_down_sync(0xffffffffu, S1, 1) * (lane < 31);
+                    const View vm = make_view(S1L, 0, S1, 0, S1R, 0);
+                    const uint64_t anyn = vm.any() | (S1 >> 1);  // Mdn already holds S1 >> 1
+                    dd = 0;
+#pragma unroll
+                    for (int r = 0; r < 32; r++)
+                        if ((SIG >> r) & 1) {
+                            const int64_t t = 2 * (int64_t)m[r] + 1, a2 = t - rec2(m[r], p + 1), c2 = t - rec2(m[r], p);
+                            dd += a2 * a2 - c2 * c2;
+                        }
+                    dd = warp_sum64(dd);
+                    for (int s0 = 0; s0 < h; s0 += 4) {
+                        SymBuf sb;
+                        for (int r = s0; r < s0 + 4 && r < h; r++) {
+                            if (!((SIG >> r) & 1)) continue;
+                            const int cx = ((REF >> r) & 1) ? 16 : (((anyn >> r) & 1) ? 15 : 14);
+                            sb.put(cx, (int)((B >> r) & 1));
+                        }
+                        emit(buf, cap, base, sb, lane, o.status);
+                    }
+                    code_pass(dd);
+                    REF |= SIG;
+                }
+                // ---- cleanup: every coefficient not significant and not coded yet in this plane
+                const uint64_t U = ~S1 & ~VIS & VALID;
+                const uint64_t Nc = U & B;
+                const uint64_t S1L = __shfl_up_sync(0xffffffffu, S1, 1) * (lane > 0);
+                const uint64_t S1R = __shfl_down_sync(0xffffffffu, S1, 1) * (lane < 31);
+                const uint64_t NcL = __shfl_up_sync(0xffffffffu, Nc, 1) * (lane > 0);
+                const uint64_t NcR = __shfl_down_sync(0xffffffffu, Nc, 1) * (lane < 31);
+                const View vc = make_view(S1L, NcL, S1, Nc, S1R, NcR);
+                // run-length test: neighbours at the moment the stripe column is reached
+                const uint64_t rl_nb = vc.Lup | vc.Lmid | vc.Ldn | vc.Rup | vc.Rmid | vc.Rdn | (S1 << 1) |
+                                       ((Nc << 1) & kStripeStart) | (S1 >> 1);
+                int64_t dd = 0;
+#pragma unroll
+                for (int r = 0; r < 32; r++)
+                    if ((Nc >> r) & 1) {
+                        const int64_t t = 2 * (int64_t)m[r] + 1, q = t - rec2(m[r], p);
+                        dd += t * t - q * q;
+                    }
+                dd = warp_sum64(dd);
+                for (int s0 = 0; s0 < h; s0 += 4) {
+                    SymBuf sb;
+                    int r = s0;
+                    const int r1 = s0 + 4 < h ? s0 + 4 : h;
+                    if (lane < w && r1 - s0 == 4 && ((U >> s0) & 0xF) == 0xF && ((rl_nb >> s0) & 0xF) == 0) {
+                        const int bits = (int)((B >> s0) & 0xF);
+                        if (!bits) {
+                            sb.put(17, 0);
+                            r = r1;
+                        } else {
+                            const int rr = __ffs(bits) - 1;
+                            sb.put(17, 1);
+                            sb.put(18, rr >> 1);
+                            sb.put(18, rr & 1);
+                            sign_sym(sb, vc, s0 + rr);
+                            r = s0 + rr + 1;
+                        }
+                    }
+                    for (; r < r1; r++) {
+                        if (!((U >> r) & 1)) continue;
+                        const int bit = (int)((B >> r) & 1);
+                        sb.put(sigt[vc.pat(r)], bit);
+                        if (bit) sign_sym(sb, vc, r);
+                    }
+                    emit(buf, cap, base, sb, lane, o.status);
+                }
+                code_pass(dd);
+                SIG = S1 | Nc;
+            }
+        }
+        // trace flags back (bit 30 of the Mallat array, or a byte array)
+#pragma unroll
+        for (int r = 0; r < 32; r++) {
+            if (lane < w && r < h) {
+                const uint32_t f = (uint32_t)((SPPF >> r) & 1);
+                const long long at = d.off + (long long)r * d.stride + lane;
+                if (mark_spp_in_q && INBQ(at, nq)) qt[at] = (qt[at] & ~0x40000000) | (int32_t)(f << 30);
+                if (spp_out) spp_out[(size_t)b * (w * h) + r * w + lane] = (uint8_t)f;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// MQ coding of the modelled symbols: one thread per code-block, so a warp
+// runs 32 blocks' arithmetic coders side by side; tables and context states
+// in shared memory.  At every pass end the coder state is terminated on a
+// copy (the stream length the rate search needs, with its tail bytes).
+constexpr int MQT = 128;
+
+__device__ __forceinline__ void mq_encode_t(MQEnc &e, uint8_t *I, uint8_t *M, const uint32_t *mq, const uint8_t *sw,
+                                            int cx, int d) {
+    const int i = I[cx];
+    const uint32_t ent = mq[i], qe = ent & 0xFFFF;
+    e.A -= qe;
+    if (d == M[cx]) {
+        if (e.A & 0x8000) { e.C += qe; return; }
+        if (e.A < qe) e.A = qe; else e.C += qe;
+        I[cx] = (uint8_t)((ent >> 16) & 0xFF);
+    } else {
+        if (e.A < qe) e.C += qe; else e.A = qe;
+        if (sw[i]) M[cx] ^= 1;
+        I[cx] = (uint8_t)(ent >> 24);
+    }
+    do {
+        e.A <<= 1; e.C <<= 1; e.CT--;
+        if (e.CT == 0) e.byteout();
+    } while (!(e.A & 0x8000));
+}
+
+__global__ void __launch_bounds__(MQT) t1_mq_kernel(int nblk, T1Out o) {
+    __shared__ uint32_t smq[48];
+    __shared__ uint8_t ssw[48];
+    __shared__ uint8_t ctx[MQT][40];
+    for (int k = threadIdx.x; k < 47; k += blockDim.x) { smq[k] = c_mq[k]; ssw[k] = c_mqsw[k]; }
+    __syncthreads();
+    const int b = blockIdx.x * MQT + threadIdx.x;
+    if (b >= nblk) return;
+    const int np = o.npass[b];
+    if (np <= 0) return;
+    uint8_t *I = ctx[threadIdx.x], *M = I + 20;
+    reset_ctx(I, M);
+    MQEnc e;
+    e.init(o.bytes + (size_t)b * o.cap, o.cap);
+    const uint8_t *sym = o.sym + (size_t)b * o.sym_cap;
+    const size_t pb = (size_t)b * o.maxpass;
+    int k = 0;
+    for (int pass = 0; pass < np && pass < o.maxpass; pass++) {
+        int end = o.pass_sym[pb + pass];
+        if (end > o.sym_cap) end = (int)o.sym_cap;
+        for (; k < end; k++) {
+            const int sy = sym[k];
+            mq_encode_t(e, I, M, smq, ssw, sy >> 1, sy & 1);
+        }
+        uint32_t tail;
+        int tl;
+        o.pass_len[pb + pass] = e.trunc(tail, tl);
+        o.tail[pb + pass] = tail;
+        o.tail_len[pb + pass] = tl;
+    }
+    if (e.overflow) atomicOr(o.status, 1);
+}
+
 // decode npass passes of each block; writes dequantised values into coef
 // (Mallat) when coef != null, else mag/plane/neg (packed per block)
 __global__ void __launch_bounds__(WARPS * 32) t1_decode_kernel(const uint8_t *bytes, const int64_t *off,
@@ -593,6 +944,14 @@ int t1_encode_blocks(int32_t *qt, const BlockDesc *blk, int nblk, int maxw, int 
     if (rc) return rc;
     if (nblk <= 0) return EBCC_OK;
     if (maxw > 64 || maxh > 64) return EBCC_EINVAL;
+    if (maxw <= 32 && maxh <= 32 && o.sym && o.pass_sym && o.sym_cap >= (long long)SYM_PER_COEF * maxw * maxh) {
+        const int g = (nblk + PW - 1) / PW;
+        PROF("t1_model_warp", st, 0.0, t1_model_warp<<<g < 152 * 64 ? g : 152 * 64, PW * 32, 0, st>>>(qt, blk, nblk, o, mark_spp_in_q, spp_out, nq));
+        CK(cudaGetLastError());
+        PROF("t1_mq_kernel", st, 0.0, t1_mq_kernel<<<(nblk + MQT - 1) / MQT, MQT, 0, st>>>(nblk, o));
+        CK(cudaGetLastError());
+        return EBCC_OK;
+    }
     SmemLayout SL = smem_layout(maxw * maxh, maxh, false);
     PROF("t1_encode_kernel", st, 0.0, t1_encode_kernel<<<grid_for(nblk), WARPS * 32, WARPS * SL.per_warp, st>>>(qt, blk, nblk, o, mark_spp_in_q,
                                                                              spp_out, SL, maxh, nq););

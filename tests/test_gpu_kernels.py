@@ -115,7 +115,8 @@ def _t1_blocks(rng, n, w, h):
     return out
 
 
-@pytest.mark.parametrize("wh", [(32, 32), (64, 64), (16, 16), (32, 64), (64, 32), (7, 5), (32, 13)])
+@pytest.mark.parametrize("wh", [(32, 32), (64, 64), (16, 16), (32, 64), (64, 32), (7, 5), (32, 13), (1, 1), (3, 32),
+                                (32, 3), (31, 30), (8, 4)])
 def test_tier1_encoder_bit_exact(B, wh):
     w, h = wh
     rng = np.random.default_rng(w * 100 + h)
