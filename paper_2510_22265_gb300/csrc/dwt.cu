@@ -341,7 +341,7 @@ int dwt_forward_b(const Live &lv, const FieldRun &one, int nslots, const BatchDi
                   cudaStream_t st) {
     if (nslots <= 0) return EBCC_OK;
     if (d.any_L0) {
-        fwd_identity<<<dim3(pgrid(d.maxN, nslots), nslots), NT, 0, st>>>(lv, one, src, norm);
+        PROF("fwd_identity", st, 0.0, fwd_identity<<<dim3(pgrid(d.maxN, nslots), nslots), NT, 0, st>>>(lv, one, src, norm));
         CK(cudaGetLastError());
     }
     for (int l = 1; l <= d.maxL; l++) {
@@ -361,7 +361,7 @@ int dwt_inverse_b(const Live &lv, const FieldRun &one, int nslots, const BatchDi
                   cudaStream_t st) {
     if (nslots <= 0) return EBCC_OK;
     if (d.any_L0) {
-        inv_identity<<<dim3(pgrid(d.maxN, nslots), nslots), NT, 0, st>>>(lv, one, src, fin);
+        PROF("inv_identity", st, 0.0, inv_identity<<<dim3(pgrid(d.maxN, nslots), nslots), NT, 0, st>>>(lv, one, src, fin));
         CK(cudaGetLastError());
     }
     for (int l = d.maxL; l >= 1; l--) {

@@ -578,7 +578,7 @@ Live live_of(const Batch &b) { return Live{b.d_run, b.live + 1, b.live}; }
 // host list -> device live list
 int set_list(Engine &e, Batch &b, const std::vector<int> &lst, cudaStream_t st) {
     RC(upload(e, b.list, lst.data(), lst.size() * sizeof(int), st));
-    set_live<<<1, 256, 0, st>>>(b.list, (int)lst.size(), b.live);
+    PROF("set_live", st, 0.0, set_live<<<1, 256, 0, st>>>(b.list, (int)lst.size(), b.live));
     CK(cudaGetLastError());
     return EBCC_OK;
 }
@@ -795,7 +795,7 @@ int run_base_loop(Engine &e, Batch &b, const std::vector<int> &A, double q, int 
     const int n = (int)A.size();
     if (!n) return EBCC_OK;
     RC(upload(e, b.list, A.data(), n * sizeof(int), st));
-    bl_start<<<(n + 255) / 256, 256, 0, st>>>(b.bl, b.d_run, b.list, n, q, fallback, p.r0, p.tol, b.hull, b.live);
+    PROF("bl_start", st, 0.0, bl_start<<<(n + 255) / 256, 256, 0, st>>>(b.bl, b.d_run, b.list, n, q, fallback, p.r0, p.tol, b.hull, b.live));
     CK(cudaGetLastError());
     int *slot = stage_take<int>(e, 2);
     if (!slot) return EBCC_ECAPACITY;
@@ -826,7 +826,7 @@ int run_trunc_loop(Engine &e, Batch &b, const std::vector<int> &A, cudaStream_t 
     const int n = (int)A.size();
     if (!n) return EBCC_OK;
     RC(set_list(e, b, A, st));
-    tl_start<<<1, 1024, 0, st>>>(b.tl, b.d_run, b.live);
+    PROF("tl_start", st, 0.0, tl_start<<<1, 1024, 0, st>>>(b.tl, b.d_run, b.live));
     CK(cudaGetLastError());
     int *slot = stage_take<int>(e, 2);
     if (!slot) return EBCC_ECAPACITY;
@@ -1021,7 +1021,7 @@ int compress_batch(Engine &e, const ebcc_field_desc *fd, int n, ebcc_out_desc *o
             RC(upload(e, b.es, esv.data(), F * sizeof(int), st));
             RC(set_list(e, b, S, st));
             const int ns = (int)S.size();
-            set_scalars<<<(ns + 255) / 256, 256, 0, st>>>(lv, b.es, 1);
+            PROF("set_scalars", st, 0.0, set_scalars<<<(ns + 255) / 256, 256, 0, st>>>(lv, b.es, 1));
             CK(cudaGetLastError());
             RC(spiht_quantise_b(lv, kNone, ns, b.dims.maxN, st));
             RC(spiht_encode_b(lv, kNone, ns, b.dims, st));
@@ -1210,7 +1210,7 @@ int decompress_batch(Engine &e, const ebcc_stream_desc *sd, int n, float *const 
         uint8_t *dh = carve<uint8_t>(e.a, (size_t)n * HDR_BYTES);
         CK(cudaMemcpyAsync(dp, hp, n * sizeof(void *), cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(dl, hl, n * sizeof(long long), cudaMemcpyHostToDevice, st));
-        hdr_gather<<<n, 64, 0, st>>>(dp, dl, n, dh);
+        PROF("hdr_gather", st, 0.0, hdr_gather<<<n, 64, 0, st>>>(dp, dl, n, dh));
         CK(cudaGetLastError());
         uint8_t *hh = nullptr;
         RC(download(e, dh, (size_t)n * HDR_BYTES, &hh, st));

@@ -301,9 +301,9 @@ unsigned sgrid(int nslots) { return (unsigned)((nslots + 255) / 256); }
 
 int minmax_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, cudaStream_t st) {
     if (nslots <= 0) return EBCC_OK;
-    mm_init<<<sgrid(nslots), 256, 0, st>>>(lv, one, nslots);
+    PROF("mm_init", st, 0.0, mm_init<<<sgrid(nslots), 256, 0, st>>>(lv, one, nslots));
     PROF("mm_kernel", st, 4.0 * maxN * nslots, mm_kernel<<<PGRID, NT, 0, st>>>(lv, one));
-    mm_final<<<sgrid(nslots), 256, 0, st>>>(lv, one, nslots);
+    PROF("mm_final", st, 0.0, mm_final<<<sgrid(nslots), 256, 0, st>>>(lv, one, nslots));
     CK(cudaGetLastError());
     return EBCC_OK;
 }
