@@ -186,7 +186,24 @@ __global__ void __launch_bounds__(IT) inv_level(Live lv, const __grid_constant__
     const int hl = (hp + 1) >> 1, wl = (wp + 1) >> 1;
     const int tid = threadIdx.x;
     __shared__ float t[EY][EX + 1];
-    if (tid < EX) {  // all EY loads of the column in flight, then the stores
+    // interior tile: the halo needs no reflection, every index is in range
+    const bool interior = ty0 >= HALO && tx0 >= HALO && ty0 + TY + HALO <= hp && tx0 + TX + HALO <= wp;
+    if (interior && tid < EX) {
+        // column gx = tx0 - HALO + tid has the parity of tid; even tile rows
+        // come from LL (even columns) or HL, odd rows from LH or HH
+        const int ph = tid & 1, sx = (tx0 - HALO + tid) >> 1, sy0 = (ty0 - HALO) >> 1;
+        const float *pe = ph ? coef + (size_t)sy0 * nx + wl + sx : ll + (size_t)sy0 * ls + sx;
+        const float *po = coef + (size_t)(hl + sy0) * nx + (ph ? wl : 0) + sx;
+        const int se = ph ? nx : ls;
+        float v[EY];
+#pragma unroll
+        for (int k = 0; k < EY / 2; k++) {
+            v[2 * k] = pe[(size_t)k * se];
+            v[2 * k + 1] = po[(size_t)k * nx];
+        }
+#pragma unroll
+        for (int ly = 0; ly < EY; ly++) t[ly][tid] = v[ly];
+    } else if (tid < EX) {  // all EY loads of the column in flight, then the stores
         const int gx = reflect(tx0 - HALO + tid, wp);
         const int ph = gx & 1, sx = gx >> 1;
         const int cx = sx + (ph ? wl : 0);  // column of the coefficient in the Mallat array
@@ -248,6 +265,19 @@ __global__ void __launch_bounds__(IT) inv_level(Live lv, const __grid_constant__
                 for (int rr = 0; rr < TY; rr++) {
                     const int i = (ty0 + rr) * ds + gx;
                     if (rr < nr && INBQ(i, lim)) dst[i] = w[HALO + rr];
+                }
+            } else if (mode == 1 && nr == TY) {  // base-loop count, full tile column
+                const float2 *__restrict__ bnd = r->bounds + (size_t)ty0 * nx + gx;
+#pragma unroll
+                for (int g0 = 0; g0 < TY; g0 += 16) {
+                    float2 bb[16];
+#pragma unroll
+                    for (int u = 0; u < 16; u++) bb[u] = bnd[(size_t)(g0 + u) * nx];
+#pragma unroll
+                    for (int u = 0; u < 16; u++) {
+                        const float v = w[HALO + g0 + u];
+                        cnt += (v >= bb[u].x && v <= bb[u].y);
+                    }
                 }
             } else if (mode == 1 || mode == 2) {  // counts: loads of a group in flight together
                 const float2 *__restrict__ bnd = r->bounds;

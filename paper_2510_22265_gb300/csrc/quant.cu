@@ -218,8 +218,15 @@ __global__ void __launch_bounds__(NT) bounds_kernel(Live lv, const __grid_consta
             }
             if (!found) { bounds[i] = make_float2(1.0f, 0.0f); continue; }  // empty interval
         }
-        int32_t ghi = f2o(__double2float_rn((x + E - mn) * inv));
-        int32_t glo = f2o(__double2float_rn((x - E - mn) * inv));
+        // guesses that account for the float32 rounding of the output: the
+        // output rounds to at most T = the float just below x + E exactly when
+        // mn + a * range stays below the midpoint of T and the next float up
+        // (and symmetrically at x - E); the searches below make them exact
+        const float Th = __double2float_rd(x + E), Tl = __double2float_ru(x - E);
+        const double mh = 0.5 * ((double)Th + (double)nextafterf(Th, INFINITY));
+        const double ml = 0.5 * ((double)Tl + (double)nextafterf(Tl, -INFINITY));
+        int32_t ghi = f2o(__double2float_rd((mh - mn) * inv));
+        int32_t glo = f2o(__double2float_ru((ml - mn) * inv));
         int32_t hi = edge(o0, ghi, +1, x, mn, range, E);
         int32_t lo = edge(o0, glo, -1, x, mn, range, E);
         bounds[i] = make_float2(o2f(lo), o2f(hi));
