@@ -108,6 +108,50 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+# ------------------------------------------------------------------ serving
+def serving_leg(B, fields, rate, window, budget_gb, max_batch):
+    """Poisson stream of mixed requests (70% compress, 30% decompress of streams
+    made beforehand) over the workload's fields, bounds drawn from {0.1, 1, 10}%,
+    admitted by the server under an HBM budget; latency from submit to result."""
+    arrivals = synth.poisson_arrivals(rate, window, seed=5)
+    pool = fields[:16]
+    made = {}
+    for i, f in enumerate(pool):
+        for b in (1e-3, 1e-2, 1e-1):
+            made[(i, b)] = B.ebcc_compress(f, b)[0]
+    lat, qs, raw = [], [], 0
+    done_t = []
+    with B.Server(int(budget_gb * (1 << 30)), max_batch) as srv:
+        tickets = []
+        t0 = time.perf_counter()
+        for k, (t, is_c, b) in enumerate(arrivals):
+            now = time.perf_counter() - t0
+            if t > now:
+                time.sleep(t - now)
+            i = k % len(pool)
+            if is_c:
+                tickets.append((srv.submit_compress(pool[i], b), pool[i].shape))
+            else:
+                tickets.append((srv.submit_decompress(made[(i, b)], *pool[i].shape), pool[i].shape))
+            raw += pool[i].nbytes
+        for tk, shape in tickets:
+            r = None
+            while r is None:
+                r = srv.poll(tk, 1.0, shape=shape)
+            assert r["status"] == 0, r["status"]
+            lat.append(r["latency_s"])
+            qs.append(r["queue_s"])
+            done_t.append(time.perf_counter() - t0)
+        wall = max(done_t)
+    lat = np.array(lat) * 1e3
+    return {"rate_req_s": rate, "window_s": window, "requests": len(arrivals),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "queue_p50_ms": float(np.percentile(np.array(qs) * 1e3, 50)),
+            "sustained_gbs": raw / wall / 1e9, "hbm_budget_gb": budget_gb, "max_batch": max_batch,
+            "what": "721x1440 fields, 70% compress / 30% decompress, bounds {0.1,1,10}%, Poisson arrivals, "
+                    "latency = submit to result inside the library"}
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
@@ -200,6 +244,9 @@ def run_gpu(args):
         e2e_in += f.numel() * 4
         e2e_out += len(s)
     t_e2e = time.perf_counter() - t
+    serving = None
+    if not args.no_serve:
+        serving = serving_leg(B, fields, args.serve_rate, args.serve_window, 40.0, 64)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -228,7 +275,7 @@ def run_gpu(args):
         "e2e": {"value": e2e_in / t_e2e / 1e9, "unit": "GB/s", "h2d_bytes_per_step": e2e_in,
                 "d2h_bytes_per_step": e2e_out, "fields": len(hfields)},
         "gpu_launches": int(sum(p["launches"] for p in prof)) // max(1, args.steps) if prof else None,
-        "roofline": roof, "kernels": prof, "clocks": clk.summary(), "cpu_baseline": cpu,
+        "roofline": roof, "serving": serving, "kernels": prof, "clocks": clk.summary(), "cpu_baseline": cpu,
     }
     print(json.dumps(line))
     if dist:
@@ -266,6 +313,9 @@ def main():
                     help="variables levels ny nx")
     ap.add_argument("--e2e-fields", type=int, default=16)
     ap.add_argument("--plain-fields", type=int, default=8)
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="serving leg: mean requests per second")
+    ap.add_argument("--serve-window", type=float, default=0.5, help="serving leg: seconds of arrivals")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -318,3 +318,66 @@ def ebcc_spiht_prefix_recon_dev(s, sig_pos, lsp_idx, refine_start, nbits, step_e
 def ebcc_count_within_dev(x, an_hat, mn, rng, eps_abs, guard, count_out, stream=None):
     _check(lib().ebcc_count_within_dev(_ptr(x), _ptr(an_hat), x.numel(), mn, rng, eps_abs, guard, _ptr(count_out),
                                        C.c_void_p(_stream(stream))), "ebcc_count_within_dev")
+
+
+# ------------------------------------------------------------------ serving
+EBCC_REQ_COMPRESS, EBCC_REQ_DECOMPRESS = 0, 1
+
+
+class Server:
+    """ebcc_server_*: requests are copied at submit, admitted while the device
+    workspace stays within the HBM budget, and each admitted group runs as one
+    compression batch and one decompression batch."""
+
+    def __init__(self, hbm_budget_bytes: int, max_batch: int = 0, p: ebcc_params | None = None):
+        h = C.c_void_p()
+        _check(lib().ebcc_server_create(int(hbm_budget_bytes), int(max_batch), C.byref(p) if p is not None else None,
+                                        C.byref(h)), "ebcc_server_create")
+        self.h = h
+
+    def submit_compress(self, field: np.ndarray, bound: float, kind: int = EBCC_BOUND_REL) -> int:
+        f = np.ascontiguousarray(field, dtype=np.float32)
+        ny, nx = f.shape
+        r = ebcc_request(EBCC_REQ_COMPRESS, f.ctypes.data, None, 0, ny, nx, float(bound), int(kind))
+        t = C.c_uint64()
+        _check(lib().ebcc_server_submit(self.h, C.byref(r), C.byref(t)), "ebcc_server_submit")
+        return int(t.value)
+
+    def submit_decompress(self, stream: bytes, ny: int, nx: int) -> int:
+        buf = (C.c_uint8 * len(stream)).from_buffer_copy(stream)
+        r = ebcc_request(EBCC_REQ_DECOMPRESS, None, C.cast(buf, C.c_void_p), len(stream), ny, nx, 0.0, 0)
+        t = C.c_uint64()
+        _check(lib().ebcc_server_submit(self.h, C.byref(r), C.byref(t)), "ebcc_server_submit")
+        return int(t.value)
+
+    def poll(self, ticket: int, timeout_s: float = 0.0, shape=None):
+        """None while the request runs; else a dict with status, the stream
+        (compress) or the field (decompress, given its shape), latency_s, queue_s."""
+        res = ebcc_result()
+        rc = lib().ebcc_server_poll(self.h, C.c_uint64(ticket), float(timeout_s), C.byref(res))
+        if rc == EBCC_ETIMEOUT:
+            return None
+        _check(rc, "ebcc_server_poll")
+        out = {"status": res.status, "latency_s": res.latency_s, "queue_s": res.queue_s, "stream": None, "field": None}
+        if res.stream:
+            out["stream"] = C.string_at(res.stream, res.stream_len)
+            lib().ebcc_free(res.stream)
+        if res.field:
+            n = int(np.prod(shape)) if shape is not None else 0
+            if n:
+                arr = np.ctypeslib.as_array(C.cast(res.field, C.POINTER(C.c_float)), shape=(n,))
+                out["field"] = arr.copy().reshape(shape)
+            lib().ebcc_free(res.field)
+        return out
+
+    def close(self):
+        if self.h:
+            lib().ebcc_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
