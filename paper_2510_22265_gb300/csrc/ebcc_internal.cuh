@@ -291,9 +291,11 @@ int minmax_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, cu
 int quantise_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, int sign_magnitude, cudaStream_t st);
 // W = base reconstruction for npass (batch-wide per-block arrays K, npass);
 // one warp per code-block of the listed fields (blocks from blk, absolute
-// offsets into the batch-wide planes starting at qt0 / W0)
+// offsets into the batch-wide planes starting at qt0 / W0).  done (optional):
+// the pass count each block of W currently holds (-1 = none); blocks whose
+// count is unchanged are skipped and the array is brought up to date
 int base_recon_b(const Live &lv, int nslots, int maxnblk, const BlockDesc *blk, const int32_t *qt0, float *W0,
-                 const int32_t *K, const int32_t *npass, long long ntot, cudaStream_t st);
+                 const int32_t *K, const int32_t *npass, int32_t *done, long long ntot, cudaStream_t st);
 int make_bounds_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, cudaStream_t st);
 // R = (x - mn) / range - Abase in FP64, rounded to float
 int residue_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, cudaStream_t st);

@@ -558,6 +558,7 @@ struct Batch {
     T1Out t1{};
     Hulls hull{};
     int32_t *npass = nullptr;
+    int32_t *w_npass = nullptr;     // pass count each block's W currently holds (-1: W holds something else)
     uint32_t *meta_off = nullptr, *pay_off = nullptr;
     int64_t *addr = nullptr;        // decoder: payload address per block
     BaseLoop *bl = nullptr;
@@ -639,6 +640,7 @@ void layout_compress(Arena &a, Batch &b, const std::vector<int> &ny, const std::
     b.hull.sdr2 = carve<uint32_t>(a, nb * T1_MAXPASS);
     b.hull.cum = carve<unsigned long long>(a, nb * T1_MAXPASS);
     b.npass = carve<int32_t>(a, nb);
+    b.w_npass = carve<int32_t>(a, nb);
     b.meta_off = carve<uint32_t>(a, nb);
     b.pay_off = carve<uint32_t>(a, nb);
     b.d_blk = carve<BlockDesc>(a, nb);
@@ -782,9 +784,16 @@ int check_shape(size_t ny, size_t nx) {
 }
 
 // ------------------------------------------------------------ the two loops
+// W was written by something other than the base reconstruction
+int w_invalidate(Batch &b, cudaStream_t st) {
+    CK(cudaMemsetAsync(b.w_npass, 0xFF, ((size_t)b.Btot + 1) * sizeof(int32_t), st));
+    return EBCC_OK;
+}
+
 // inverse DWT of the base reconstruction for the kept passes b.npass
 int base_eval(Batch &b, const Live &lv, int nslots, InvFinal fin, cudaStream_t st) {
-    RC(base_recon_b(lv, nslots, b.dims.maxnblk, b.d_blk, b.run[0].qt, b.run[0].W, b.t1.K, b.npass, b.Ntot, st));
+    RC(base_recon_b(lv, nslots, b.dims.maxnblk, b.d_blk, b.run[0].qt, b.run[0].W, b.t1.K, b.npass, b.w_npass, b.Ntot,
+                    st));
     return dwt_inverse_b(lv, kNone, nslots, b.dims, PL_W, fin, st);
 }
 
@@ -989,6 +998,7 @@ int compress_batch(Engine &e, const ebcc_field_desc *fd, int n, ebcc_out_desc *o
         RC(pcrd_prepare_b(lv, kNone, na, b.hull, st));
         STAGE(st, "hulls");
         // ---- base loop with q
+        RC(w_invalidate(b, st));  // W holds the forward transform
         RC(run_base_loop(e, b, A, p.q, 0, p, st));
         BaseLoop *hb = nullptr;
         RC(download(e, b.bl, F, &hb, st));
@@ -1012,6 +1022,7 @@ int compress_batch(Engine &e, const ebcc_field_desc *fd, int n, ebcc_out_desc *o
         RC(base_eval(b, lv, na, InvFinal{0, 0, PL_ABASE, 0}, st));
         RC(residue_b(lv, kNone, na, b.dims.maxN, st));
         RC(dwt_forward_b(lv, kNone, na, b.dims, PL_R, 0, st));
+        RC(w_invalidate(b, st));  // W now holds the residual's transform
         STAGE(st, "residue dwt");
         for (int f : A) sel_two[f] = hb1[f].sel_f;
         // ---- SPIHT with guard retries: step 2^(floor(log2 eps_n) - G)
@@ -1049,6 +1060,7 @@ int compress_batch(Engine &e, const ebcc_field_desc *fd, int n, ebcc_out_desc *o
             RC(set_list(e, b, X, st));
             Live lv = live_of(b);
             RC(dwt_inverse_b(lv, kNone, (int)X.size(), b.dims, PL_R, InvFinal{0, 0, PL_W, 0}, st));
+            RC(w_invalidate(b, st));
             PROF("escape_kernel", st, 0.0, escape_kernel<<<(int)X.size(), 1024, 0, st>>>(lv));
             CK(cudaGetLastError());
             RC(download(e, b.d_sc, F, &hs, st));

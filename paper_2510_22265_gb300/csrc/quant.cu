@@ -124,14 +124,16 @@ constexpr int RW = 8;  // warps (code-blocks) per reconstruction CTA
 __global__ void __launch_bounds__(RW * 32) recon_kernel(Live lv, const BlockDesc *__restrict__ blk,
                                                         const int32_t *__restrict__ qt0, float *__restrict__ W0,
                                                         const int32_t *__restrict__ Kb, const int32_t *__restrict__ npb,
-                                                        long long ntot) {
+                                                        int32_t *__restrict__ done, long long ntot) {
     if ((int)blockIdx.y >= *lv.n) return;
     const FieldRun &r = lv.tab[lv.idx[blockIdx.y]];
     const int lb = blockIdx.x * RW + (threadIdx.x >> 5);
     if (lb >= r.nblk) return;
     const int b = r.blk0 + lb;
-    const BlockDesc d = blk[b];
     const int K = Kb[b], np = npb[b];
+    // W already holds this block for np kept passes: nothing to do
+    if (done && done[b] == np) return;
+    const BlockDesc d = blk[b];
     const int lane = threadIdx.x & 31;
     for (int c = lane; c < d.w; c += 32) {
         for (int r0 = 0; r0 < d.h; r0 += 8) {  // eight loads in flight per lane
@@ -148,6 +150,7 @@ __global__ void __launch_bounds__(RW * 32) recon_kernel(Live lv, const BlockDesc
             }
         }
     }
+    if (done && (threadIdx.x & 31) == 0) done[b] = np;
 }
 
 __device__ __forceinline__ int32_t f2o(float f) {
@@ -323,10 +326,10 @@ int quantise_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, 
 }
 
 int base_recon_b(const Live &lv, int nslots, int maxnblk, const BlockDesc *blk, const int32_t *qt0, float *W0,
-                 const int32_t *K, const int32_t *npass, long long ntot, cudaStream_t st) {
+                 const int32_t *K, const int32_t *npass, int32_t *done, long long ntot, cudaStream_t st) {
     if (nslots <= 0 || maxnblk <= 0) return EBCC_OK;
     dim3 grid((maxnblk + RW - 1) / RW, nslots);
-    PROF("recon_kernel", st, 0.0, recon_kernel<<<grid, RW * 32, 0, st>>>(lv, blk, qt0, W0, K, npass, ntot));
+    PROF("recon_kernel", st, 0.0, recon_kernel<<<grid, RW * 32, 0, st>>>(lv, blk, qt0, W0, K, npass, done, ntot));
     CK(cudaGetLastError());
     return EBCC_OK;
 }
