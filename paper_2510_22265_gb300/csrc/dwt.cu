@@ -167,7 +167,7 @@ constexpr int IT = 96;  // threads of an inverse-level CTA (72 stage the tile's 
 // finished output per fin.  Thread c < EX stages column c of the extended
 // tile (its source column is fixed, rows step down), then each row and each
 // column is lifted in registers by one thread.
-__global__ void __launch_bounds__(IT) inv_level(Live lv, const __grid_constant__ FieldRun one, int l, int src_plane,
+__global__ void __launch_bounds__(IT, 10) inv_level(Live lv, const __grid_constant__ FieldRun one, int l, int src_plane,
                                                 InvFinal fin) {
     int f;
     const FieldRun *r = pick(lv, one, blockIdx.z, f);
