@@ -471,10 +471,18 @@ __device__ __forceinline__ int64_t warp_sum64(int64_t v) {
 __global__ void __launch_bounds__(PW * 32) t1_model_warp(int32_t *qt, const BlockDesc *blk, int nblk, T1Out o,
                                                          int mark_spp_in_q, uint8_t *spp_out, long long nq) {
     __shared__ PWShared tb;
+    __shared__ uint32_t smag[PW][32][33];  // each warp's block, column-major by lane (for distortion sums)
     for (int k = threadIdx.x; k < 4 * 256; k += blockDim.x) tb.sig[k >> 8][k & 255] = c_sigctx[k >> 8][k & 255];
     for (int k = threadIdx.x; k < 256; k += blockDim.x) tb.sgn[k] = c_signctx[k];
     __syncthreads();
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t(*mg)[33] = smag[wid];
+    // sum over the coefficients of mask of f(magnitude), one lane's column
+    auto dsum = [&](uint64_t mask, auto f) -> int64_t {
+        int64_t acc = 0;
+        for (; mask; mask &= mask - 1) acc += f((int64_t)mg[__ffsll((long long)mask) - 1][lane]);
+        return acc;
+    };
     for (int b = blockIdx.x * PW + wid; b < nblk; b += gridDim.x * PW) {
         const BlockDesc d = blk[b];
         const int w = d.w, h = d.h;
@@ -496,7 +504,9 @@ __global__ void __launch_bounds__(PW * 32) t1_model_warp(int32_t *qt, const Bloc
                 const int64_t t = 2 * (int64_t)m[r] + 1;
                 d0 += t * t;
             }
+            mg[r][lane] = m[r];
         }
+        __syncwarp();
 #pragma unroll
         for (int s2 = 16; s2; s2 >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, s2));
         d0 = warp_sum64(d0);
@@ -559,13 +569,10 @@ __global__ void __launch_bounds__(PW * 32) t1_model_warp(int32_t *qt, const Bloc
                         v = make_view(SL, NL, SIG, N, SR, NR);
                     }
                     const uint64_t coded = ~SIG & VALID & v.any();
-                    int64_t dd = 0;
-#pragma unroll
-                    for (int r = 0; r < 32; r++)
-                        if ((N >> r) & 1) {
-                            const int64_t t = 2 * (int64_t)m[r] + 1, q = t - rec2(m[r], p);
-                            dd += t * t - q * q;
-                        }
+                    int64_t dd = dsum(N, [&](int64_t mm) {
+                        const int64_t t = 2 * mm + 1, q = t - rec2(mm, p);
+                        return t * t - q * q;
+                    });
                     dd = warp_sum64(dd);
                     for (int s0 = 0; s0 < h; s0 += 4) {
                         SymBuf sb;
@@ -586,13 +593,10 @@ __global__ void __launch_bounds__(PW * 32) t1_model_warp(int32_t *qt, const Bloc
                     const uint64_t S1R = __shfl_down_sync(0xffffffffu, S1, 1) * (lane < 31);
                     const View vm = make_view(S1L, 0, S1, 0, S1R, 0);
                     const uint64_t anyn = vm.any() | (S1 >> 1);  // Mdn already holds S1 >> 1
-                    dd = 0;
-#pragma unroll
-                    for (int r = 0; r < 32; r++)
-                        if ((SIG >> r) & 1) {
-                            const int64_t t = 2 * (int64_t)m[r] + 1, a2 = t - rec2(m[r], p + 1), c2 = t - rec2(m[r], p);
-                            dd += a2 * a2 - c2 * c2;
-                        }
+                    dd = dsum(SIG, [&](int64_t mm) {
+                        const int64_t t = 2 * mm + 1, a2 = t - rec2(mm, p + 1), c2 = t - rec2(mm, p);
+                        return a2 * a2 - c2 * c2;
+                    });
                     dd = warp_sum64(dd);
                     for (int s0 = 0; s0 < h; s0 += 4) {
                         SymBuf sb;
@@ -617,13 +621,10 @@ __global__ void __launch_bounds__(PW * 32) t1_model_warp(int32_t *qt, const Bloc
                 // run-length test: neighbours at the moment the stripe column is reached
                 const uint64_t rl_nb = vc.Lup | vc.Lmid | vc.Ldn | vc.Rup | vc.Rmid | vc.Rdn | (S1 << 1) |
                                        ((Nc << 1) & kStripeStart) | (S1 >> 1);
-                int64_t dd = 0;
-#pragma unroll
-                for (int r = 0; r < 32; r++)
-                    if ((Nc >> r) & 1) {
-                        const int64_t t = 2 * (int64_t)m[r] + 1, q = t - rec2(m[r], p);
-                        dd += t * t - q * q;
-                    }
+                int64_t dd = dsum(Nc, [&](int64_t mm) {
+                    const int64_t t = 2 * mm + 1, q = t - rec2(mm, p);
+                    return t * t - q * q;
+                });
                 dd = warp_sum64(dd);
                 for (int s0 = 0; s0 < h; s0 += 4) {
                     SymBuf sb;
