@@ -136,3 +136,32 @@ def test_era5_shaped_full_size(B):
             s, st = B.ebcc_compress(x, b)
             assert _within(x, O.decompress(s, *x.shape), eps)
             assert _within(x, B.ebcc_decompress(s, *x.shape), eps)
+
+
+def test_uneven_batch_one_call(B):
+    # fields of uneven grids and mixed bounds in one batch: every stream equals
+    # the same field compressed alone and decodes on the oracle within its bound
+    spec = synth.batch_spec(12, seed=7)
+    grids = [(91, 180), (181, 360), (33, 65), (361, 720), (64, 48)]
+    fields, bounds = [], []
+    for k, (_, b, seed) in enumerate(spec):
+        ny, nx = grids[k % len(grids)]
+        fields.append(synth.smooth_field(ny, nx, seed=seed % 100000))
+        bounds.append(b)
+    rc, res = B.ebcc_compress_batch_dev([torch.from_numpy(f).cuda() for f in fields], bounds)
+    assert rc == 0
+    for (buf, ln, st, _), f, b in zip(res, fields, bounds):
+        assert st == 0
+        s = bytes(buf[:ln].cpu().numpy())
+        assert s == B.ebcc_compress(f, b)[0]
+        assert _within(f, O.decompress(s, *f.shape), b * (float(f.max()) - float(f.min())))
+
+
+@pytest.mark.slow
+def test_high_resolution_spiky_field(B):
+    # 3601 x 7200 with 1% heavy-tailed spikes at a 1% bound
+    x = synth.smooth_field(3601, 7200, seed=4, kscale=4.0, spikes=0.01)
+    eps = 1e-2 * (float(x.max()) - float(x.min()))
+    s, st = B.ebcc_compress(x, 1e-2)
+    assert _within(x, B.ebcc_decompress(s, *x.shape), eps)
+    assert _within(x, O.decompress(s, *x.shape), eps)
