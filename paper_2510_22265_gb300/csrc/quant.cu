@@ -211,6 +211,22 @@ __global__ void __launch_bounds__(NT) bounds_kernel(Live lv, const __grid_consta
     const long long n = r->N;
     for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
         const double x = xs[i];
+        // guesses that account for the float32 rounding of the output: the
+        // output rounds to at most T = the float just below x + E exactly when
+        // mn + a * range stays below the midpoint of T and the next float up
+        // (and symmetrically at x - E)
+        const float Th = __double2float_rd(x + E), Tl = __double2float_ru(x - E);
+        const double mh = 0.5 * ((double)Th + (double)nextafterf(Th, INFINITY));
+        const double ml = 0.5 * ((double)Tl + (double)nextafterf(Tl, -INFINITY));
+        const int32_t ghi = f2o(__double2float_rd((mh - mn) * inv));
+        const int32_t glo = f2o(__double2float_ru((ml - mn) * inv));
+        // the ok values form one interval: both guesses ok and their outer
+        // neighbours not ok pins both edges exactly
+        if (point_ok(o2f(ghi), x, mn, range, E) && point_ok(o2f(glo), x, mn, range, E) &&
+            !point_ok(o2f(ghi + 1), x, mn, range, E) && !point_ok(o2f(glo - 1), x, mn, range, E)) {
+            bounds[i] = make_float2(o2f(glo), o2f(ghi));
+            continue;
+        }
         float a0 = __double2float_rn((x - mn) * inv);
         int32_t o0 = f2o(a0);
         if (!point_ok(a0, x, mn, range, E)) {
@@ -221,15 +237,7 @@ __global__ void __launch_bounds__(NT) bounds_kernel(Live lv, const __grid_consta
             }
             if (!found) { bounds[i] = make_float2(1.0f, 0.0f); continue; }  // empty interval
         }
-        // guesses that account for the float32 rounding of the output: the
-        // output rounds to at most T = the float just below x + E exactly when
-        // mn + a * range stays below the midpoint of T and the next float up
-        // (and symmetrically at x - E); the searches below make them exact
-        const float Th = __double2float_rd(x + E), Tl = __double2float_ru(x - E);
-        const double mh = 0.5 * ((double)Th + (double)nextafterf(Th, INFINITY));
-        const double ml = 0.5 * ((double)Tl + (double)nextafterf(Tl, -INFINITY));
-        int32_t ghi = f2o(__double2float_rd((mh - mn) * inv));
-        int32_t glo = f2o(__double2float_ru((ml - mn) * inv));
+        // otherwise search from the guesses (galloping, then bisection)
         int32_t hi = edge(o0, ghi, +1, x, mn, range, E);
         int32_t lo = edge(o0, glo, -1, x, mn, range, E);
         bounds[i] = make_float2(o2f(lo), o2f(hi));

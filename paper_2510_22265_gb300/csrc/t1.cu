@@ -74,6 +74,19 @@ struct MQEnc {
             if (CT == 0) byteout();
         } while (!(A & 0x8000));
     }
+    // the same renormalisation with the shift count taken from the leading
+    // zeros of A (C moves the same distance, a byte out whenever CT runs out)
+    __device__ __forceinline__ void renorm() {
+        int n = __clz(A) - 16;
+        A <<= n;
+        while (n > 0) {
+            const int s = n < CT ? n : CT;
+            C <<= s;
+            CT -= s;
+            n -= s;
+            if (CT == 0) byteout();
+        }
+    }
     // terminate a copy of the state (SETBITS, two BYTEOUTs, drop a final 0xFF)
     __device__ int trunc(uint32_t &tail, int &tl) const {
         uint32_t a = A, c = C, b = B;
@@ -676,30 +689,32 @@ __global__ void __launch_bounds__(PW * 32) t1_model_warp(int32_t *qt, const Bloc
 // copy (the stream length the rate search needs, with its tail bytes).
 constexpr int MQT = 128;
 
+// one MQ symbol: the common MPS case without renormalisation returns early;
+// otherwise the interval update is a select (T.800 C.2: the conditional
+// exchange swaps which sub-interval is coded, the state transition depends
+// only on MPS / LPS) and one renormalisation
 __device__ __forceinline__ void mq_encode_t(MQEnc &e, uint8_t *I, uint8_t *M, const uint32_t *mq, const uint8_t *sw,
                                             int cx, int d) {
     const int i = I[cx];
     const uint32_t ent = mq[i], qe = ent & 0xFFFF;
-    e.A -= qe;
-    if (d == M[cx]) {
-        if (e.A & 0x8000) { e.C += qe; return; }
-        if (e.A < qe) e.A = qe; else e.C += qe;
-        I[cx] = (uint8_t)((ent >> 16) & 0xFF);
-    } else {
-        if (e.A < qe) e.C += qe; else e.A = qe;
-        if (sw[i]) M[cx] ^= 1;
-        I[cx] = (uint8_t)(ent >> 24);
+    const uint32_t A = e.A - qe;
+    const bool mps = d == M[cx];
+    if (mps && (A & 0x8000)) {
+        e.A = A;
+        e.C += qe;
+        return;
     }
-    do {
-        e.A <<= 1; e.C <<= 1; e.CT--;
-        if (e.CT == 0) e.byteout();
-    } while (!(e.A & 0x8000));
+    const bool small = A < qe;
+    if (mps != small) { e.A = A; e.C += qe; } else { e.A = qe; }
+    I[cx] = (uint8_t)(mps ? ((ent >> 16) & 0xFF) : (ent >> 24));
+    if (!mps && sw[i]) M[cx] ^= 1;
+    e.renorm();
 }
 
 __global__ void __launch_bounds__(MQT) t1_mq_kernel(int nblk, T1Out o) {
     __shared__ uint32_t smq[48];
     __shared__ uint8_t ssw[48];
-    __shared__ uint8_t ctx[MQT][40];
+    __shared__ uint8_t ctx[MQT][44];  // 11 words per thread: no bank conflicts
     for (int k = threadIdx.x; k < 47; k += blockDim.x) { smq[k] = c_mq[k]; ssw[k] = c_mqsw[k]; }
     __syncthreads();
     const int b = blockIdx.x * MQT + threadIdx.x;
@@ -710,21 +725,28 @@ __global__ void __launch_bounds__(MQT) t1_mq_kernel(int nblk, T1Out o) {
     reset_ctx(I, M);
     MQEnc e;
     e.init(o.bytes + (size_t)b * o.cap, o.cap);
+    // one loop over all the block's symbols; a pass end is recorded when the
+    // symbol count reaches it, so lanes are not held together pass by pass
     const uint8_t *sym = o.sym + (size_t)b * o.sym_cap;
     const size_t pb = (size_t)b * o.maxpass;
-    int k = 0;
-    for (int pass = 0; pass < np && pass < o.maxpass; pass++) {
-        int end = o.pass_sym[pb + pass];
-        if (end > o.sym_cap) end = (int)o.sym_cap;
-        for (; k < end; k++) {
-            const int sy = sym[k];
-            mq_encode_t(e, I, M, smq, ssw, sy >> 1, sy & 1);
+    const int npp = np < o.maxpass ? np : o.maxpass;
+    int total = o.pass_sym[pb + npp - 1];
+    if (total > o.sym_cap) total = (int)o.sym_cap;
+    int pass = 0;
+    int end = o.pass_sym[pb];
+    for (int k = 0;; k++) {
+        while (pass < npp && k >= end) {  // pass `pass` ends here (possibly empty)
+            uint32_t tail;
+            int tl;
+            o.pass_len[pb + pass] = e.trunc(tail, tl);
+            o.tail[pb + pass] = tail;
+            o.tail_len[pb + pass] = tl;
+            pass++;
+            if (pass < npp) end = o.pass_sym[pb + pass];
         }
-        uint32_t tail;
-        int tl;
-        o.pass_len[pb + pass] = e.trunc(tail, tl);
-        o.tail[pb + pass] = tail;
-        o.tail_len[pb + pass] = tl;
+        if (k >= total) break;
+        const int sy = sym[k];
+        mq_encode_t(e, I, M, smq, ssw, sy >> 1, sy & 1);
     }
     if (e.overflow) atomicOr(o.status, 1);
 }
@@ -945,7 +967,9 @@ int t1_encode_blocks(int32_t *qt, const BlockDesc *blk, int nblk, int maxw, int 
     if (rc) return rc;
     if (nblk <= 0) return EBCC_OK;
     if (maxw > 64 || maxh > 64) return EBCC_EINVAL;
-    if (maxw <= 32 && maxh <= 32 && o.sym && o.pass_sym && o.sym_cap >= (long long)SYM_PER_COEF * maxw * maxh) {
+    // the split coder reads each block's symbols in aligned 16-byte chunks
+    if (maxw <= 32 && maxh <= 32 && o.sym && o.pass_sym && o.sym_cap >= (long long)SYM_PER_COEF * maxw * maxh &&
+        o.sym_cap % 16 == 0 && ((uintptr_t)o.sym & 15) == 0) {
         const int g = (nblk + PW - 1) / PW;
         PROF("t1_model_warp", st, 0.0, t1_model_warp<<<g < 152 * 64 ? g : 152 * 64, PW * 32, 0, st>>>(qt, blk, nblk, o, mark_spp_in_q, spp_out, nq));
         CK(cudaGetLastError());
