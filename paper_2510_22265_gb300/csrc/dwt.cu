@@ -35,46 +35,13 @@ __device__ __forceinline__ int reflect(int i, int n) {
     return i >= n ? p - i : i;
 }
 
-// one lifting step on rows of parity `par` (local index parity == global parity)
-template <bool VERT>
-__device__ __forceinline__ void lift(float (*t)[EX + 1], int par, float c, int lo, int hi) {
-    // VERT: update rows ly of parity par in [1, EY-2], columns [lo, hi)
-    // !VERT: update columns lx of parity par in [1, EX-2], rows [lo, hi)
-    const int nrow = VERT ? (EY - 1 - par) / 2 : (hi - lo);
-    const int ncol = VERT ? (hi - lo) : (EX - 1 - par) / 2;
-    for (int k = threadIdx.x; k < nrow * ncol; k += NT) {
-        int a = k / ncol, b = k % ncol;
-        if (VERT) {
-            int ly = par ? 1 + 2 * a : 2 + 2 * a;
-            int lx = lo + b;
-            if (ly <= EY - 2) t[ly][lx] += c * (t[ly - 1][lx] + t[ly + 1][lx]);
-        } else {
-            int ly = lo + a;
-            int lx = par ? 1 + 2 * b : 2 + 2 * b;
-            if (lx <= EX - 2) t[ly][lx] += c * (t[ly][lx - 1] + t[ly][lx + 1]);
-        }
-    }
-}
-
-template <bool VERT>
-__device__ __forceinline__ void scale(float (*t)[EX + 1], float even_f, float odd_f, int lo, int hi) {
-    const int n = VERT ? EY * (hi - lo) : (hi - lo) * EX;
-    for (int k = threadIdx.x; k < n; k += NT) {
-        int ly, lx;
-        if (VERT) { ly = k / (hi - lo); lx = lo + k % (hi - lo); }
-        else { ly = lo + k / EX; lx = k % EX; }
-        int par = VERT ? (ly & 1) : (lx & 1);
-        t[ly][lx] *= par ? odd_f : even_f;
-    }
-}
-
 __device__ __forceinline__ int ceil_sh(int n, int l) { return (int)(((long long)n + (1LL << l) - 1) >> l); }
 
 // forward level l of the field in grid slot blockIdx.z: the level's input
 // (plane `src` at level 1, else the LL scratch of level l - 1) -> detail bands
 // into W, LL into the scratch of level l (into W at the last level)
 template <bool NORM>
-__global__ void __launch_bounds__(NT) fwd_level(Live lv, const __grid_constant__ FieldRun one, int l, int src_plane) {
+__global__ void __launch_bounds__(96) fwd_level(Live lv, const __grid_constant__ FieldRun one, int l, int src_plane) {
     int f;
     const FieldRun *r = pick(lv, one, blockIdx.z, f);
     if (!r || l > r->L) return;
@@ -90,27 +57,53 @@ __global__ void __launch_bounds__(NT) fwd_level(Live lv, const __grid_constant__
     const long long ncoef = r->N;
     const int hl = (hp + 1) >> 1, wl = (wp + 1) >> 1, ls = wl;
     const double mn = r->mn, inv = r->inv_range;
+    const int tid = threadIdx.x;
     __shared__ float t[EY][EX + 1];
-    for (int k = threadIdx.x; k < EY * EX; k += NT) {
-        int ly = k / EX, lx = k % EX;
-        int gy = reflect(ty0 - HALO + ly, hp), gx = reflect(tx0 - HALO + lx, wp);
-        float v = INB((long long)gy * ss + gx, (long long)hp * ss) ? src[(size_t)gy * ss + gx] : 0.0f;
-        if (NORM) v = (float)(((double)v - mn) * inv);
-        t[ly][lx] = v;
+    if (tid < EX) {  // column tid: all loads in flight, the four lifting steps and the scaling in registers
+        const int gx = reflect(tx0 - HALO + tid, wp);
+        float w[EY];
+#pragma unroll
+        for (int ly = 0; ly < EY; ly++) {
+            const int gy = reflect(ty0 - HALO + ly, hp);
+            const long long i = (long long)gy * ss + gx;
+            float v = INBQ(i, (long long)hp * ss) ? src[i] : 0.0f;
+            if (NORM) v = (float)(((double)v - mn) * inv);
+            w[ly] = v;
+        }
+#pragma unroll
+        for (int i = 1; i <= EY - 2; i += 2) w[i] += ALPHA * (w[i - 1] + w[i + 1]);
+#pragma unroll
+        for (int i = 2; i <= EY - 2; i += 2) w[i] += BETA * (w[i - 1] + w[i + 1]);
+#pragma unroll
+        for (int i = 1; i <= EY - 2; i += 2) w[i] += GAMMA * (w[i - 1] + w[i + 1]);
+#pragma unroll
+        for (int i = 2; i <= EY - 2; i += 2) w[i] += DELTA * (w[i - 1] + w[i + 1]);
+#pragma unroll
+        for (int i = 0; i < EY; i++) w[i] *= (i & 1) ? KAPPA : INV_KAPPA;
+#pragma unroll
+        for (int i = HALO; i < HALO + TY; i++) t[i][tid] = w[i];
     }
     __syncthreads();
-    lift<true>(t, 1, ALPHA, 0, EX); __syncthreads();
-    lift<true>(t, 0, BETA, 0, EX); __syncthreads();
-    lift<true>(t, 1, GAMMA, 0, EX); __syncthreads();
-    lift<true>(t, 0, DELTA, 0, EX); __syncthreads();
-    scale<true>(t, INV_KAPPA, KAPPA, 0, EX); __syncthreads();
-    lift<false>(t, 1, ALPHA, HALO, HALO + TY); __syncthreads();
-    lift<false>(t, 0, BETA, HALO, HALO + TY); __syncthreads();
-    lift<false>(t, 1, GAMMA, HALO, HALO + TY); __syncthreads();
-    lift<false>(t, 0, DELTA, HALO, HALO + TY); __syncthreads();
-    scale<false>(t, INV_KAPPA, KAPPA, HALO, HALO + TY); __syncthreads();
+    if (tid < TY) {  // row HALO + tid
+        float v[EX];
+#pragma unroll
+        for (int i = 0; i < EX; i++) v[i] = t[HALO + tid][i];
+#pragma unroll
+        for (int i = 1; i <= EX - 2; i += 2) v[i] += ALPHA * (v[i - 1] + v[i + 1]);
+#pragma unroll
+        for (int i = 2; i <= EX - 2; i += 2) v[i] += BETA * (v[i - 1] + v[i + 1]);
+#pragma unroll
+        for (int i = 1; i <= EX - 2; i += 2) v[i] += GAMMA * (v[i - 1] + v[i + 1]);
+#pragma unroll
+        for (int i = 2; i <= EX - 2; i += 2) v[i] += DELTA * (v[i - 1] + v[i + 1]);
+#pragma unroll
+        for (int i = 0; i < EX; i++) v[i] *= (i & 1) ? KAPPA : INV_KAPPA;
+#pragma unroll
+        for (int i = 0; i < EX; i++) t[HALO + tid][i] = v[i];
+    }
+    __syncthreads();
     constexpr int QH = TY / 2, QW = TX / 2;
-    for (int k = threadIdx.x; k < TY * TX; k += NT) {
+    for (int k = tid; k < TY * TX; k += blockDim.x) {
         int sub = k / (QH * QW), rr = (k / QW) % QH, c = k % QW;
         int pv = sub >> 1, ph = sub & 1;
         int gy = ty0 + 2 * rr + pv, gx = tx0 + 2 * c + ph;
@@ -118,10 +111,10 @@ __global__ void __launch_bounds__(NT) fwd_level(Live lv, const __grid_constant__
         float v = t[HALO + 2 * rr + pv][HALO + 2 * c + ph];
         int oy = (gy >> 1) + (pv ? hl : 0), ox = (gx >> 1) + (ph ? wl : 0);
         if (!pv && !ph) {
-            if (ll && INB((long long)oy * ls + ox, (long long)hl * ls)) ll[(size_t)oy * ls + ox] = v;
-            if (last && INB((long long)oy * nx + ox, ncoef)) coef[(size_t)oy * nx + ox] = v;
+            if (ll && INBQ((long long)oy * ls + ox, (long long)hl * ls)) ll[(size_t)oy * ls + ox] = v;
+            if (last && INBQ((long long)oy * nx + ox, ncoef)) coef[(size_t)oy * nx + ox] = v;
         } else {
-            if (INB((long long)oy * nx + ox, ncoef)) coef[(size_t)oy * nx + ox] = v;
+            if (INBQ((long long)oy * nx + ox, ncoef)) coef[(size_t)oy * nx + ox] = v;
         }
     }
 }
@@ -379,9 +372,9 @@ int dwt_forward_b(const Live &lv, const FieldRun &one, int nslots, const BatchDi
         dim3 grid((wp + TX - 1) / TX, (hp + TY - 1) / TY, nslots);
         const double bytes = 8.0 * hp * wp * nslots;
         if (l == 1 && norm)
-            PROF("fwd_level", st, bytes, fwd_level<true><<<grid, NT, 0, st>>>(lv, one, l, src));
+            PROF("fwd_level", st, bytes, fwd_level<true><<<grid, 96, 0, st>>>(lv, one, l, src));
         else
-            PROF("fwd_level", st, bytes, fwd_level<false><<<grid, NT, 0, st>>>(lv, one, l, src));
+            PROF("fwd_level", st, bytes, fwd_level<false><<<grid, 96, 0, st>>>(lv, one, l, src));
         CK(cudaGetLastError());
     }
     return EBCC_OK;
