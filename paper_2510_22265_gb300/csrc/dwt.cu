@@ -1,15 +1,18 @@
 // CDF 9/7 irreversible lifting DWT on GB300 (T.800 Annex F; EBCC's base
 // layer and residual layer, Algorithm 1 DWT / IDWT).
 //
-// One kernel per level.  A CTA owns a 32 x 64 tile of the level's input,
-// stages it with a 4-sample halo in shared memory (symmetric extension is
+// One kernel per level, batched over fields (grid z = field slot).  A CTA owns
+// a 32 x 64 tile of the level and its 4-sample halo (symmetric extension is
 // applied while loading: whole-sample reflection keeps the sample parity, so
-// lifting the extended tile gives the finite transform exactly), runs the
-// four lifting steps and the scaling on columns then rows (inverse: rows then
-// columns), and writes the four subbands de-interleaved with coalesced rows.
-// The detail bands go straight to the Mallat array; the LL band goes to a
-// compact scratch buffer that the next level reads, so no level reads data a
-// concurrent tile overwrites.
+// lifting the extended tile gives the finite transform exactly).  One thread
+// per column and one per row run the four lifting steps and the scaling in
+// registers (forward: columns, then rows; inverse: rows, then columns), the
+// tile passing between the two through shared memory.  The forward writes
+// the four subbands de-interleaved with coalesced rows; the inverse finishes
+// its last level in place (store, add the base layer, denormalise, or count
+// the points inside their acceptance intervals).  Detail bands live in the
+// Mallat array; each level's LL band goes to a compact scratch buffer that the
+// next level reads, so no level reads data a concurrent tile overwrites.
 #include <string.h>
 #include "ebcc_internal.cuh"
 
