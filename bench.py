@@ -226,12 +226,16 @@ def run_gpu(args):
     shapes = [tuple(f.shape) for f in dfields]
     assert B.ebcc_decompress_batch_dev([r[0] for r in res], lens, shapes, douts) == 0
     torch.cuda.synchronize()
+    B.lib().ebcc_profile_reset()
+    B.lib().ebcc_profile_enable(1)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
         assert B.ebcc_decompress_batch_dev([r[0] for r in res], lens, shapes, douts) == 0
     e1.record(stream)
     torch.cuda.synchronize()
+    B.lib().ebcc_profile_enable(0)
+    prof_dec = B.profile_read()
     t_dec = e0.elapsed_time(e1) / args.steps
     max_err = max(float((d - f).abs().max()) / (BOUND * float(f.max() - f.min())) for d, f in zip(douts, dfields))
     # end to end: every step copies the stack from pinned host memory, runs the
@@ -295,7 +299,8 @@ def run_gpu(args):
                            "fields": min(n, args.e2e_fields),
                            "what": "ebcc_compress (host buffers, one field per call)"},
         "gpu_launches": int(sum(p["launches"] for p in prof)) // max(1, args.steps) if prof else None,
-        "roofline": roof, "serving": serving, "kernels": prof, "clocks": clk.summary(), "cpu_baseline": cpu,
+        "roofline": roof, "serving": serving, "kernels": prof, "kernels_decompress": prof_dec,
+        "clocks": clk.summary(), "cpu_baseline": cpu,
     }
     print(json.dumps(line))
     if dist:
