@@ -34,6 +34,11 @@ sys.path.insert(0, ROOT)
 from paper_2510_22265_gb300 import synth  # noqa: E402
 
 METRIC = "compress/decompress GB/s at 1% rel bound (batched vs plain); CR; p99 latency"
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) that ncu measured for the
+# dominant kernel on the default workload, averaged over the launches of one compression step
+# (profiles/launches_compress_era5_148x721x1440.md); reported only for that workload
+NCU_TRAFFIC = {"inv_level": 404.8e6}
+DEFAULT_SHAPE = [4, 37, 721, 1440]
 BOUND = 1e-2
 
 
@@ -278,8 +283,10 @@ def run_gpu(args):
     if prof:
         top = max(prof, key=lambda p: p["ms"])
         ach = top["bytes"] / (top["ms"] / 1e3) / 1e9 if top["ms"] > 0 else 0.0
+        traffic = NCU_TRAFFIC.get(top["name"]) if list(args.shape) == DEFAULT_SHAPE else None
         roof = {"bound": "hbm", "kernel": top["name"], "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                "frac": ach / peaks["hbm_gbs"], "traffic": traffic,
+                "algorithmic_bytes_per_launch": top["bytes"] / max(1, top["launches"]),
                 "share_of_step": top["ms"] / (t_ms * args.steps), "peak_source": "measured burst copy"}
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -334,7 +341,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--shape", type=int, nargs=4, default=[4, 37, 721, 1440],
+    ap.add_argument("--shape", type=int, nargs=4, default=DEFAULT_SHAPE,
                     help="variables levels ny nx")
     ap.add_argument("--e2e-fields", type=int, default=16)
     ap.add_argument("--plain-fields", type=int, default=8)
