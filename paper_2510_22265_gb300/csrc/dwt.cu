@@ -163,6 +163,9 @@ constexpr int IT = 96;  // threads of an inverse-level CTA (72 stage the tile's 
 // finished output per fin.  Thread c < EX stages column c of the extended
 // tile (its source column is fixed, rows step down), then each row and each
 // column is lifted in registers by one thread.
+// MODE: the finish this launch applies (fin.mode at level 1, -1 above), as a
+// template parameter so each instantiation carries only its own finish
+template <int MODE>
 __global__ void __launch_bounds__(IT, 10) inv_level(Live lv, const __grid_constant__ FieldRun one, int l, int src_plane,
                                                 InvFinal fin) {
     int f;
@@ -177,7 +180,7 @@ __global__ void __launch_bounds__(IT, 10) inv_level(Live lv, const __grid_consta
     const int ls = l < L ? ceil_sh(nx, l) : nx;
     float *__restrict__ dst = l == 1 ? plane_ptr(*r, fin.dst) : ((l & 1) ? r->s2 : r->s1);
     const int ds = l == 1 ? nx : wp;
-    const int mode = l == 1 ? fin.mode : -1;
+    constexpr int mode = MODE;
     const int ncoef = (int)r->N;
     const int hl = (hp + 1) >> 1, wl = (wp + 1) >> 1;
     const int tid = threadIdx.x;
@@ -400,7 +403,14 @@ int dwt_inverse_b(const Live &lv, const FieldRun &one, int nslots, const BatchDi
         else if (fin.mode == 1) per += 8.0;
         else if (fin.mode == 2) per += 12.0;
         else per += fin.add_base ? 8.0 : 4.0;
-        PROF("inv_level", st, per * hp * wp * nslots, inv_level<<<grid, IT, 0, st>>>(lv, one, l, src, fin));
+        const int mode = l == 1 ? fin.mode : -1;
+        switch (mode) {
+        case -1: PROF("inv_level", st, per * hp * wp * nslots, inv_level<-1><<<grid, IT, 0, st>>>(lv, one, l, src, fin)); break;
+        case 0: PROF("inv_level", st, per * hp * wp * nslots, inv_level<0><<<grid, IT, 0, st>>>(lv, one, l, src, fin)); break;
+        case 1: PROF("inv_level", st, per * hp * wp * nslots, inv_level<1><<<grid, IT, 0, st>>>(lv, one, l, src, fin)); break;
+        case 2: PROF("inv_level", st, per * hp * wp * nslots, inv_level<2><<<grid, IT, 0, st>>>(lv, one, l, src, fin)); break;
+        default: PROF("inv_level", st, per * hp * wp * nslots, inv_level<3><<<grid, IT, 0, st>>>(lv, one, l, src, fin)); break;
+        }
         CK(cudaGetLastError());
     }
     return EBCC_OK;
