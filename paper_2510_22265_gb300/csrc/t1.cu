@@ -793,18 +793,40 @@ __global__ void __launch_bounds__(WARPS * 32) t1_decode_kernel(const uint8_t *by
                 mag[r * w + j] = 1u << p;
                 pl[r * w + j] = (int8_t)p;
             };
+            // columns of stripe s with a coefficient that is not significant
+            // but has a significant neighbour (candidates of the significance
+            // propagation pass), among the columns >= j0
+            auto spp_cols = [&](int s, int r1, int j0) -> uint64_t {
+                uint64_t cm = 0;
+                for (int r = s; r < r1; r++) {
+                    const uint64_t up = r > 0 ? S.sig[r - 1] : 0, dn = r + 1 < h ? S.sig[r + 1] : 0;
+                    const uint64_t nb = up | (up << 1) | (up >> 1) | (S.sig[r] << 1) | (S.sig[r] >> 1) | dn |
+                                        (dn << 1) | (dn >> 1);
+                    cm |= ~S.sig[r] & nb;
+                }
+                return cm & full & (j0 >= 64 ? 0ull : (~0ull << j0));
+            };
             for (int p = K - 1; p >= 0 && pass < np; p--) {
                 if (p < K - 1) {
                     for (int s = 0; s < h; s += 4) {
                         const int r1 = min(s + 4, h);
-                        for (int j = 0; j < w; j++)
+                        uint64_t cm = spp_cols(s, r1, 0);
+                        while (cm) {
+                            const int j = __ffsll((long long)cm) - 1;
+                            bool grew = false;
                             for (int r = s; r < r1; r++) {
                                 if ((S.sig[r] >> j) & 1) continue;
                                 uint32_t nb = S.nbr(r, j);
                                 if (!nb) continue;
                                 S.vis[r] |= 1ull << j;
-                                if (dc.decode(I, M, c_sigctx[orient][nb])) dec_sign(r, j, p);
+                                if (dc.decode(I, M, c_sigctx[orient][nb])) {
+                                    dec_sign(r, j, p);
+                                    grew = true;
+                                }
                             }
+                            // a new significance can make the next column a candidate
+                            cm = grew ? spp_cols(s, r1, j + 1) : (cm & (cm - 1));
+                        }
                     }
                     if (++pass >= np) break;
                     for (int s = 0; s < h; s += 4) {
