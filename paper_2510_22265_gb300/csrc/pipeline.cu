@@ -127,32 +127,65 @@ __device__ void compact(int *live, F &&step) {
     if (tid == 0) live[0] = out;
 }
 
-__global__ void bl_start(BaseLoop *bl, const FieldRun *tab, const int *list, int n, double q, int fallback, double r0,
-                         double tol, Hulls h, int *live) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const int f = list[k];
+// Evaluations of a field's base layer at the budgets tried so far (both
+// loops): an evaluation depends only on the budget, so a budget met again
+// (the q = 1 loop retraces the q loop's bracketing from r0) is answered from
+// here instead of being evaluated again -- the loop's decisions are unchanged.
+constexpr int EVC = 96;
+struct EvalCache {
+    int n, pad;
+    double budget[EVC];
+    unsigned long long count[EVC];
+};
+
+// set up the evaluation at s.budget, resolving budgets already evaluated
+__device__ void bl_advance(BaseLoop &s, const FieldRun &r, const Hulls &h, const EvalCache &c) {
+    while (!s.done) {
+        int k = -1;
+        for (int j = 0; j < c.n && j < EVC; j++)
+            if (c.budget[j] == s.budget) { k = j; break; }
+        if (k < 0) {
+            s.sel_eval = select_field(h, r, s.budget);  // next evaluation
+            return;
+        }
+        s.sel_eval = select_field(h, r, s.budget);
+        bl_step(s, (double)c.count[k] / s.N);
+    }
+}
+
+__global__ void __launch_bounds__(1024) bl_start(BaseLoop *bl, EvalCache *evc, const FieldRun *tab, double q,
+                                                 int fallback, double r0, double tol, Hulls h, int *live) {
+    compact(live, [&](int f) {
         const FieldRun &r = tab[f];
+        EvalCache &c = evc[f];
+        if (!fallback) c.n = 0;  // a new field: nothing evaluated yet
         BaseLoop s;
         memset(&s, 0, sizeof(s));
         s.q = q; s.r0 = r0; s.tol = tol; s.N = (double)r.N; s.rmax = 4.0 * (double)r.N;
         s.fallback = fallback; s.phase = 0; s.budget = 4.0 * (double)r.N / r0;
-        s.sel_eval = select_field(h, r, s.budget);
+        bl_advance(s, r, h, c);
         bl[f] = s;
         r.sc->cnt[0] = 0;
-        live[1 + k] = f;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) live[0] = n;
+        return !s.done;
+    });
 }
 
-__global__ void __launch_bounds__(1024) bl_update(BaseLoop *bl, const FieldRun *tab, Hulls h, int *live) {
+__global__ void __launch_bounds__(1024) bl_update(BaseLoop *bl, EvalCache *evc, const FieldRun *tab, Hulls h,
+                                                  int *live) {
     compact(live, [&](int f) {
         BaseLoop s = bl[f];
         const FieldRun &r = tab[f];
+        EvalCache &c = evc[f];
         if (!s.done) {
-            const double qA = (double)r.sc->cnt[0] / s.N;
+            const unsigned long long cnt = r.sc->cnt[0];
             r.sc->cnt[0] = 0;
-            bl_step(s, qA);
-            if (!s.done) s.sel_eval = select_field(h, r, s.budget);  // next evaluation
+            if (c.n < EVC) {
+                c.budget[c.n] = s.budget;
+                c.count[c.n] = cnt;
+                c.n++;
+            }
+            bl_step(s, (double)cnt / s.N);
+            bl_advance(s, r, h, c);
             bl[f] = s;
         }
         return !s.done;
@@ -562,6 +595,7 @@ struct Batch {
     uint32_t *meta_off = nullptr, *pay_off = nullptr;
     int64_t *addr = nullptr;        // decoder: payload address per block
     BaseLoop *bl = nullptr;
+    EvalCache *evc = nullptr;
     TruncLoop *tl = nullptr;
     int *live = nullptr;            // F + 1
     int *list = nullptr;            // F
@@ -648,6 +682,7 @@ void layout_compress(Arena &a, Batch &b, const std::vector<int> &ny, const std::
     b.d_geom = carve<FieldGeom>(a, F);
     b.d_sc = carve<FieldScal>(a, F);
     b.bl = carve<BaseLoop>(a, F);
+    b.evc = carve<EvalCache>(a, F);
     b.tl = carve<TruncLoop>(a, F);
     b.live = carve<int>(a, F + 1);
     b.list = carve<int>(a, F + 1);
@@ -803,20 +838,23 @@ int run_base_loop(Engine &e, Batch &b, const std::vector<int> &A, double q, int 
                   cudaStream_t st) {
     const int n = (int)A.size();
     if (!n) return EBCC_OK;
-    RC(upload(e, b.list, A.data(), n * sizeof(int), st));
-    PROF("bl_start", st, 0.0, bl_start<<<(n + 255) / 256, 256, 0, st>>>(b.bl, b.d_run, b.list, n, q, fallback, p.r0, p.tol, b.hull, b.live));
+    RC(set_list(e, b, A, st));
+    PROF("bl_start", st, 0.0, bl_start<<<1, 1024, 0, st>>>(b.bl, b.evc, b.d_run, q, fallback, p.r0, p.tol, b.hull, b.live));
     CK(cudaGetLastError());
     int *slot = stage_take<int>(e, 2);
     if (!slot) return EBCC_ECAPACITY;
+    int *h0 = nullptr;
+    RC(download(e, b.live, 1, &h0, st));  // fields whose loop is already settled by earlier evaluations drop out
     const Live lv = live_of(b);
     const InvFinal fin{1, 0, 0, 0};
     const Sel *sel = &b.bl[0].sel_eval;
-    int hn = n, rc = EBCC_OK;
+    int hn = *h0, rc = EBCC_OK;
+    if (hn <= 0) return cudaStreamSynchronize(st) == cudaSuccess ? EBCC_OK : EBCC_ECUDA;
     for (int step = 0; step < 400; step++) {
         rc = pcrd_npass_b(lv, kNone, hn, b.dims.maxnblk, b.hull, sel, sizeof(BaseLoop), b.npass, st);
         if (!rc) rc = base_eval(b, lv, hn, fin, st);
         if (rc) break;
-        PROF("bl_update", st, 0.0, bl_update<<<1, 1024, 0, st>>>(b.bl, b.d_run, b.hull, b.live));
+        PROF("bl_update", st, 0.0, bl_update<<<1, 1024, 0, st>>>(b.bl, b.evc, b.d_run, b.hull, b.live));
         if (ebcc_debug_sync_enabled() && ebcc_stage_check(st, "base eval", __LINE__)) { rc = EBCC_ECUDA; break; }
         if (cudaMemcpyAsync(&slot[step & 1], b.live, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaEventRecord(e.ev[step & 1], st) != cudaSuccess) { rc = EBCC_ECUDA; break; }
