@@ -64,7 +64,9 @@ typedef struct {
     int used_fallback;           /* 1 = base layer alone was shorter */
     int guard_bits, n_escape;    /* SPIHT guard bits used; escaped points */
     long long base_bytes, res_bytes, total_bytes, spiht_len_bytes;
-    long long len_two, len_one;  /* two-layer and base-only stream lengths (0 = none) */
+    long long len_two, len_one;  /* two-layer and base-only stream lengths (0 = none; len_two is also 0
+                                    when the base-only stream was proven shorter before the two-layer
+                                    stream was finished) */
     double q_base;               /* q_A of the kept base encoding */
 } ebcc_stats;
 
@@ -114,9 +116,12 @@ typedef struct {
 } ebcc_out_desc;
 
 /* Compress n device fields of any sizes together: every step of Algorithm 1 is
- * one launch over all fields that are still iterating (persistent grid-stride
- * kernels), the steps replayed from a captured CUDA graph.  Synchronises
- * `stream` before returning (it reads the per-field outcomes).  The return
+ * one launch over all fields that take part in it, and the two feedback loops
+ * are per-field state machines on the device that drop fields from the
+ * launches as they finish (a batch of one field is the plain path).  Fields
+ * whose workspace would exceed half the free device memory are split into
+ * several batches.  Synchronises `stream` before returning (it reads the
+ * per-field outcomes).  The return
  * value is EBCC_OK if every field succeeded, else the first failing status;
  * per-field status is in outs[i].status.  Stream capacity needed per field:
  * ebcc_max_stream_bytes(ny, nx). */

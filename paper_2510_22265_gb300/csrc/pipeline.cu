@@ -194,7 +194,8 @@ __global__ void __launch_bounds__(1024) bl_update(BaseLoop *bl, EvalCache *evc, 
 
 struct TruncLoop {
     long long lo, hi, mid, nbits, T;
-    int iters, done;
+    long long stop;  // the search ends "lost" once lo >= stop (two-layer proven longer than base-only)
+    int iters, done, lost, pad;
 };
 
 __device__ void tl_next(TruncLoop &t) {
@@ -208,13 +209,16 @@ __device__ void tl_next(TruncLoop &t) {
 
 // binary search for the best feasible truncation point (Algorithm 1), over
 // the stream's bytes
-__global__ void __launch_bounds__(1024) tl_start(TruncLoop *tl, const FieldRun *tab, int *live) {
+__global__ void __launch_bounds__(1024) tl_start(TruncLoop *tl, const FieldRun *tab, const long long *stop,
+                                                 int *live) {
     compact(live, [&](int f) {
         const FieldRun &r = tab[f];
         TruncLoop t;
         t.nbits = r.sc->nbits;
         t.lo = 0; t.hi = (t.nbits + 7) / 8; t.iters = 0; t.done = 0; t.mid = 0; t.T = 0;
-        tl_next(t);
+        t.stop = stop[f]; t.lost = 0; t.pad = 0;
+        if (t.hi > 0 && t.lo >= t.stop) { t.done = 1; t.lost = 1; }
+        else tl_next(t);
         tl[f] = t;
         r.sc->T = t.T;
         r.sc->cnt[1] = 0;
@@ -230,7 +234,8 @@ __global__ void __launch_bounds__(1024) tl_update(TruncLoop *tl, const FieldRun 
             t.iters++;
             if (r.sc->cnt[1] > 0) t.lo = t.mid; else t.hi = t.mid;
             r.sc->cnt[1] = 0;
-            tl_next(t);
+            if (t.lo >= t.stop) { t.done = 1; t.lost = 1; }
+            else tl_next(t);
             r.sc->T = t.T;
             tl[f] = t;
         }
@@ -597,6 +602,7 @@ struct Batch {
     BaseLoop *bl = nullptr;
     EvalCache *evc = nullptr;
     TruncLoop *tl = nullptr;
+    long long *stop = nullptr;      // F: truncation search limits
     int *live = nullptr;            // F + 1
     int *list = nullptr;            // F
     int *es = nullptr;              // F
@@ -684,6 +690,7 @@ void layout_compress(Arena &a, Batch &b, const std::vector<int> &ny, const std::
     b.bl = carve<BaseLoop>(a, F);
     b.evc = carve<EvalCache>(a, F);
     b.tl = carve<TruncLoop>(a, F);
+    b.stop = carve<long long>(a, F + 1);
     b.live = carve<int>(a, F + 1);
     b.list = carve<int>(a, F + 1);
     b.es = carve<int>(a, F + 1);
@@ -873,7 +880,7 @@ int run_trunc_loop(Engine &e, Batch &b, const std::vector<int> &A, cudaStream_t 
     const int n = (int)A.size();
     if (!n) return EBCC_OK;
     RC(set_list(e, b, A, st));
-    PROF("tl_start", st, 0.0, tl_start<<<1, 1024, 0, st>>>(b.tl, b.d_run, b.live));
+    PROF("tl_start", st, 0.0, tl_start<<<1, 1024, 0, st>>>(b.tl, b.d_run, b.stop, b.live));
     CK(cudaGetLastError());
     int *slot = stage_take<int>(e, 2);
     if (!slot) return EBCC_ECAPACITY;
@@ -1051,20 +1058,58 @@ int compress_batch(Engine &e, const ebcc_field_desc *fd, int n, ebcc_out_desc *o
             if (!hb1[f].done) { status[f] = EBCC_ETIMEOUT; drop[f] = 1; }
         remove_from(A, drop);
     }
+    // The base-only (q = 1) candidate is computed before the residual layer:
+    // its length shows which two-layer candidates cannot be the shorter one
+    // (their base section alone, or base plus the truncation's proven lower
+    // bound, is already longer), and their residual work stops there.  The
+    // stream chosen is the same as when every candidate is computed in full.
+    const long long NOLEN = 0x3FFFFFFFFFFFFFFFLL;
+    std::vector<long long> L1(F, NOLEN);  // base-only stream length (NOLEN: no base-only stream meets the bound)
+    std::vector<char> lost(F, 0);         // the two-layer stream is certainly longer than the base-only one
+    std::vector<int> Rl;                  // fields that need the residual layer
     if (!A.empty()) {
         const int na = (int)A.size();
         RC(set_list(e, b, A, st));
         Live lv = live_of(b);
-        // ---- A_base = dec_base(e_f), the residue in FP64, its DWT
+        for (int f : A) sel_two[f] = hb1[f].sel_f;
+        // ---- A_base = dec_base(e_f) into its own plane, and the size of that base section
         RC(pcrd_npass_b(lv, kNone, na, b.dims.maxnblk, b.hull, &b.bl[0].sel_f, sizeof(BaseLoop), b.npass, st));
         RC(base_eval(b, lv, na, InvFinal{0, 0, PL_ABASE, 0}, st));
-        RC(residue_b(lv, kNone, na, b.dims.maxN, st));
-        RC(dwt_forward_b(lv, kNone, na, b.dims, PL_R, 0, st));
+        STAGE(st, "A_base");
+        RC(base_sizes_for(e, b, A, &b.bl[0].sel_f, sizeof(BaseLoop), st));
+        RC(download(e, b.d_sc, F, &hs, st));
+        for (int f : A) bl2[f] = (long long)(hs[f].tot[0] + hs[f].tot[1]);
+        // ---- the fallback (q = 1) base loop
+        RC(run_base_loop(e, b, A, 1.0, 1, p, st));
+        BaseLoop *hb = nullptr;
+        RC(download(e, b.bl, F, &hb, st));
+        std::vector<int> O;
+        for (int f : A) {
+            hb2[f] = hb[f];
+            if (hb2[f].done && hb2[f].q_f >= 1.0) O.push_back(f);
+        }
+        RC(base_sizes_for(e, b, O, &b.bl[0].sel_f, sizeof(BaseLoop), st));
+        if (!O.empty()) RC(download(e, b.d_sc, F, &hs, st));
+        for (int f : O) {
+            bl1[f] = (long long)(hs[f].tot[0] + hs[f].tot[1]);
+            L1[f] = HDR_BYTES + bl1[f];
+        }
+        for (int f : A) {
+            if (HDR_BYTES + bl2[f] > L1[f]) lost[f] = 1;
+            else Rl.push_back(f);
+        }
+    }
+    if (!Rl.empty()) {
+        const int nr = (int)Rl.size();
+        RC(set_list(e, b, Rl, st));
+        Live lv = live_of(b);
+        // ---- the residue in FP64, its DWT
+        RC(residue_b(lv, kNone, nr, b.dims.maxN, st));
+        RC(dwt_forward_b(lv, kNone, nr, b.dims, PL_R, 0, st));
         RC(w_invalidate(b, st));  // W now holds the residual's transform
         STAGE(st, "residue dwt");
-        for (int f : A) sel_two[f] = hb1[f].sel_f;
         // ---- SPIHT with guard retries: step 2^(floor(log2 eps_n) - G)
-        std::vector<int> S = A;
+        std::vector<int> S = Rl;
         for (int attempt = 0; attempt < 3 && !S.empty(); attempt++) {
             for (int f : S) esv[f] = (int)floor(log2(eps_n[f])) - G[f];
             RC(upload(e, b.es, esv.data(), F * sizeof(int), st));
@@ -1089,10 +1134,11 @@ int compress_batch(Engine &e, const ebcc_field_desc *fd, int n, ebcc_out_desc *o
             S.swap(again);
         }
         remove_from(A, drop);
+        remove_from(Rl, drop);
     }
     std::vector<int> X;  // fields with escapes
-    if (!A.empty()) {
-        for (int f : A)
+    if (!Rl.empty()) {
+        for (int f : Rl)
             if (bad[f] > 0) X.push_back(f);
         if (!X.empty()) {  // last resort: exact values of the points still outside the bound
             RC(set_list(e, b, X, st));
@@ -1107,44 +1153,29 @@ int compress_batch(Engine &e, const ebcc_field_desc *fd, int n, ebcc_out_desc *o
                 if (nesc[f] > (unsigned long long)b.run[f].esc_cap) { status[f] = EBCC_ECAPACITY; drop[f] = 1; }
             }
             remove_from(A, drop);
-            remove_from(X, drop);
+            remove_from(Rl, drop);
+        }
+    }
+    if (!Rl.empty()) {
+        // ---- binary search for the truncation point; a field stops once its
+        // two-layer stream is proven longer than its base-only stream
+        std::vector<long long> stop(F, NOLEN);
+        for (int f : Rl)
+            if (L1[f] != NOLEN) stop[f] = L1[f] - HDR_BYTES - bl2[f] - 8 * (long long)nesc[f];
+        RC(upload(e, b.stop, stop.data(), F * sizeof(long long), st));
+        RC(run_trunc_loop(e, b, Rl, st));
+        TruncLoop *ht = nullptr;
+        RC(download(e, b.tl, F, &ht, st));
+        for (int f : Rl) {
+            htl[f] = ht[f];
+            if (ht[f].lost) lost[f] = 1;
+            else len2[f] = HDR_BYTES + bl2[f] + htl[f].hi + 8 * (long long)nesc[f];
         }
     }
     if (!A.empty()) {
-        // ---- binary search for the truncation point
-        RC(run_trunc_loop(e, b, A, st));
-        TruncLoop *ht = nullptr;
-        RC(download(e, b.tl, F, &ht, st));
-        for (int f : A) htl[f] = ht[f];
-        // ---- sizes of the two-layer candidates
-        RC(base_sizes_for(e, b, A, &b.bl[0].sel_f, sizeof(BaseLoop), st));
-        RC(download(e, b.d_sc, F, &hs, st));
         for (int f : A) {
-            bl2[f] = (long long)(hs[f].tot[0] + hs[f].tot[1]);
-            len2[f] = HDR_BYTES + bl2[f] + htl[f].hi + 8 * (long long)nesc[f];
-        }
-        // escaped points had their acceptance interval opened up for the
-        // truncation search; the base-only candidate is judged on the true bound
-        if (!X.empty()) {
-            RC(set_list(e, b, X, st));
-            RC(make_bounds_b(live_of(b), kNone, (int)X.size(), b.dims.maxN, st));
-        }
-        // ---- the fallback (q = 1) base loop
-        RC(run_base_loop(e, b, A, 1.0, 1, p, st));
-        BaseLoop *hb = nullptr;
-        RC(download(e, b.bl, F, &hb, st));
-        std::vector<int> O;
-        for (int f : A) {
-            hb2[f] = hb[f];
-            if (hb2[f].done && hb2[f].q_f >= 1.0) O.push_back(f);
-        }
-        RC(base_sizes_for(e, b, O, &b.bl[0].sel_f, sizeof(BaseLoop), st));
-        if (!O.empty()) RC(download(e, b.d_sc, F, &hs, st));
-        for (int f : O) {
-            bl1[f] = (long long)(hs[f].tot[0] + hs[f].tot[1]);
-            use_one[f] = HDR_BYTES + bl1[f] < len2[f];
-        }
-        for (int f : A) {
+            use_one[f] = lost[f] || (L1[f] != NOLEN && L1[f] < len2[f]);
+            if (!use_one[f] && !len2[f]) { status[f] = EBCC_ETIMEOUT; drop[f] = 1; continue; }
             sel_fin[f] = use_one[f] ? hb2[f].sel_f : sel_two[f];
             const long long total = use_one[f] ? HDR_BYTES + bl1[f] : len2[f];
             if (total > b.run[f].out_cap) { status[f] = EBCC_ECAPACITY; drop[f] = 1; }
