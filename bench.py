@@ -157,6 +157,42 @@ def serving_leg(B, fields, rate, window, budget_gb, max_batch):
                     "latency = submit to result inside the library"}
 
 
+# ------------------------------------------------------------------ uneven batch
+def uneven_leg(B, torch, n, steps, warmup, plain_fields):
+    """Fields of uneven grids (91x180 .. 1441x2880) with log-uniform bounds in
+    [0.1%, 10%], all in one batch call; against one field per call on a subset."""
+    spec = synth.batch_spec(n, seed=3)
+    fields = [torch.from_numpy(synth.batch_field(g, sd)).cuda() for g, _, sd in spec]
+    bounds = [b for _, b, _ in spec]
+    caps = [B.ebcc_max_stream_bytes(*f.shape) for f in fields]
+    outs = [torch.empty(c, dtype=torch.uint8, device="cuda") for c in caps]
+    stream = torch.cuda.current_stream()
+    raw = sum(f.numel() * 4 for f in fields)
+    for _ in range(warmup):
+        rc, res = B.ebcc_compress_batch_dev(fields, bounds, outs=outs, stream=stream.cuda_stream)
+        assert rc == 0, rc
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        rc, res = B.ebcc_compress_batch_dev(fields, bounds, outs=outs, stream=stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / steps / 1e3
+    k = min(n, plain_fields)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for i in range(k):
+        rc, _ = B.ebcc_compress_batch_dev([fields[i]], [bounds[i]], outs=[outs[i]], stream=stream.cuda_stream)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    praw = sum(f.numel() * 4 for f in fields[:k])
+    return {"fields": n, "raw_bytes": raw, "compress_gbs": raw / t / 1e9, "ms_per_step": t * 1e3,
+            "plain_compress_gbs": praw / (p0.elapsed_time(p1) / 1e3) / 1e9, "plain_fields": k,
+            "cr": raw / sum(r[1] for r in res),
+            "what": "grids drawn from 91x180..1441x2880, bounds log-uniform in [0.1%, 10%], one batch call"}
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
@@ -269,6 +305,7 @@ def run_gpu(args):
         B.ebcc_compress(f.numpy(), BOUND, B.EBCC_BOUND_REL)
         plain_in += f.numel() * 4
     t_host_plain = time.perf_counter() - t
+    uneven = uneven_leg(B, torch, args.uneven, args.steps, args.warmup, args.plain_fields) if args.uneven else None
     serving = None
     if not args.no_serve:
         serving = serving_leg(B, fields, args.serve_rate, args.serve_window, 40.0, 64)
@@ -306,7 +343,8 @@ def run_gpu(args):
                            "fields": min(n, args.e2e_fields),
                            "what": "ebcc_compress (host buffers, one field per call)"},
         "gpu_launches": int(sum(p["launches"] for p in prof)) // max(1, args.steps) if prof else None,
-        "roofline": roof, "serving": serving, "kernels": prof, "kernels_decompress": prof_dec,
+        "roofline": roof, "serving": serving, "uneven_batch": uneven, "kernels": prof,
+        "kernels_decompress": prof_dec,
         "clocks": clk.summary(), "cpu_baseline": cpu,
     }
     print(json.dumps(line))
@@ -348,6 +386,7 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="serving leg: mean requests per second")
     ap.add_argument("--serve-window", type=float, default=0.5, help="serving leg: seconds of arrivals")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--uneven", type=int, default=0, help="also time a batch of this many uneven-grid fields")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
