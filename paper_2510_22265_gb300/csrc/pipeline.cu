@@ -127,28 +127,30 @@ __device__ void compact(int *live, F &&step) {
     if (tid == 0) live[0] = out;
 }
 
-// Evaluations of a field's base layer at the budgets tried so far (both
-// loops): an evaluation depends only on the budget, so a budget met again
-// (the q = 1 loop retraces the q loop's bracketing from r0) is answered from
-// here instead of being evaluated again -- the loop's decisions are unchanged.
+// Evaluations of a field's base layer so far (both loops), keyed by the PCRD
+// selection they evaluated: an evaluation depends only on the selection, and
+// many budgets select the same segments (the bisection's late steps move the
+// budget less than one segment's bytes; the q = 1 loop retraces the q loop's
+// bracketing from r0), so a selection met again is answered from here instead
+// of being evaluated again -- the loops' decisions are unchanged.
 constexpr int EVC = 96;
 struct EvalCache {
     int n, pad;
-    double budget[EVC];
+    Sel sel[EVC];
     unsigned long long count[EVC];
 };
 
-// set up the evaluation at s.budget, resolving budgets already evaluated
+// set up the evaluation at s.budget, resolving selections already evaluated
 __device__ void bl_advance(BaseLoop &s, const FieldRun &r, const Hulls &h, const EvalCache &c) {
     while (!s.done) {
+        s.sel_eval = select_field(h, r, s.budget);
         int k = -1;
         for (int j = 0; j < c.n && j < EVC; j++)
-            if (c.budget[j] == s.budget) { k = j; break; }
-        if (k < 0) {
-            s.sel_eval = select_field(h, r, s.budget);  // next evaluation
-            return;
-        }
-        s.sel_eval = select_field(h, r, s.budget);
+            if (c.sel[j].mode == s.sel_eval.mode && (s.sel_eval.mode == 0 || c.sel[j].thr == s.sel_eval.thr)) {
+                k = j;
+                break;
+            }
+        if (k < 0) return;  // a new selection: evaluate it
         bl_step(s, (double)c.count[k] / s.N);
     }
 }
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(1024) bl_update(BaseLoop *bl, EvalCache *evc, 
             const unsigned long long cnt = r.sc->cnt[0];
             r.sc->cnt[0] = 0;
             if (c.n < EVC) {
-                c.budget[c.n] = s.budget;
+                c.sel[c.n] = s.sel_eval;
                 c.count[c.n] = cnt;
                 c.n++;
             }
