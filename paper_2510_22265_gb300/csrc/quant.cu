@@ -200,6 +200,95 @@ __device__ int32_t edge(int32_t in, int32_t guess, int dir, double x, double mn,
     return good;
 }
 
+// ---- certified single-precision edges
+// The interval of normalised values passing the bound test is fixed by two
+// thresholds: on the output side the floats Tl <= x <= Th the test accepts,
+// on the input side the positions (C - mn) / range of the rounding midpoints
+// C = Th + ulp/2 and Tl - ulp/2 of the float32 output. Both are located here
+// in float-float arithmetic (error-free sums and products on float32 pairs),
+// together with a bound on how far that arithmetic and the FP64 roundings of
+// the test itself can move them. An edge whose threshold lies further than
+// that bound from both neighbouring floats is exactly the edge the FP64 test
+// gives; any other point (a few in 10^5 on smooth fields) takes the FP64
+// search. Error budget, in units of the quantity compared:
+//   output side: E split into two floats 2^-48 E, FP64 rounding of |x - T|
+//     2^-52 E, float rounding of the distances 2^-23 relative; margin 2^-44 E;
+//   input side: FP64 rounding of mn + a*range 2^-52 (|a| + |C| / range), the
+//     float-float position 2^-44 |t| (+ 2^-46 |mn| / range when mn is not a
+//     float), underflow below 2^-110; margin 2^-42 |t| + 2^-50 |T| / range
+//     (+ 2^-44 |mn| / range) + 2^-100.
+// Covered range (else every point of the field takes the FP64 search):
+// 2^-40 <= range <= 2^40, 2^-60 <= E <= 2^40, |mn| <= 2^40 and mn = 0 or
+// |mn| >= 2^-60; per point |x| <= 2^40.
+
+struct BoundsK {
+    float mn_h, mn_l, i_h, i_l, E_h, E_l;
+    float M;   // output-side margin
+    float dT;  // input-side margin per unit |T|
+    float d0;  // input-side constant margin
+    int ok;    // the field's constants lie in the covered range
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ float next_f(float a) { return o2f(f2o(a) + 1); }
+__device__ __forceinline__ float prev_f(float a) { return o2f(f2o(a) - 1); }
+
+// t1 + t2 ~ (T + h - mn) / range, h = +-ulp/2 (exact)
+__device__ __forceinline__ void a_position(float T, float h, const BoundsK &k, float &t1, float &t2) {
+    float p, q, p2, q2, ch, cl;
+    two_sum(T, -k.mn_h, p, q);
+    two_sum(p, h, p2, q2);
+    two_sum(p2, __fsub_rn(__fadd_rn(q, q2), k.mn_l), ch, cl);
+    const float m = __fmul_rn(ch, k.i_h);
+    const float em = __fmaf_rn(ch, k.i_h, -m);
+    const float tl = __fadd_rn(em, __fmaf_rn(ch, k.i_l, __fmul_rn(cl, k.i_h)));
+    t1 = __fadd_rn(m, tl);
+    t2 = __fsub_rn(tl, __fsub_rn(t1, m));
+}
+
+__device__ __forceinline__ bool bounds_fast(float x, const BoundsK &k, float2 &out) {
+    if (!(fabsf(x) <= 0x1p40f)) return false;
+    float s0, e0, w, v, su, eu;
+    // x + E = su + (eu + v): Th = largest float <= x + E
+    two_sum(x, k.E_h, s0, e0);
+    two_sum(e0, k.E_l, w, v);
+    two_sum(s0, w, su, eu);
+    const float du = __fadd_rn(eu, v);
+    const float Th = du < 0.f ? prev_f(su) : su;
+    const float h_lo = du < 0.f ? __fadd_rn(__fsub_rn(su, Th), du) : du;             // x + E - Th
+    const float h_hi = du < 0.f ? -du : __fsub_rn(__fsub_rn(next_f(su), su), du);    // next(Th) - (x + E)
+    // x - E = sd + dd: Tl = smallest float >= x - E
+    float sd, ed;
+    two_sum(x, -k.E_h, s0, e0);
+    two_sum(e0, -k.E_l, w, v);
+    two_sum(s0, w, sd, ed);
+    const float dd = __fadd_rn(ed, v);
+    const float Tl = dd > 0.f ? next_f(sd) : sd;
+    const float l_hi = dd > 0.f ? __fsub_rn(__fsub_rn(Tl, sd), dd) : -dd;            // Tl - (x - E)
+    const float l_lo = dd > 0.f ? dd : __fadd_rn(__fsub_rn(sd, prev_f(sd)), dd);     // (x - E) - prev(Tl)
+    if (!(fminf(fminf(h_lo, h_hi), fminf(l_hi, l_lo)) >= k.M)) return false;
+    // largest a with mn + a * range below Th + ulp/2
+    float t1, t2;
+    a_position(Th, __fmul_rn(__fsub_rn(next_f(Th), Th), 0.5f), k, t1, t2);
+    const float ahi = t2 < 0.f ? prev_f(t1) : t1;
+    const float mh = __fmaf_rn(fabsf(t1), 0x1p-42f, __fmaf_rn(fabsf(Th), k.dT, k.d0));
+    const float hb = __fadd_rn(__fsub_rn(t1, ahi), t2);                // t - ahi
+    const float ha = __fsub_rn(__fsub_rn(next_f(ahi), t1), t2);        // next(ahi) - t
+    // smallest a with mn + a * range above Tl - ulp/2
+    a_position(Tl, -__fmul_rn(__fsub_rn(Tl, prev_f(Tl)), 0.5f), k, t1, t2);
+    const float alo = t2 > 0.f ? next_f(t1) : t1;
+    const float ml = __fmaf_rn(fabsf(t1), 0x1p-42f, __fmaf_rn(fabsf(Tl), k.dT, k.d0));
+    const float la = __fsub_rn(__fsub_rn(alo, t1), t2);                // alo - t
+    const float lb = __fadd_rn(__fsub_rn(t1, prev_f(alo)), t2);        // t - prev(alo)
+    if (!(fminf(hb, ha) >= mh && fminf(la, lb) >= ml)) return false;
+    out = f2o(alo) <= f2o(ahi) ? make_float2(alo, ahi) : make_float2(1.0f, 0.0f);
+    return true;
+}
+
 __global__ void __launch_bounds__(NT) bounds_kernel(Live lv, const __grid_constant__ FieldRun one) {
     int f;
     const FieldRun *r = pick(lv, one, blockIdx.y, f);
@@ -209,8 +298,32 @@ __global__ void __launch_bounds__(NT) bounds_kernel(Live lv, const __grid_consta
     const double mn = r->mn, range = r->range, E = r->E;
     const double inv = 1.0 / range;
     const long long n = r->N;
+    __shared__ BoundsK sk;
+    if (threadIdx.x == 0) {
+        BoundsK k;
+        k.ok = isfinite(mn) && range >= 0x1p-40 && range <= 0x1p40 && E >= 0x1p-60 && E <= 0x1p40 &&
+               fabs(mn) <= 0x1p40 && (mn == 0.0 || fabs(mn) >= 0x1p-60);
+        k.mn_h = __double2float_rn(mn);
+        k.mn_l = __double2float_rn(mn - (double)k.mn_h);
+        k.i_h = __double2float_rn(inv);
+        k.i_l = __double2float_rn(inv - (double)k.i_h);
+        k.E_h = __double2float_rn(E);
+        k.E_l = __double2float_rn(E - (double)k.E_h);
+        k.M = k.E_h * 0x1p-44f;
+        k.dT = k.i_h * 0x1p-50f;
+        k.d0 = (k.mn_l != 0.0f ? fabsf(k.mn_h) * k.i_h * 0x1p-44f : 0.0f) + 0x1p-100f;
+        sk = k;
+    }
+    __syncthreads();
+    const BoundsK k = sk;
     for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
-        const double x = xs[i];
+        const float xf = xs[i];
+        float2 fb;
+        if (k.ok && bounds_fast(xf, k, fb)) {
+            bounds[i] = fb;
+            continue;
+        }
+        const double x = xf;
         // guesses that account for the float32 rounding of the output: the
         // output rounds to at most T = the float just below x + E exactly when
         // mn + a * range stays below the midpoint of T and the next float up

@@ -265,3 +265,93 @@ def test_count_within_matches_fp64_predicate(B):
     expect = int((np.abs(x.astype(np.float64) - xr.astype(np.float64)) <= eps - guard).sum())
     assert int(cnt.item()) == expect
     assert 0 < expect < x.size
+
+
+def _ord(a):
+    b = a.view(np.int32).astype(np.int64)
+    return np.where(b >= 0, b, b ^ 0x7FFFFFFF)
+
+
+def _flt(o):
+    o = np.asarray(o, np.int64)
+    return np.where(o >= 0, o, o ^ 0x7FFFFFFF).astype(np.int32).view(np.float32)
+
+
+def _passes(a, x, mn, rg, E):
+    # the bound test in FP64 on the float32 output, written out
+    xr = (mn + a.astype(np.float64) * rg).astype(np.float32)
+    return np.abs(x.astype(np.float64) - xr.astype(np.float64)) <= E
+
+
+def _edges(x, mn, rg, E):
+    """Exact interval of float32 normalised values passing the test, per point:
+    galloping from a passing start, then bisection over float ordinals.
+    Points with no passing value near (x - mn) / range get NaN edges."""
+    a0 = ((x.astype(np.float64) - mn) / rg).astype(np.float32)
+    start = _ord(a0)
+    found = _passes(a0, x, mn, rg, E)
+    for k in (1, -1, 2, -2, 3, -3, 4, -4):
+        c = ~found & _passes(_flt(_ord(a0) + k), x, mn, rg, E)
+        start = np.where(c, _ord(a0) + k, start)
+        found |= c
+    out = []
+    for d in (+1, -1):
+        good, step = start.copy(), np.ones_like(start)
+        bad = good + d
+        act = found & _passes(_flt(bad), x, mn, rg, E)
+        while act.any():
+            good = np.where(act, bad, good)
+            step = np.where(act, step * 2, step)
+            bad = np.where(act, good + d * step, bad)
+            act &= _passes(_flt(bad), x, mn, rg, E)
+        while True:
+            m = found & (np.abs(bad - good) > 1)
+            if not m.any():
+                break
+            mid = np.where(m, (good + bad) // 2, good)
+            ok = _passes(_flt(mid), x, mn, rg, E)
+            good = np.where(m & ok, mid, good)
+            bad = np.where(m & ~ok, mid, bad)
+        out.append(good)
+    hi, lo = out
+    nan = np.float32(np.nan)
+    return np.where(found, _flt(lo), nan), np.where(found, _flt(hi), nan), found
+
+
+BOUND_CASES = [("era5", v, 1e-1) for v in range(4)] + [("era5", v, 1e-3) for v in range(4)] + [
+    ("era5", 1, 1e-5), ("offset", 1000.0, 1e-2), ("offset", -2e5, 1e-4), ("spiky", 0.0, 1e-3),
+    ("era5_mn_not_float", 2, 1e-2), ("coarse", 5.0, 1e-2)]
+
+
+@pytest.mark.parametrize("case", BOUND_CASES)
+def test_acceptance_interval_edges_exact(B, case):
+    # every point's interval edges: the largest and smallest normalised values
+    # passing the FP64 test are counted, their outer neighbours are not
+    kind, p, rel = case
+    rng = np.random.default_rng(11)
+    if kind.startswith("era5"):
+        x = synth.era5_like(p, 7, 181, 360)
+    elif kind == "offset":
+        x = (p + abs(p) * 1e-6 * rng.standard_normal((181, 360))).astype(np.float32)
+    elif kind == "spiky":
+        x = synth.smooth_field(181, 360, seed=4, spikes=0.01)
+    else:
+        x = (p + 1e-3 * np.round(rng.standard_normal((181, 360)) * 40) / 40).astype(np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    mn, mx = float(x.min()), float(x.max())
+    if kind == "era5_mn_not_float":
+        mn -= 1e-4 * (mx - mn) / 3.0
+    rg = mx - mn
+    eps = rel * rg
+    guard = min(rg * 2.0 ** -17, eps / 4)
+    E = eps - guard
+    lo, hi, found = _edges(x.ravel(), mn, rg, E)
+    nf = int(found.sum())
+    assert nf > 0.9 * x.size
+    with np.errstate(invalid="ignore"):
+        probes = [(hi, nf), (_flt(_ord(hi) + 1), 0), (lo, nf), (_flt(_ord(lo) - 1), 0)]
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for a, expect in probes:
+        a = np.where(found, a, np.float32(np.nan)).astype(np.float32).reshape(x.shape)
+        B.ebcc_count_within_dev(dev(x), dev(a), mn, rg, eps, guard, cnt)
+        assert int(cnt.item()) == expect, (case, expect)
