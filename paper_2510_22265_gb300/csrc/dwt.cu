@@ -69,9 +69,12 @@ __global__ void __launch_bounds__(96) fwd_level(Live lv, const __grid_constant__
         for (int ly = 0; ly < EY; ly++) {
             const int gy = reflect(ty0 - HALO + ly, hp);
             const long long i = (long long)gy * ss + gx;
-            float v = INBQ(i, (long long)hp * ss) ? src[i] : 0.0f;
-            if (NORM) v = (float)(((double)v - mn) * inv);
-            w[ly] = v;
+            w[ly] = INBQ(i, (long long)hp * ss) ? src[i] : 0.0f;
+        }
+        if (NORM) {
+            const NormK k = make_norm_k(mn, inv);
+#pragma unroll
+            for (int ly = 0; ly < EY; ly++) w[ly] = norm_value(w[ly], k, mn, inv);
         }
 #pragma unroll
         for (int i = 1; i <= EY - 2; i += 2) w[i] += ALPHA * (w[i - 1] + w[i + 1]);

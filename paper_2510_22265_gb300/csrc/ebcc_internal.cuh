@@ -163,6 +163,84 @@ __device__ __forceinline__ float *plane_ptr(const FieldRun &r, int p) {
     default: return r.dst;
     }
 }
+
+// ---- FP64 expressions on float32 data, evaluated in float-float
+// Normalisation (x - mn) * inv and the residue (x - mn) * inv - a, each
+// rounded to float32 from FP64, are evaluated on float32 pairs (error-free
+// sums and products); the float-float value decides the rounding whenever it
+// lies further from both neighbouring float32 rounding midpoints than its
+// error bound plus the FP64 roundings (2^-44.5 (|t| + |r|) in all), else the
+// caller evaluates in FP64. Covered range: 2^-40 <= inv <= 2^40,
+// |mn| <= 2^40 and mn = 0 or |mn| >= 2^-60; per point |x| <= 2^40.
+struct NormK {
+    float mn_h, mn_l, i_h, i_l;
+    float d0;  // constant margin: split error of mn (when not a float) + underflow floor
+    int ok;
+};
+
+__device__ __forceinline__ NormK make_norm_k(double mn, double inv) {
+    NormK k;
+    k.ok = isfinite(mn) && inv >= 0x1p-40 && inv <= 0x1p40 && fabs(mn) <= 0x1p40 && (mn == 0.0 || fabs(mn) >= 0x1p-60);
+    k.mn_h = __double2float_rn(mn);
+    k.mn_l = __double2float_rn(mn - (double)k.mn_h);
+    k.i_h = __double2float_rn(inv);
+    k.i_l = __double2float_rn(inv - (double)k.i_h);
+    k.d0 = (k.mn_l != 0.0f ? fabsf(k.mn_h) * k.i_h * 0x1p-44f : 0.0f) + 0x1p-100f;
+    return k;
+}
+
+__device__ __forceinline__ void ff_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ float ff_step(float a, int d) {  // neighbouring float (d = +-1), +0 and -0 distinct
+    int32_t b = __float_as_int(a);
+    int32_t o = b >= 0 ? b : b ^ 0x7FFFFFFF;
+    o += d;
+    return __int_as_float(o >= 0 ? o : o ^ 0x7FFFFFFF);
+}
+
+// t1 + t2 ~ (x - mn) * inv, |t2| <= ulp(t1) / 2
+__device__ __forceinline__ void ff_norm(float x, const NormK &k, float &t1, float &t2) {
+    float p, q, ch, cl;
+    ff_sum(x, -k.mn_h, p, q);
+    ff_sum(p, __fsub_rn(q, k.mn_l), ch, cl);
+    const float m = __fmul_rn(ch, k.i_h);
+    const float em = __fmaf_rn(ch, k.i_h, -m);
+    const float tl = __fadd_rn(em, __fmaf_rn(ch, k.i_l, __fmul_rn(cl, k.i_h)));
+    t1 = __fadd_rn(m, tl);
+    t2 = __fsub_rn(tl, __fsub_rn(t1, m));
+}
+
+// t1 when t1 + t2 lies at least m from both rounding midpoints around t1
+__device__ __forceinline__ bool ff_round(float t1, float t2, float m) {
+    const float gap = t2 >= 0.0f ? __fsub_rn(__fmul_rn(__fsub_rn(ff_step(t1, 1), t1), 0.5f), t2)
+                                 : __fadd_rn(__fmul_rn(__fsub_rn(t1, ff_step(t1, -1)), 0.5f), t2);
+    return gap >= m;
+}
+
+// float32(FP64 (x - mn) * inv)
+__device__ __forceinline__ float norm_value(float x, const NormK &k, double mn, double inv) {
+    if (k.ok && fabsf(x) <= 0x1p40f) {
+        float t1, t2;
+        ff_norm(x, k, t1, t2);
+        if (ff_round(t1, t2, __fmaf_rn(fabsf(t1), 0x1p-42f, k.d0))) return t1;
+    }
+    return __double2float_rn(__dmul_rn(__dsub_rn((double)x, mn), inv));
+}
+
+// float32(FP64 ((x - mn) * inv - a))
+__device__ __forceinline__ float residue_value(float x, float a, const NormK &k, double mn, double inv) {
+    if (k.ok && fabsf(x) <= 0x1p40f && fabsf(a) <= 0x1p40f) {
+        float t1, t2, u, w, r1, r2;
+        ff_norm(x, k, t1, t2);
+        ff_sum(t1, -a, u, w);
+        ff_sum(u, __fadd_rn(w, t2), r1, r2);
+        if (ff_round(r1, r2, __fmaf_rn(fabsf(t1) + fabsf(r1), 0x1p-42f, k.d0))) return r1;
+    }
+    return __double2float_rn(__dsub_rn(__dmul_rn(__dsub_rn((double)x, mn), inv), (double)a));
+}
 #endif
 
 // largest per-level extents over the fields of a batch (grid sizes)

@@ -365,9 +365,10 @@ __global__ void __launch_bounds__(NT) residue_kernel(Live lv, const __grid_const
     const float *__restrict__ ab = r->Abase;
     float *__restrict__ res = r->R;
     const double mn = r->mn, inv = r->inv_range;
+    const NormK k = make_norm_k(mn, inv);
     const long long n = r->N;
     for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT)
-        res[i] = __double2float_rn(__dsub_rn(__dmul_rn(__dsub_rn((double)x[i], mn), inv), (double)ab[i]));
+        res[i] = residue_value(x[i], ab[i], k, mn, inv);
 }
 
 __global__ void __launch_bounds__(NT) squant_kernel(Live lv, const __grid_constant__ FieldRun one) {
