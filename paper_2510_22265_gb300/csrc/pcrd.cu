@@ -200,8 +200,11 @@ __global__ void select_kernel(Hulls h, const int *nseg, const double *budget, Se
     *out = select_for_budget(h.skey, h.cum, *nseg, *budget);
 }
 
-__global__ void npass_kernel(Live lv, const __grid_constant__ FieldRun one, Hulls h, const char *sel_base,
-                             size_t sel_stride, int32_t *npass_out) {
+// one thread per code-block: the kept passes are those of the leading run of
+// hull keys at or above the threshold, read 8 keys (and their pass counts) at
+// a time so the loads of a chunk are in flight together
+__global__ void __launch_bounds__(128) npass_kernel(Live lv, const __grid_constant__ FieldRun one, Hulls h,
+                                                    const char *sel_base, size_t sel_stride, int32_t *npass_out) {
     int f;
     const FieldRun *r = pick(lv, one, blockIdx.y, f);
     if (!r) return;
@@ -209,14 +212,27 @@ __global__ void npass_kernel(Live lv, const __grid_constant__ FieldRun one, Hull
     if (b >= r->nblk) return;
     const Sel s = *(const Sel *)(sel_base + (size_t)f * sel_stride);
     const int gb = r->blk0 + b;
-    const int nh = h.nh[gb];
+    const int lim = min(h.nh[gb], h.maxpt);
     const size_t base = (size_t)gb * h.maxpt;
     int n = 0;
     if (s.mode == 1)
-        for (int k = 1; k < nh; k++) {
-            if (!INB(k, h.maxpt)) break;
-            if (h.key[base + k] >= s.thr) n = h.pt[base + k];
-            else break;
+        for (int k0 = 1; k0 < lim; k0 += 8) {
+            uint64_t kv[8];
+            int pv[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const int k = k0 + j;
+                kv[j] = k < lim ? h.key[base + k] : 0;
+                pv[j] = k < lim ? h.pt[base + k] : 0;
+            }
+            bool stop = false;
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                if (stop) break;
+                if (k0 + j < lim && kv[j] >= s.thr) n = pv[j];
+                else stop = true;
+            }
+            if (stop) break;
         }
     npass_out[gb] = n;
 }

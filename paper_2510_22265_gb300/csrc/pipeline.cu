@@ -6,9 +6,9 @@
 // Algorithm 1 are device-side state machines, one per field: after each
 // evaluation (PCRD selection for the current ratio, base reconstruction from
 // the tier-1 trace, inverse DWT with the bound test fused into its last level)
-// a one-CTA kernel advances every live field's bracketing / bisection exactly
-// as Algorithm 1 prints it, sets up its next evaluation, and compacts the list
-// of fields still iterating.  The host only launches: it learns the live count
+// a kernel with one warp per live field advances its bracketing / bisection
+// exactly as Algorithm 1 prints it and sets up its next evaluation, and a
+// one-CTA kernel compacts the list of fields still iterating.  The host only launches: it learns the live count
 // one evaluation late (a pinned copy), so the GPU never waits on the host
 // inside a loop, and the grids shrink as fields finish.  A batch of one field
 // is the plain path.
@@ -89,11 +89,6 @@ __device__ void bl_step(BaseLoop &s, double qA) {
     }
 }
 
-__device__ __forceinline__ Sel select_field(const Hulls &h, const FieldRun &r, double B) {
-    const long long sb = (long long)r.blk0 * T1_MAXPASS;
-    return select_for_budget(h.skey + sb, h.cum + sb, r.sc->nseg, B);
-}
-
 // Live lists: live[0] = count, live[1 + k] = table index of grid slot k.
 // One CTA runs `step` on every listed field and keeps, in order and in place,
 // those for which it returns true.
@@ -140,58 +135,169 @@ struct EvalCache {
     unsigned long long count[EVC];
 };
 
-// set up the evaluation at s.budget, resolving selections already evaluated
-__device__ void bl_advance(BaseLoop &s, const FieldRun &r, const Hulls &h, const EvalCache &c) {
-    while (!s.done) {
-        s.sel_eval = select_field(h, r, s.budget);
-        int k = -1;
-        for (int j = 0; j < c.n && j < EVC; j++)
-            if (c.sel[j].mode == s.sel_eval.mode && (s.sel_eval.mode == 0 || c.sel[j].thr == s.sel_eval.thr)) {
-                k = j;
-                break;
-            }
-        if (k < 0) return;  // a new selection: evaluate it
-        bl_step(s, (double)c.count[k] / s.N);
+// ---- loop steps, one warp per live field: a selection's searches split their
+// range 33 ways per round (a few dependent loads instead of a binary search's
+// ~16), and the evaluation cache is scanned 32 entries at a time
+
+// largest index in (lo, hi) where pred holds (pred holds on a prefix; lo is
+// returned when it holds nowhere)
+template <typename P>
+__device__ __forceinline__ int warp_last_true(int lo, int hi, int lane, P pred) {
+    while (hi - lo > 1) {
+        const long long span = (long long)hi - lo;
+        const int p = span <= 33 ? lo + 1 + lane : lo + (int)(span * (lane + 1) / 33);
+        const bool valid = p < hi;
+        const bool t = valid && pred(p);
+        const unsigned yes = __ballot_sync(0xffffffffu, t), no = __ballot_sync(0xffffffffu, valid && !t);
+        if (yes) lo = __shfl_sync(0xffffffffu, p, 31 - __clz(yes));
+        if (no) hi = __shfl_sync(0xffffffffu, p, __ffs(no) - 1);
+    }
+    return lo;
+}
+
+// select_for_budget with the whole warp (same result on every lane)
+__device__ Sel select_field_w(const Hulls &h, const FieldRun &r, double B, int lane) {
+    const long long sb = (long long)r.blk0 * T1_MAXPASS;
+    const uint64_t *skey = h.skey + sb;
+    const unsigned long long *cum = h.cum + sb;
+    const int m = r.sc->nseg;
+    Sel s;
+    s.thr = 0; s.mode = 0; s.pad = 0;
+    int i = warp_last_true(-1, m, lane, [&](int p) { return (double)cum[p] <= B; });
+    if (i < 0) return s;
+    if (i + 1 < m && skey[i + 1] == skey[i]) {  // that group does not fit whole
+        const unsigned long long kk = skey[i];
+        i = warp_last_true(-1, i, lane, [&](int p) { return skey[p] > kk; });
+        if (i < 0) return s;
+    }
+    s.thr = skey[i];
+    s.mode = 1;
+    return s;
+}
+
+// the evaluation cache of one field held in the warp's registers: lane l
+// holds entries l, l + 32 and l + 64
+struct WarpCache {
+    Sel sel[EVC / 32];
+    unsigned long long count[EVC / 32];
+    int n;
+};
+static_assert(EVC % 32 == 0, "cache entries are spread over the lanes");
+
+__device__ __forceinline__ void wc_load(WarpCache &w, const EvalCache &c, int nc, int lane) {
+    w.n = nc;
+#pragma unroll
+    for (int q = 0; q < EVC / 32; q++) {
+        const int j = q * 32 + lane;
+        if (j < nc) { w.sel[q] = c.sel[j]; w.count[q] = c.count[j]; }
+        else { w.sel[q].mode = -1; w.count[q] = 0; }
     }
 }
 
-__global__ void __launch_bounds__(1024) bl_start(BaseLoop *bl, EvalCache *evc, const FieldRun *tab, double q,
-                                                 int fallback, double r0, double tol, Hulls h, int *live) {
-    compact(live, [&](int f) {
-        const FieldRun &r = tab[f];
-        EvalCache &c = evc[f];
-        if (!fallback) c.n = 0;  // a new field: nothing evaluated yet
-        BaseLoop s;
-        memset(&s, 0, sizeof(s));
-        s.q = q; s.r0 = r0; s.tol = tol; s.N = (double)r.N; s.rmax = 4.0 * (double)r.N;
-        s.fallback = fallback; s.phase = 0; s.budget = 4.0 * (double)r.N / r0;
-        bl_advance(s, r, h, c);
-        bl[f] = s;
-        r.sc->cnt[0] = 0;
-        return !s.done;
-    });
+__device__ void bl_advance_w(BaseLoop &s, const FieldRun &r, const Hulls &h, const WarpCache &w, int lane) {
+    while (!s.done) {
+        s.sel_eval = select_field_w(h, r, s.budget, lane);
+        int k = -1;
+        unsigned long long cnt = 0;
+#pragma unroll
+        for (int q = 0; q < EVC / 32; q++) {
+            const bool hit = q * 32 + lane < w.n && w.sel[q].mode == s.sel_eval.mode &&
+                             (s.sel_eval.mode == 0 || w.sel[q].thr == s.sel_eval.thr);
+            const unsigned b = __ballot_sync(0xffffffffu, hit);
+            if (k < 0 && b) {
+                const int src = __ffs(b) - 1;
+                k = q * 32 + src;
+                cnt = __shfl_sync(0xffffffffu, w.count[q], src);
+            }
+        }
+        if (k < 0) return;  // a new selection: evaluate it
+        bl_step(s, (double)cnt / s.N);
+    }
 }
 
-__global__ void __launch_bounds__(1024) bl_update(BaseLoop *bl, EvalCache *evc, const FieldRun *tab, Hulls h,
-                                                  int *live) {
-    compact(live, [&](int f) {
-        BaseLoop s = bl[f];
-        const FieldRun &r = tab[f];
-        EvalCache &c = evc[f];
-        if (!s.done) {
-            const unsigned long long cnt = r.sc->cnt[0];
-            r.sc->cnt[0] = 0;
-            if (c.n < EVC) {
-                c.sel[c.n] = s.sel_eval;
-                c.count[c.n] = cnt;
-                c.n++;
+// one warp per live slot; keep[slot] = the field's loop goes on
+__global__ void __launch_bounds__(256) bl_start_w(BaseLoop *bl, EvalCache *evc, const FieldRun *tab, double q,
+                                                  int fallback, double r0, double tol, Hulls h, const int *live,
+                                                  int *keep) {
+    const int lane = threadIdx.x & 31, k = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (k >= live[0]) return;
+    const int f = live[1 + k];
+    const FieldRun &r = tab[f];
+    EvalCache &c = evc[f];
+    const int nc = fallback ? min(c.n, EVC) : 0;  // a new field: nothing evaluated yet
+    WarpCache w;
+    wc_load(w, c, nc, lane);
+    __syncwarp();
+    if (lane == 0 && !fallback) c.n = 0;
+    BaseLoop s;
+    memset(&s, 0, sizeof(s));
+    s.q = q; s.r0 = r0; s.tol = tol; s.N = (double)r.N; s.rmax = 4.0 * (double)r.N;
+    s.fallback = fallback; s.phase = 0; s.budget = 4.0 * (double)r.N / r0;
+    bl_advance_w(s, r, h, w, lane);
+    if (lane == 0) {
+        bl[f] = s;
+        r.sc->cnt[0] = 0;
+        keep[k] = !s.done;
+    }
+}
+
+__global__ void __launch_bounds__(256) bl_update_w(BaseLoop *bl, EvalCache *evc, const FieldRun *tab, Hulls h,
+                                                   const int *live, int *keep) {
+    const int lane = threadIdx.x & 31, k = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (k >= live[0]) return;
+    const int f = live[1 + k];
+    BaseLoop s = bl[f];
+    const FieldRun &r = tab[f];
+    EvalCache &c = evc[f];
+    if (!s.done) {
+        const unsigned long long cnt = r.sc->cnt[0];
+        const int nc = min(c.n, EVC);
+        WarpCache w;
+        wc_load(w, c, nc, lane);
+        __syncwarp();
+        if (nc < EVC) {  // record this evaluation, in memory and in the registers
+            if (lane == 0) {
+                c.sel[nc] = s.sel_eval;
+                c.count[nc] = cnt;
+                c.n = nc + 1;
             }
-            bl_step(s, (double)cnt / s.N);
-            bl_advance(s, r, h, c);
-            bl[f] = s;
+#pragma unroll
+            for (int q = 0; q < EVC / 32; q++)
+                if (q * 32 + lane == nc) { w.sel[q] = s.sel_eval; w.count[q] = cnt; }
+            w.n = nc + 1;
         }
-        return !s.done;
-    });
+        if (lane == 0) r.sc->cnt[0] = 0;
+        bl_step(s, (double)cnt / s.N);
+        bl_advance_w(s, r, h, w, lane);
+        if (lane == 0) bl[f] = s;
+    }
+    if (lane == 0) keep[k] = !s.done;
+}
+
+// drop the slots whose keep flag is 0 from the live list (order kept)
+__global__ void __launch_bounds__(1024) live_compact(int *live, const int *keep) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    __shared__ int ws[32];
+    __shared__ int out;
+    const int n = live[0];
+    if (tid == 0) out = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+        const int k = c0 + tid;
+        const bool kp = k < n && keep[k];
+        const int f = k < n ? live[1 + k] : -1;
+        const unsigned m = __ballot_sync(0xffffffffu, kp);
+        if (lane == 0) ws[wid] = __popc(m);
+        __syncthreads();
+        int off = out;
+        for (int q = 0; q < wid; q++) off += ws[q];
+        if (kp) live[1 + off + __popc(m & ((1u << lane) - 1))] = f;
+        __syncthreads();
+        if (tid == 0)
+            for (int q = 0; q < nw; q++) out += ws[q];
+        __syncthreads();
+    }
+    if (tid == 0) live[0] = out;
 }
 
 struct TruncLoop {
@@ -606,6 +712,7 @@ struct Batch {
     TruncLoop *tl = nullptr;
     long long *stop = nullptr;      // F: truncation search limits
     int *live = nullptr;            // F + 1
+    int *keep = nullptr;            // F: per live slot, the loop goes on
     int *list = nullptr;            // F
     int *es = nullptr;              // F
     Sel *sel = nullptr;             // F
@@ -694,6 +801,7 @@ void layout_compress(Arena &a, Batch &b, const std::vector<int> &ny, const std::
     b.tl = carve<TruncLoop>(a, F);
     b.stop = carve<long long>(a, F + 1);
     b.live = carve<int>(a, F + 1);
+    b.keep = carve<int>(a, F + 1);
     b.list = carve<int>(a, F + 1);
     b.es = carve<int>(a, F + 1);
     b.sel = carve<Sel>(a, F + 1);
@@ -848,7 +956,10 @@ int run_base_loop(Engine &e, Batch &b, const std::vector<int> &A, double q, int 
     const int n = (int)A.size();
     if (!n) return EBCC_OK;
     RC(set_list(e, b, A, st));
-    PROF("bl_start", st, 0.0, bl_start<<<1, 1024, 0, st>>>(b.bl, b.evc, b.d_run, q, fallback, p.r0, p.tol, b.hull, b.live));
+    PROF("bl_start", st, 0.0,
+         bl_start_w<<<(n + 7) / 8, 256, 0, st>>>(b.bl, b.evc, b.d_run, q, fallback, p.r0, p.tol, b.hull, b.live, b.keep));
+    CK(cudaGetLastError());
+    PROF("live_compact", st, 0.0, live_compact<<<1, 1024, 0, st>>>(b.live, b.keep));
     CK(cudaGetLastError());
     int *slot = stage_take<int>(e, 2);
     if (!slot) return EBCC_ECAPACITY;
@@ -863,7 +974,11 @@ int run_base_loop(Engine &e, Batch &b, const std::vector<int> &A, double q, int 
         rc = pcrd_npass_b(lv, kNone, hn, b.dims.maxnblk, b.hull, sel, sizeof(BaseLoop), b.npass, st);
         if (!rc) rc = base_eval(b, lv, hn, fin, st);
         if (rc) break;
-        PROF("bl_update", st, 0.0, bl_update<<<1, 1024, 0, st>>>(b.bl, b.evc, b.d_run, b.hull, b.live));
+        PROF("bl_update", st, 0.0, bl_update_w<<<(hn + 7) / 8, 256, 0, st>>>(b.bl, b.evc, b.d_run, b.hull, b.live, b.keep));
+        if (!rc && cudaGetLastError() != cudaSuccess) rc = EBCC_ECUDA;
+        PROF("live_compact", st, 0.0, live_compact<<<1, 1024, 0, st>>>(b.live, b.keep));
+        if (!rc && cudaGetLastError() != cudaSuccess) rc = EBCC_ECUDA;
+        if (rc) break;
         if (ebcc_debug_sync_enabled() && ebcc_stage_check(st, "base eval", __LINE__)) { rc = EBCC_ECUDA; break; }
         if (cudaMemcpyAsync(&slot[step & 1], b.live, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaEventRecord(e.ev[step & 1], st) != cudaSuccess) { rc = EBCC_ECUDA; break; }
