@@ -138,6 +138,25 @@ __device__ __forceinline__ void block_count_add(unsigned long long v, unsigned l
     }
 }
 
+// block sums of the points inside and outside the bound -> two counters
+template <int NTH>
+__device__ __forceinline__ void block_count_fail_add(unsigned long long in, unsigned long long out,
+                                                     unsigned long long *dst_in, unsigned long long *dst_out) {
+    __shared__ unsigned long long red[2][NTH / 32];
+    for (int o = 16; o; o >>= 1) {
+        in += __shfl_down_sync(0xffffffffu, in, o);
+        out += __shfl_down_sync(0xffffffffu, out, o);
+    }
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = in; red[1][threadIdx.x >> 5] = out; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long a = 0, b = 0;
+        for (int i = 0; i < NTH / 32; i++) { a += red[0][i]; b += red[1][i]; }
+        if (a) atomicAdd(dst_in, a);
+        if (b) atomicAdd(dst_out, b);
+    }
+}
+
 // the last step of an inverse transform at point gi of field r
 __device__ __forceinline__ void finish_point(const InvFinal &fin, const FieldRun &r, float *dst, float v, long long gi,
                                              unsigned long long &cnt) {
@@ -160,7 +179,7 @@ __device__ __forceinline__ void finish_point(const InvFinal &fin, const FieldRun
 
 constexpr int IT = 96;  // threads of an inverse-level CTA (72 stage the tile's columns)
 
-// inverse level l of the field in grid slot blockIdx.z: LL (the Mallat array
+// inverse level l of the field in grid slot blockIdx.x (tile blockIdx.y, .z): LL (the Mallat array
 // at the top level, else the scratch of level l + 1) + detail bands of plane
 // `src` -> the level-(l-1) region: the scratch of level l, or at level 1 the
 // finished output per fin.  Thread c < EX stages column c of the extended
@@ -172,12 +191,22 @@ template <int MODE>
 __global__ void __launch_bounds__(IT, 10) inv_level(Live lv, const __grid_constant__ FieldRun one, int l, int src_plane,
                                                 InvFinal fin) {
     int f;
-    const FieldRun *r = pick(lv, one, blockIdx.z, f);
+    const FieldRun *r = pick(lv, one, blockIdx.x, f);
     if (!r || l > r->L) return;
     const int nx = r->nx, L = r->L;
     const int hp = ceil_sh(r->ny, l - 1), wp = ceil_sh(nx, l - 1);
-    const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
+    const int ty0 = blockIdx.z * TY, tx0 = blockIdx.y * TX;
     if (ty0 >= hp || tx0 >= wp) return;
+    const int tid = threadIdx.x;
+    if (MODE == 1) {  // base-loop count: nothing left to decide once enough points fail
+        __shared__ int quit;
+        if (tid == 0) {
+            const unsigned long long thr = r->sc->fail_thr;
+            quit = thr != 0 && *(volatile unsigned long long *)&r->sc->fail >= thr;
+        }
+        __syncthreads();
+        if (quit) return;
+    }
     const float *__restrict__ coef = plane_ptr(*r, src_plane);
     const float *__restrict__ ll = l < L ? (((l + 1) & 1) ? r->s2 : r->s1) : coef;
     const int ls = l < L ? ceil_sh(nx, l) : nx;
@@ -186,7 +215,6 @@ __global__ void __launch_bounds__(IT, 10) inv_level(Live lv, const __grid_consta
     constexpr int mode = MODE;
     const int ncoef = (int)r->N;
     const int hl = (hp + 1) >> 1, wl = (wp + 1) >> 1;
-    const int tid = threadIdx.x;
     __shared__ float t[EY][EX + 1];
     // interior tile: the halo needs no reflection, every index is in range
     const bool interior = ty0 >= HALO && tx0 >= HALO && ty0 + TY + HALO <= hp && tx0 + TX + HALO <= wp;
@@ -243,7 +271,7 @@ __global__ void __launch_bounds__(IT, 10) inv_level(Live lv, const __grid_consta
         for (int i = 0; i < EX; i++) t[tid][i] = v[i];
     }
     __syncthreads();
-    unsigned long long cnt = 0;
+    unsigned long long cnt = 0, npts = 0;
     if (tid < TX) {  // columns: thread c lifts column HALO + c and finishes its TY outputs
         float w[EY];
 #pragma unroll
@@ -261,6 +289,7 @@ __global__ void __launch_bounds__(IT, 10) inv_level(Live lv, const __grid_consta
         const int gx = tx0 + tid;
         if (gx < wp) {
             const int nr = hp - ty0 < TY ? hp - ty0 : TY;
+            npts = nr;
             if (mode < 0) {
                 const int lim = l == 1 ? ncoef : hp * ds;
 #pragma unroll
@@ -315,7 +344,8 @@ __global__ void __launch_bounds__(IT, 10) inv_level(Live lv, const __grid_consta
             }
         }
     }
-    if (mode == 1 || mode == 2) block_count_add<IT>(cnt, &r->sc->cnt[fin.counter]);
+    if (mode == 1) block_count_fail_add<IT>(cnt, npts - cnt, &r->sc->cnt[fin.counter], &r->sc->fail);
+    if (mode == 2) block_count_add<IT>(cnt, &r->sc->cnt[fin.counter]);
 }
 
 // fields with no DWT level: the transform is the identity
@@ -398,7 +428,11 @@ int dwt_inverse_b(const Live &lv, const FieldRun &one, int nslots, const BatchDi
     }
     for (int l = d.maxL; l >= 1; l--) {
         const int hp = d.h[l - 1], wp = d.w[l - 1];
-        dim3 grid((wp + TX - 1) / TX, (hp + TY - 1) / TY, nslots);
+        // field slot fastest: the tiles of a field are spread over the launch,
+        // so a count that is already decided skips the rest of its tiles
+        const int ntx = (wp + TX - 1) / TX, nty = (hp + TY - 1) / TY;
+        if (ntx > 65535 || nty > 65535) return EBCC_EINVAL;
+        dim3 grid(nslots, ntx, nty);
         // algorithmic bytes: read the level's coefficients, then write the
         // region (levels > 1) or finish it (read bounds / base as needed)
         double per = 4.0;

@@ -92,6 +92,8 @@ struct FieldScal {
     long long T;                   // truncation (bits) under evaluation
     unsigned long long cnt[2];     // counters of the base loop and the truncation loop
     unsigned long long nesc;       // escaped points
+    unsigned long long fail;       // base-loop evaluation: points found outside the bound so far
+    unsigned long long fail_thr;   // a count below q N is certain once fail reaches this (0: count everything)
     unsigned long long tot[2];     // base section: metadata bytes, payload bytes
     long long refine_start[32];    // SPIHT: bit offset of each plane's refinement pass
 };

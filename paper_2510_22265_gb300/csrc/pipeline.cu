@@ -127,7 +127,9 @@ __device__ void compact(int *live, F &&step) {
 // many budgets select the same segments (the bisection's late steps move the
 // budget less than one segment's bytes; the q = 1 loop retraces the q loop's
 // bracketing from r0), so a selection met again is answered from here instead
-// of being evaluated again -- the loops' decisions are unchanged.
+// of being evaluated again -- the loops' decisions are unchanged. A count
+// whose evaluation stopped early (fail_threshold) is recorded as it stood:
+// below q N, so it decides the same way in every loop of the field.
 constexpr int EVC = 96;
 struct EvalCache {
     int n, pad;
@@ -215,6 +217,23 @@ __device__ void bl_advance_w(BaseLoop &s, const FieldRun &r, const Hulls &h, con
     }
 }
 
+// the smallest number of points outside the bound that makes a count c of N
+// fail the test c / N < q of Algorithm 1 certain: N - (largest c with c / N < q)
+// in the loop's own double arithmetic. An evaluation stops counting once that
+// many points fail (its count is then only known to be below q N, which
+// decides every comparison the loop makes with q, and every later loop of the
+// field runs with a q at least as large)
+__device__ unsigned long long fail_threshold(long long N, double q) {
+    const double Nd = (double)N;
+    long long c = (long long)floor(q * Nd);
+    if (c > N) c = N;
+    if (c < 0) c = 0;
+    while (c > 0 && !((double)c / Nd < q)) c--;
+    while (c + 1 <= N && (double)(c + 1) / Nd < q) c++;
+    if (!((double)c / Nd < q)) return 0;  // no count fails: count everything
+    return (unsigned long long)(N - c);
+}
+
 // one warp per live slot; keep[slot] = the field's loop goes on
 __global__ void __launch_bounds__(256) bl_start_w(BaseLoop *bl, EvalCache *evc, const FieldRun *tab, double q,
                                                   int fallback, double r0, double tol, Hulls h, const int *live,
@@ -237,6 +256,8 @@ __global__ void __launch_bounds__(256) bl_start_w(BaseLoop *bl, EvalCache *evc, 
     if (lane == 0) {
         bl[f] = s;
         r.sc->cnt[0] = 0;
+        r.sc->fail = 0;
+        r.sc->fail_thr = s.done ? 0 : fail_threshold(r.N, q);
         keep[k] = !s.done;
     }
 }
@@ -266,10 +287,16 @@ __global__ void __launch_bounds__(256) bl_update_w(BaseLoop *bl, EvalCache *evc,
                 if (q * 32 + lane == nc) { w.sel[q] = s.sel_eval; w.count[q] = cnt; }
             w.n = nc + 1;
         }
-        if (lane == 0) r.sc->cnt[0] = 0;
+        if (lane == 0) {
+            r.sc->cnt[0] = 0;
+            r.sc->fail = 0;
+        }
         bl_step(s, (double)cnt / s.N);
         bl_advance_w(s, r, h, w, lane);
-        if (lane == 0) bl[f] = s;
+        if (lane == 0) {
+            bl[f] = s;
+            if (s.done) r.sc->fail_thr = 0;
+        }
     }
     if (lane == 0) keep[k] = !s.done;
 }
