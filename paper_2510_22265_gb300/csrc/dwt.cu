@@ -188,7 +188,7 @@ constexpr int IT = 96;  // threads of an inverse-level CTA (72 stage the tile's 
 // MODE: the finish this launch applies (fin.mode at level 1, -1 above), as a
 // template parameter so each instantiation carries only its own finish
 template <int MODE>
-__global__ void __launch_bounds__(IT, 10) inv_level(Live lv, const __grid_constant__ FieldRun one, int l, int src_plane,
+__global__ void __launch_bounds__(IT, 12) inv_level(Live lv, const __grid_constant__ FieldRun one, int l, int src_plane,
                                                 InvFinal fin) {
     int f;
     const FieldRun *r = pick(lv, one, blockIdx.x, f);
