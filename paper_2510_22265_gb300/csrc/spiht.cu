@@ -10,9 +10,10 @@
 // Encoder: the set maxima (max |s| over all descendants, and over descendants
 // beyond the children) come from one full-grid kernel per level, bottom up.
 // Then one CTA per field runs the bit-planes.  Each list pass is processed in
-// chunks of 1024 entries: every thread evaluates its entry's tests, a
-// block-wide exclusive scan of (bits, LIP appends, LSP appends, next-wave
-// appends, stays) gives every output position, and the chunk's 1-bits are
+// chunks of 1024 threads x a few consecutive entries (8 of the LIP or LSP, 4
+// of the LIS): every thread evaluates its entries' tests, a block-wide
+// exclusive scan of (bits, LIP appends, LSP appends, next-wave appends,
+// stays) gives every thread's output positions, and the chunk's 1-bits are
 // gathered in a shared-memory window before being OR-ed into the stream.  A
 // sorting pass over the LIS runs as waves: the entries a pass appends form the
 // next wave, processed in append order -- exactly the order of the sequential
@@ -136,7 +137,9 @@ __global__ void maxima_kernel(Live lv, const __grid_constant__ FieldRun one, int
 
 constexpr int ET = 1024;
 constexpr int NQ = 5;
-constexpr int WIN_WORDS = 640;  // >= 1024 entries * 19 bits / 32 + 2
+constexpr int EPL = 8;  // LIP and LSP entries per thread in a chunk
+constexpr int EPS = 4;  // LIS entries per thread in a chunk
+constexpr int WIN_WORDS = ET * EPS * 19 / 32 + 2;  // a LIS entry emits at most 19 bits
 
 struct EncShared {
     unsigned long long pos;
@@ -271,36 +274,52 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
     for (int n = nmax; n >= 0; n--) {
         const uint32_t T = 1u << n;
         const long long lsp_before = sh.nlsp;
-        // ---- sorting pass: LIP
+        // ---- sorting pass: LIP (EPL consecutive entries per thread; the
+        // entries are held in registers, as the pass compacts the list in place)
         {
             const long long nl = sh.nlip;
             long long keep_n = 0;
-            for (long long base = 0; base < nl; base += ET) {
-                long long k = base + tid;
+            for (long long base = 0; base < nl; base += (long long)ET * EPL) {
+                const long long k0 = base + (long long)tid * EPL;
                 int v[NQ] = {0, 0, 0, 0, 0};
-                uint32_t x = 0;
-                bool sg = false;
-                if (k < nl) {
-                    x = INB(k, NN) ? lip[k] : 0;
-                    if (!INB(x, NN)) x = 0;
-                    sg = absi(s[x]) >= T;
-                    v[0] = 1 + sg; v[1] = !sg; v[2] = sg;
+                uint32_t xs[EPL];
+                unsigned sgm = 0;
+#pragma unroll
+                for (int j = 0; j < EPL; j++) {
+                    const long long k = k0 + j;
+                    uint32_t x = 0;
+                    if (k < nl) {
+                        x = INB(k, NN) ? lip[k] : 0;
+                        if (!INB(x, NN)) x = 0;
+                        const bool sg = absi(s[x]) >= T;
+                        sgm |= (unsigned)sg << j;
+                        v[0] += 1 + sg; v[1] += !sg; v[2] += sg;
+                    }
+                    xs[j] = x;
                 }
                 if (tid == 0) sh.wbase = sh.pos >> 5;
                 win_clear(sh);
                 block_scan(v, sh);
-                const unsigned long long bp = sh.pos + v[0];
-                if (k < nl) {
-                    if (sg) {
+                unsigned long long bp = sh.pos + v[0];
+                long long keep = keep_n + v[1], ls = sh.nlsp + v[2];
+#pragma unroll
+                for (int j = 0; j < EPL; j++) {
+                    if (k0 + j >= nl) break;
+                    const uint32_t x = xs[j];
+                    if ((sgm >> j) & 1) {
                         win_set(sh, bp);
                         if (s[x] < 0) win_set(sh, bp + 1);
-                        if (INB(sh.nlsp + v[2], NN)) {
-                        sig_pos[x] = (uint32_t)(bp + 1);
-                        lsp_idx[x] = (uint32_t)(sh.nlsp + v[2]);
-                        lsp[sh.nlsp + v[2]] = x;
+                        if (INB(ls, NN)) {
+                            sig_pos[x] = (uint32_t)(bp + 1);
+                            lsp_idx[x] = (uint32_t)ls;
+                            lsp[ls] = x;
                         }
+                        ls++;
+                        bp += 2;
                     } else {
-                        if (INB(keep_n + v[1], NN)) lip[keep_n + v[1]] = x;
+                        if (INB(keep, NN)) lip[keep] = x;
+                        keep++;
+                        bp += 1;
                     }
                 }
                 __syncthreads();
@@ -323,50 +342,67 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
             while (ncur > 0) {
                 if (tid == 0) sh.nnext = 0;
                 __syncthreads();
-                for (long long base = 0; base < ncur; base += ET) {
-                    long long k = base + tid;
+                for (long long base = 0; base < ncur; base += (long long)ET * EPS) {
+                    // EPS consecutive entries per thread: counts first, then
+                    // (after the scan) the same tests again for the outputs
+                    const long long k0 = base + (long long)tid * EPS;
                     int v[NQ] = {0, 0, 0, 0, 0};
-                    uint32_t e = 0, idx = 0, c[9];
-                    int nc = 0;
-                    bool sg = false;
-                    uint32_t sigmask = 0;
-                    if (k < ncur) {
-                        e = INB(k, NN) ? cur[k] : 0;
-                        if (!INB(e >> 1, NN)) e = 0;
-                        idx = e >> 1;
-                        v[0] = 1;
-                        if ((e & 1) == 0) {  // type A: S_n(D)
-                            sg = maxd[idx] >= T;
-                            if (sg) {
-                                nc = children(g, idx, c);
-                                for (int q = 0; q < nc; q++) {
-                                    if (!INB(c[q], NN)) c[q] = 0;
-                                    bool cs = absi(s[c[q]]) >= T;
-                                    sigmask |= (uint32_t)cs << q;
-                                    v[0] += 1 + cs; v[1] += !cs; v[2] += cs;
+                    uint32_t es[EPS];
+#pragma unroll
+                    for (int j = 0; j < EPS; j++) {
+                        const long long k = k0 + j;
+                        uint32_t e = 0;
+                        if (k < ncur) {
+                            e = INB(k, NN) ? cur[k] : 0;
+                            if (!INB(e >> 1, NN)) e = 0;
+                            const uint32_t idx = e >> 1;
+                            v[0] += 1;
+                            if ((e & 1) == 0) {  // type A: S_n(D)
+                                if (maxd[idx] >= T) {
+                                    uint32_t c[9];
+                                    const int nc = children(g, idx, c);
+                                    for (int q = 0; q < nc; q++) {
+                                        const uint32_t cq = INB(c[q], NN) ? c[q] : 0;
+                                        const bool cs = absi(s[cq]) >= T;
+                                        v[0] += 1 + cs; v[1] += !cs; v[2] += cs;
+                                    }
+                                    v[3] += has_L(g, idx);
+                                } else {
+                                    v[4] += 1;
                                 }
-                                v[3] = has_L(g, idx);
-                            } else {
-                                v[4] = 1;
+                            } else {  // type B: S_n(L)
+                                if (maxl[idx] >= T) {
+                                    uint32_t c[9];
+                                    v[3] += children(g, idx, c);
+                                } else {
+                                    v[4] += 1;
+                                }
                             }
-                        } else {  // type B: S_n(L)
-                            sg = maxl[idx] >= T;
-                            if (sg) { nc = children(g, idx, c); v[3] = nc; }
-                            else v[4] = 1;
                         }
+                        es[j] = e;
                     }
                     if (tid == 0) sh.wbase = sh.pos >> 5;
                     win_clear(sh);
                     block_scan(v, sh);
-                    if (k < ncur) {
-                        unsigned long long bp = sh.pos + v[0];
-                        if (!sg) {
-                            if (INB(sh.nstay + v[4], NN)) lis_new[sh.nstay + v[4]] = e;
-                        } else if ((e & 1) == 0) {
+                    unsigned long long bp = sh.pos + v[0];
+                    long long li = sh.nlip + v[1], ls = sh.nlsp + v[2], nn = sh.nnext + v[3], st = sh.nstay + v[4];
+#pragma unroll 1
+                    for (int j = 0; j < EPS; j++) {
+                        if (k0 + j >= ncur) break;
+                        const uint32_t e = es[j], idx = e >> 1;
+                        uint32_t c[9];
+                        if ((e & 1) == 0) {
+                            if (!(maxd[idx] >= T)) {
+                                if (INB(st, NN)) lis_new[st] = e;
+                                st++;
+                                bp++;
+                                continue;
+                            }
                             win_set(sh, bp++);
-                            long long li = sh.nlip + v[1], ls = sh.nlsp + v[2];
+                            const int nc = children(g, idx, c);
                             for (int q = 0; q < nc; q++) {
-                                if ((sigmask >> q) & 1) {
+                                if (!INB(c[q], NN)) c[q] = 0;
+                                if (absi(s[c[q]]) >= T) {
                                     win_set(sh, bp);
                                     if (s[c[q]] < 0) win_set(sh, bp + 1);
                                     sig_pos[c[q]] = (uint32_t)(bp + 1);
@@ -380,11 +416,23 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                                     bp += 1;
                                 }
                             }
-                            if (has_L(g, idx) && INB(sh.nnext + v[3], NN)) nxt[sh.nnext + v[3]] = (idx << 1) | 1;
+                            if (has_L(g, idx)) {
+                                if (INB(nn, NN)) nxt[nn] = (idx << 1) | 1;
+                                nn++;
+                            }
                         } else {
-                            win_set(sh, bp);
-                            for (int q = 0; q < nc; q++)
-                                if (INB(sh.nnext + v[3] + q, NN)) nxt[sh.nnext + v[3] + q] = c[q] << 1;
+                            if (!(maxl[idx] >= T)) {
+                                if (INB(st, NN)) lis_new[st] = e;
+                                st++;
+                                bp++;
+                                continue;
+                            }
+                            win_set(sh, bp++);
+                            const int nc = children(g, idx, c);
+                            for (int q = 0; q < nc; q++) {
+                                if (INB(nn, NN)) nxt[nn] = c[q] << 1;
+                                nn++;
+                            }
                         }
                     }
                     __syncthreads();
@@ -413,14 +461,19 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
         // ---- refinement pass over the LSP entries of earlier planes
         {
             if (tid == 0) refine_start[n] = (long long)sh.pos;
-            for (long long base = 0; base < lsp_before; base += ET) {
-                long long k = base + tid;
+            for (long long base = 0; base < lsp_before; base += (long long)ET * EPL) {
                 if (tid == 0) sh.wbase = (sh.pos + base) >> 5;
                 win_clear(sh);
                 __syncthreads();
-                if (k < lsp_before && INB(k, NN) && INB(lsp[k], NN) && ((absi(s[lsp[k]]) >> n) & 1)) win_set(sh, sh.pos + k);
+                const long long k0 = base + (long long)tid * EPL;
+#pragma unroll
+                for (int j = 0; j < EPL; j++) {
+                    const long long k = k0 + j;
+                    if (k < lsp_before && INB(k, NN) && INB(lsp[k], NN) && ((absi(s[lsp[k]]) >> n) & 1))
+                        win_set(sh, sh.pos + k);
+                }
                 __syncthreads();
-                long long end = base + ET < lsp_before ? base + ET : lsp_before;
+                const long long end = base + (long long)ET * EPL < lsp_before ? base + (long long)ET * EPL : lsp_before;
                 win_flush(sh, out32, cap_words, sh.pos + end, status);
                 __syncthreads();
             }
