@@ -100,9 +100,11 @@ struct FieldScal {
 
 struct SpihtWork {  // per-field device lists and maxima
     uint32_t *maxd, *maxl;      // N each
-    uint32_t *lip, *lsp;        // N each
-    uint32_t *lis_a, *lis_b;    // 2N each (idx << 1 | type)
-    uint32_t *tmp;              // 2N
+    uint2 *elip, *elsp;         // encoder LIP / LSP: N entries (node, value) each
+    uint2 *elis, *ewav;         // encoder LIS + next LIS, two waves: 2N entries each
+    uint32_t *lip, *lsp;        // decoder lists (sharing the encoder's memory): N each
+    uint32_t *lis_a, *lis_b;    // decoder LIS: 4N words from lis_a (idx << 1 | type)
+    uint32_t *tmp;
 };
 
 // One field of a batch as the kernels see it.  All pointers are device

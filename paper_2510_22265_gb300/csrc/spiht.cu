@@ -10,7 +10,7 @@
 // Encoder: the set maxima (max |s| over all descendants, and over descendants
 // beyond the children) come from one full-grid kernel per level, bottom up.
 // Then one CTA per field runs the bit-planes.  Each list pass is processed in
-// chunks of 1024 threads x a few consecutive entries (8 of the LIP or LSP, 4
+// chunks of 1024 threads x a few consecutive entries (8 of the LIP or LSP, 1
 // of the LIS): every thread evaluates its entries' tests, a block-wide
 // exclusive scan of (bits, LIP appends, LSP appends, next-wave appends,
 // stays) gives every thread's output positions, and the chunk's 1-bits are
@@ -137,9 +137,9 @@ __global__ void maxima_kernel(Live lv, const __grid_constant__ FieldRun one, int
 
 constexpr int ET = 1024;
 constexpr int NQ = 5;
-constexpr int EPL = 8;  // LIP and LSP entries per thread in a chunk
-constexpr int EPS = 4;  // LIS entries per thread in a chunk
-constexpr int WIN_WORDS = ET * EPS * 19 / 32 + 2;  // a LIS entry emits at most 19 bits
+constexpr int EPL = 8;  // LIP and LSP entries per thread in a chunk (the LIS takes one)
+// a chunk's bits: a LIS entry emits at most 19, a LIP entry 2, an LSP entry 1
+constexpr int WIN_WORDS = (ET * 19 > ET * EPL * 2 ? ET * 19 : ET * EPL * 2) / 32 + 2;
 
 struct EncShared {
     unsigned long long pos;
@@ -208,6 +208,13 @@ __device__ __forceinline__ void win_flush(EncShared &sh, uint32_t *out32, unsign
     }
 }
 
+// |v| with the sign in bit 31
+__device__ __forceinline__ uint32_t smag(int32_t v) { return absi(v) | (v < 0 ? 0x80000000u : 0u); }
+
+// List entries carry the value their tests read: a LIP entry (node, |s| and
+// sign), an LSP entry (node, |s|), a LIS entry (node << 1 | type, the set
+// maximum of its type).  Every pass then reads its list in order; a node's
+// value is gathered once, when the entry is made.
 __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_constant__ FieldRun one) {
     int f;
     const FieldRun *r = pick(lv, one, blockIdx.x, f);
@@ -226,11 +233,10 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
     long long *refine_start = r->sc->refine_start;
     int *status = &r->sc->spiht_status;
     const long long N = r->N;
-    uint32_t *lip = r->sw.lip, *lsp = r->sw.lsp, *lis = r->sw.lis_a, *lis_new = r->sw.lis_a + N;
-    uint32_t *wave_a = r->sw.lis_b, *wave_b = r->sw.lis_b + N;
+    uint2 *lip = r->sw.elip, *lsp = r->sw.elsp, *lis = r->sw.elis, *lis_new = r->sw.elis + N;
+    uint2 *wave_a = r->sw.ewav, *wave_b = r->sw.ewav + N;
     const int tid = threadIdx.x;
     const long long NN = (long long)g.ny * g.nx;
-    (void)NN;
     const int hL = g.h[g.L], wL = g.w[g.L];
     const long nroot = (long)hL * wL;
     // top plane from the LL roots (every coefficient is a root or below one)
@@ -258,14 +264,14 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
         uint32_t idx = 0;
         if (k < nroot) {
             idx = (uint32_t)(k / wL) * g.nx + (uint32_t)(k % wL);
-            if (INB(k, NN)) lip[k] = idx;
+            if (INB(k, NN)) lip[k] = make_uint2(idx, smag(s[idx]));
             uint32_t c[9];
             v[0] = children(g, idx, c) > 0;
         }
         block_scan(v, sh);
-        if (k < nroot && v[0] != (int)0x7FFFFFFF) {
+        if (k < nroot) {
             uint32_t c[9];
-            if (children(g, idx, c) > 0 && INB(sh.nlis + v[0], NN)) lis[sh.nlis + v[0]] = idx << 1;
+            if (children(g, idx, c) > 0 && INB(sh.nlis + v[0], NN)) lis[sh.nlis + v[0]] = make_uint2(idx << 1, maxd[idx]);
         }
         __syncthreads();
         if (tid == 0) sh.nlis += sh.tot[0];
@@ -282,16 +288,16 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
             for (long long base = 0; base < nl; base += (long long)ET * EPL) {
                 const long long k0 = base + (long long)tid * EPL;
                 int v[NQ] = {0, 0, 0, 0, 0};
-                uint32_t xs[EPL];
+                uint2 xs[EPL];
                 unsigned sgm = 0;
 #pragma unroll
                 for (int j = 0; j < EPL; j++) {
                     const long long k = k0 + j;
-                    uint32_t x = 0;
+                    uint2 x = make_uint2(0, 0);
                     if (k < nl) {
-                        x = INB(k, NN) ? lip[k] : 0;
-                        if (!INB(x, NN)) x = 0;
-                        const bool sg = absi(s[x]) >= T;
+                        if (INB(k, NN)) x = lip[k];
+                        if (!INB(x.x, NN)) x.x = 0;
+                        const bool sg = (x.y & 0x7FFFFFFFu) >= T;
                         sgm |= (unsigned)sg << j;
                         v[0] += 1 + sg; v[1] += !sg; v[2] += sg;
                     }
@@ -305,14 +311,14 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
 #pragma unroll
                 for (int j = 0; j < EPL; j++) {
                     if (k0 + j >= nl) break;
-                    const uint32_t x = xs[j];
+                    const uint2 x = xs[j];
                     if ((sgm >> j) & 1) {
                         win_set(sh, bp);
-                        if (s[x] < 0) win_set(sh, bp + 1);
+                        if (x.y >> 31) win_set(sh, bp + 1);
                         if (INB(ls, NN)) {
-                            sig_pos[x] = (uint32_t)(bp + 1);
-                            lsp_idx[x] = (uint32_t)ls;
-                            lsp[ls] = x;
+                            sig_pos[x.x] = (uint32_t)(bp + 1);
+                            lsp_idx[x.x] = (uint32_t)ls;
+                            lsp[ls] = make_uint2(x.x, x.y & 0x7FFFFFFFu);
                         }
                         ls++;
                         bp += 2;
@@ -332,106 +338,84 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
             if (tid == 0) sh.nlip = keep_n;
             __syncthreads();
         }
-        // ---- sorting pass: LIS, in waves
+        // ---- sorting pass: LIS, in waves (one entry per thread; a type-A
+        // entry's children and their values stay in registers)
         {
-            const uint32_t *cur = lis;
+            const uint2 *cur = lis;
             long long ncur = sh.nlis;
-            uint32_t *nxt = wave_a;
+            uint2 *nxt = wave_a;
             if (tid == 0) sh.nstay = 0;
             __syncthreads();
             while (ncur > 0) {
                 if (tid == 0) sh.nnext = 0;
                 __syncthreads();
-                for (long long base = 0; base < ncur; base += (long long)ET * EPS) {
-                    // EPS consecutive entries per thread: counts first, then
-                    // (after the scan) the same tests again for the outputs
-                    const long long k0 = base + (long long)tid * EPS;
+                for (long long base = 0; base < ncur; base += ET) {
+                    const long long k = base + tid;
                     int v[NQ] = {0, 0, 0, 0, 0};
-                    uint32_t es[EPS];
-#pragma unroll
-                    for (int j = 0; j < EPS; j++) {
-                        const long long k = k0 + j;
-                        uint32_t e = 0;
-                        if (k < ncur) {
-                            e = INB(k, NN) ? cur[k] : 0;
-                            if (!INB(e >> 1, NN)) e = 0;
-                            const uint32_t idx = e >> 1;
-                            v[0] += 1;
-                            if ((e & 1) == 0) {  // type A: S_n(D)
-                                if (maxd[idx] >= T) {
-                                    uint32_t c[9];
-                                    const int nc = children(g, idx, c);
-                                    for (int q = 0; q < nc; q++) {
-                                        const uint32_t cq = INB(c[q], NN) ? c[q] : 0;
-                                        const bool cs = absi(s[cq]) >= T;
-                                        v[0] += 1 + cs; v[1] += !cs; v[2] += cs;
-                                    }
-                                    v[3] += has_L(g, idx);
-                                } else {
-                                    v[4] += 1;
+                    uint2 e = make_uint2(0, 0);
+                    uint32_t c[9];
+                    int32_t sv[9];
+                    int nc = 0;
+                    bool sg = false;
+                    uint32_t sigmask = 0;
+                    if (k < ncur) {
+                        if (INB(k, NN)) e = cur[k];
+                        if (!INB(e.x >> 1, NN)) e.x = 0;
+                        const uint32_t idx = e.x >> 1;
+                        v[0] = 1;
+                        sg = e.y >= T;
+                        if ((e.x & 1) == 0) {  // type A: S_n(D)
+                            if (sg) {
+                                nc = children(g, idx, c);
+                                for (int q = 0; q < nc; q++) {
+                                    if (!INB(c[q], NN)) c[q] = 0;
+                                    sv[q] = s[c[q]];
+                                    const bool cs = absi(sv[q]) >= T;
+                                    sigmask |= (uint32_t)cs << q;
+                                    v[0] += 1 + cs; v[1] += !cs; v[2] += cs;
                                 }
-                            } else {  // type B: S_n(L)
-                                if (maxl[idx] >= T) {
-                                    uint32_t c[9];
-                                    v[3] += children(g, idx, c);
-                                } else {
-                                    v[4] += 1;
-                                }
+                                v[3] = has_L(g, idx);
+                            } else {
+                                v[4] = 1;
                             }
+                        } else {  // type B: S_n(L)
+                            if (sg) { nc = children(g, idx, c); v[3] = nc; }
+                            else v[4] = 1;
                         }
-                        es[j] = e;
                     }
                     if (tid == 0) sh.wbase = sh.pos >> 5;
                     win_clear(sh);
                     block_scan(v, sh);
-                    unsigned long long bp = sh.pos + v[0];
-                    long long li = sh.nlip + v[1], ls = sh.nlsp + v[2], nn = sh.nnext + v[3], st = sh.nstay + v[4];
-#pragma unroll 1
-                    for (int j = 0; j < EPS; j++) {
-                        if (k0 + j >= ncur) break;
-                        const uint32_t e = es[j], idx = e >> 1;
-                        uint32_t c[9];
-                        if ((e & 1) == 0) {
-                            if (!(maxd[idx] >= T)) {
-                                if (INB(st, NN)) lis_new[st] = e;
-                                st++;
-                                bp++;
-                                continue;
-                            }
+                    if (k < ncur) {
+                        const uint32_t idx = e.x >> 1;
+                        unsigned long long bp = sh.pos + v[0];
+                        if (!sg) {
+                            if (INB(sh.nstay + v[4], NN)) lis_new[sh.nstay + v[4]] = e;
+                        } else if ((e.x & 1) == 0) {
                             win_set(sh, bp++);
-                            const int nc = children(g, idx, c);
+                            long long li = sh.nlip + v[1], ls = sh.nlsp + v[2];
                             for (int q = 0; q < nc; q++) {
-                                if (!INB(c[q], NN)) c[q] = 0;
-                                if (absi(s[c[q]]) >= T) {
+                                if ((sigmask >> q) & 1) {
                                     win_set(sh, bp);
-                                    if (s[c[q]] < 0) win_set(sh, bp + 1);
+                                    if (sv[q] < 0) win_set(sh, bp + 1);
                                     sig_pos[c[q]] = (uint32_t)(bp + 1);
                                     lsp_idx[c[q]] = (uint32_t)ls;
-                                    if (INB(ls, NN)) lsp[ls] = c[q];
+                                    if (INB(ls, NN)) lsp[ls] = make_uint2(c[q], absi(sv[q]));
                                     ls++;
                                     bp += 2;
                                 } else {
-                                    if (INB(li, NN)) lip[li] = c[q];
+                                    if (INB(li, NN)) lip[li] = make_uint2(c[q], smag(sv[q]));
                                     li++;
                                     bp += 1;
                                 }
                             }
-                            if (has_L(g, idx)) {
-                                if (INB(nn, NN)) nxt[nn] = (idx << 1) | 1;
-                                nn++;
-                            }
+                            if (has_L(g, idx) && INB(sh.nnext + v[3], NN))
+                                nxt[sh.nnext + v[3]] = make_uint2((idx << 1) | 1, maxl[idx]);
                         } else {
-                            if (!(maxl[idx] >= T)) {
-                                if (INB(st, NN)) lis_new[st] = e;
-                                st++;
-                                bp++;
-                                continue;
-                            }
-                            win_set(sh, bp++);
-                            const int nc = children(g, idx, c);
+                            win_set(sh, bp);
                             for (int q = 0; q < nc; q++) {
-                                if (INB(nn, NN)) nxt[nn] = c[q] << 1;
-                                nn++;
+                                const uint32_t cq = INB(c[q], NN) ? c[q] : 0;
+                                if (INB(sh.nnext + v[3] + q, NN)) nxt[sh.nnext + v[3] + q] = make_uint2(c[q] << 1, maxd[cq]);
                             }
                         }
                     }
@@ -469,8 +453,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
 #pragma unroll
                 for (int j = 0; j < EPL; j++) {
                     const long long k = k0 + j;
-                    if (k < lsp_before && INB(k, NN) && INB(lsp[k], NN) && ((absi(s[lsp[k]]) >> n) & 1))
-                        win_set(sh, sh.pos + k);
+                    if (k < lsp_before && INB(k, NN) && ((lsp[k].y >> n) & 1)) win_set(sh, sh.pos + k);
                 }
                 __syncthreads();
                 const long long end = base + (long long)ET * EPL < lsp_before ? base + (long long)ET * EPL : lsp_before;
@@ -634,16 +617,23 @@ unsigned pg(long long maxN, int nslots) {
 
 }  // namespace
 
-size_t spiht_work_bytes(size_t n) { return (size_t)4 * n * (2 + 2 + 4) + 256; }
+size_t spiht_work_bytes(size_t n) { return (size_t)4 * n * (2 + 12) + 256; }
 
+// maxd, maxl (n words each), then the encoder's lists of (word, word) entries:
+// LIP (n), LSP (n), LIS + next LIS (2n), two waves (2n); the decoder's
+// one-word lists share that memory
 void spiht_work_carve(uint8_t *base, size_t n, SpihtWork *w) {
     uint32_t *p = (uint32_t *)(((uintptr_t)base + 255) & ~(uintptr_t)255);
     w->maxd = p; p += n;
     w->maxl = p; p += n;
-    w->lip = p; p += n;
-    w->lsp = p; p += n;
-    w->lis_a = p; p += 2 * n;  // lis (n) + lis_new (n)
-    w->lis_b = p; p += 2 * n;  // wave_a (n) + wave_b (n)
+    w->elip = (uint2 *)p;
+    w->elsp = (uint2 *)(p + 2 * n);
+    w->elis = (uint2 *)(p + 4 * n);
+    w->ewav = (uint2 *)(p + 8 * n);
+    w->lip = p;
+    w->lsp = p + 2 * n;
+    w->lis_a = p + 4 * n;  // the decoder's LIS: 4n words
+    w->lis_b = p + 8 * n;
     w->tmp = w->lis_a;
 }
 
