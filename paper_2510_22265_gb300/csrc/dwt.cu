@@ -198,11 +198,15 @@ __global__ void __launch_bounds__(IT, 12) inv_level(Live lv, const __grid_consta
     const int ty0 = blockIdx.z * TY, tx0 = blockIdx.y * TX;
     if (ty0 >= hp || tx0 >= wp) return;
     const int tid = threadIdx.x;
-    if (MODE == 1) {  // base-loop count: nothing left to decide once enough points fail
+    if (MODE == 1 || MODE == 2) {  // counts: nothing left to decide once enough points fail
         __shared__ int quit;
         if (tid == 0) {
-            const unsigned long long thr = r->sc->fail_thr;
-            quit = thr != 0 && *(volatile unsigned long long *)&r->sc->fail >= thr;
+            if (MODE == 1) {
+                const unsigned long long thr = r->sc->fail_thr;
+                quit = thr != 0 && *(volatile unsigned long long *)&r->sc->fail >= thr;
+            } else {
+                quit = *(volatile unsigned long long *)&r->sc->cnt[fin.counter] != 0;
+            }
         }
         __syncthreads();
         if (quit) return;

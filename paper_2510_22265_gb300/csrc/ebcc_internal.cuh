@@ -261,8 +261,10 @@ void batch_dims_init(BatchDims &d);
 // ------------------------------------------------------------ DWT
 struct InvFinal {
     // -1: store into plane `dst`; 0: store (+ Abase if add_base) into `dst`;
-    // 1: count points whose value lies inside bounds[i]; 2: count points with
-    // Abase + value outside bounds[i]; 3: store mn + (value (+ Abase)) * range
+    // 1: count points whose value lies inside bounds[i] (tiles are skipped once
+    // sc->fail reaches a nonzero sc->fail_thr); 2: count points with Abase +
+    // value outside bounds[i] (tiles are skipped once the count is nonzero:
+    // only count > 0 is meaningful); 3: store mn + (value (+ Abase)) * range
     // (original units) into `dst`.  Counts add to sc->cnt[counter].
     int mode, add_base, dst, counter;
 };
