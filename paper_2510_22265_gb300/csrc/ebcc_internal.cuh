@@ -394,7 +394,10 @@ int spiht_prefix_recon_b(const Live &lv, const FieldRun &one, int nslots, long l
 size_t spiht_work_bytes(size_t n);
 void spiht_work_carve(uint8_t *base, size_t n, SpihtWork *w);
 // encode s -> sp (sc->nbits, nmax, spiht_status, refine_start; sig_pos, lsp_idx)
-int spiht_encode_b(const Live &lv, const FieldRun &one, int nslots, const BatchDims &d, cudaStream_t st);
+// full_trace: also mark never-significant coefficients in sig_pos / lsp_idx
+// (0xFFFFFFFF); otherwise only the entries of coefficients with s != 0 are set
+int spiht_encode_b(const Live &lv, const FieldRun &one, int nslots, const BatchDims &d, int full_trace,
+                   cudaStream_t st);
 // decode in[HDR + base_len ..] (res_len bytes) with sc->nmax, sc->es -> R
 // (coef) when to_coef, else mag (qt) / plane8 / neg8
 int spiht_decode_b(const Live &lv, const FieldRun &one, int nslots, long long maxN, int to_coef, cudaStream_t st);

@@ -1262,7 +1262,7 @@ int compress_batch(Engine &e, const ebcc_field_desc *fd, int n, ebcc_out_desc *o
             PROF("set_scalars", st, 0.0, set_scalars<<<(ns + 255) / 256, 256, 0, st>>>(lv, b.es, 1));
             CK(cudaGetLastError());
             RC(spiht_quantise_b(lv, kNone, ns, b.dims.maxN, st));
-            RC(spiht_encode_b(lv, kNone, ns, b.dims, st));
+            RC(spiht_encode_b(lv, kNone, ns, b.dims, 0, st));
             STAGE(st, "spiht encode");
             RC(spiht_prefix_recon_b(lv, kNone, ns, b.dims.maxN, 0, st));
             RC(dwt_inverse_b(lv, kNone, ns, b.dims, PL_R, InvFinal{2, 0, 0, 1}, st));

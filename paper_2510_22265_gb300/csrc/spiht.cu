@@ -115,6 +115,7 @@ __global__ void maxima_kernel(Live lv, const __grid_constant__ FieldRun one, int
         else band_box(g, l, k + 1, y0s[k], x0s[k], bhs[k], bws[k]);
         cnt[k + 1] = cnt[k] + (long)bhs[k] * bws[k];
     }
+    const bool leaf_children = (l == 0 ? g.L : l - 1) <= 1;
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < cnt[nb]; t += (long)gridDim.x * blockDim.x) {
         int k = t < cnt[1] ? 0 : (t < cnt[2] ? 1 : 2);
         long r = t - cnt[k];
@@ -125,7 +126,7 @@ __global__ void maxima_kernel(Live lv, const __grid_constant__ FieldRun one, int
         uint32_t md = 0, ml = 0;
         for (int q = 0; q < n; q++) {
             if (!INB(c[q], (long long)g.ny * g.nx)) continue;
-            uint32_t cd = maxd[c[q]];
+            uint32_t cd = leaf_children ? 0u : maxd[c[q]];  // level-1 nodes have no descendants
             md = max(md, max(absi(s[c[q]]), cd));
             ml = max(ml, cd);
         }
@@ -196,15 +197,22 @@ __device__ __forceinline__ void win_clear(EncShared &sh) {
 __device__ __forceinline__ void win_set(EncShared &sh, unsigned long long b) {
     if (INB((long long)(b >> 5) - (long long)sh.wbase, WIN_WORDS)) atomicOr(&sh.win[(b >> 5) - sh.wbase], bitmask(b));
 }
+// The chunk's bits are [start_bit, end_bit).  When start_bit is not on a word
+// boundary the window's first word also holds bits of the chunk before (the
+// chunk's are OR-ed in); every other word is the chunk's alone and is stored
+// whole, zeros included, so the stream needs no clearing beforehand
 __device__ __forceinline__ void win_flush(EncShared &sh, uint32_t *out32, unsigned long long cap_words,
-                                          unsigned long long end_bit, int *status) {
-    unsigned long long nw = ((end_bit + 31) >> 5) - sh.wbase;
+                                          unsigned long long start_bit, unsigned long long end_bit, int *status) {
+    const unsigned long long nw = ((end_bit + 31) >> 5) - sh.wbase;
+    const bool shared_first = (start_bit & 31) != 0;
     for (unsigned long long k = threadIdx.x; k < nw && k < WIN_WORDS; k += ET) {
-        uint32_t v = sh.win[k];
-        if (!v) continue;
-        unsigned long long gw = sh.wbase + k;
-        if (gw < cap_words) atomicOr(&out32[gw], v);
-        else atomicOr(status, 1);
+        const uint32_t v = sh.win[k];
+        const unsigned long long gw = sh.wbase + k;
+        const bool merge = k == 0 && shared_first;
+        if (merge && !v) continue;
+        if (gw >= cap_words) atomicOr(status, 1);
+        else if (merge) atomicOr(&out32[gw], v);
+        else out32[gw] = v;
     }
 }
 
@@ -221,6 +229,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
     if (!r) return;
     __shared__ EncShared sh;
     __shared__ SG g;
+    if (threadIdx.x == 0) r->sc->spiht_status = 0;  // before the barrier in load_sg
     load_sg(g, *r);
     const int32_t *__restrict__ s = r->s;
     const uint32_t *__restrict__ maxd = r->sw.maxd;
@@ -243,7 +252,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
     uint32_t mx = 0;
     for (long k = tid; k < nroot; k += ET) {
         uint32_t idx = (uint32_t)(k / wL) * g.nx + (uint32_t)(k % wL);
-        mx = max(mx, max(absi(s[idx]), maxd[idx]));
+        mx = max(mx, max(absi(s[idx]), g.L >= 1 ? maxd[idx] : 0u));
     }
     for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((tid & 31) == 0) sh.nmax_red[tid >> 5] = (int)mx;
@@ -329,7 +338,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                     }
                 }
                 __syncthreads();
-                win_flush(sh, out32, cap_words, sh.pos + sh.tot[0], status);
+                win_flush(sh, out32, cap_words, sh.pos, sh.pos + sh.tot[0], status);
                 keep_n += sh.tot[1];
                 __syncthreads();
                 if (tid == 0) { sh.pos += sh.tot[0]; sh.nlsp += sh.tot[2]; }
@@ -420,7 +429,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                         }
                     }
                     __syncthreads();
-                    win_flush(sh, out32, cap_words, sh.pos + sh.tot[0], status);
+                    win_flush(sh, out32, cap_words, sh.pos, sh.pos + sh.tot[0], status);
                     __syncthreads();
                     if (tid == 0) {
                         sh.pos += sh.tot[0]; sh.nlip += sh.tot[1]; sh.nlsp += sh.tot[2];
@@ -457,7 +466,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                 }
                 __syncthreads();
                 const long long end = base + (long long)ET * EPL < lsp_before ? base + (long long)ET * EPL : lsp_before;
-                win_flush(sh, out32, cap_words, sh.pos + end, status);
+                win_flush(sh, out32, cap_words, sh.pos + base, sh.pos + end, status);
                 __syncthreads();
             }
             if (tid == 0) sh.pos += lsp_before;
@@ -589,23 +598,18 @@ __global__ void dequant_kernel(Live lv, const __grid_constant__ FieldRun one) {
 }
 
 // encoder: zero maxima, stream and plane table; no sign positions yet
+// the trace of never-significant coefficients (0xFFFFFFFF), for callers that
+// read it for every coefficient; the compressor's prefix reconstruction reads
+// it only where s != 0, which the encoder always writes
 __global__ void enc_reset_kernel(Live lv, const __grid_constant__ FieldRun one) {
     int f;
     const FieldRun *r = pick(lv, one, blockIdx.y, f);
     if (!r) return;
     const long long n = r->N;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        r->sw.maxd[i] = 0;
-        r->sw.maxl[i] = 0;
         r->sig_pos[i] = 0xFFFFFFFFu;
         r->lsp_idx[i] = 0xFFFFFFFFu;
     }
-    uint32_t *o = (uint32_t *)r->sp;
-    const long long nw = r->sp_cap / 4;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nw; i += (long long)gridDim.x * blockDim.x)
-        o[i] = 0;
-    if (blockIdx.x == 0 && threadIdx.x < 32) r->sc->refine_start[threadIdx.x] = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) r->sc->spiht_status = 0;
 }
 
 unsigned pg(long long maxN, int nslots) {
@@ -637,11 +641,14 @@ void spiht_work_carve(uint8_t *base, size_t n, SpihtWork *w) {
     w->tmp = w->lis_a;
 }
 
-int spiht_encode_b(const Live &lv, const FieldRun &one, int nslots, const BatchDims &d, cudaStream_t st) {
+int spiht_encode_b(const Live &lv, const FieldRun &one, int nslots, const BatchDims &d, int full_trace,
+                   cudaStream_t st) {
     if (nslots <= 0) return EBCC_OK;
     if (d.maxN >= 0x7FFFFFFFLL) return EBCC_EINVAL;
-    PROF("enc_reset_kernel", st, 0.0, enc_reset_kernel<<<dim3(pg(d.maxN, nslots), nslots), 256, 0, st>>>(lv, one));
-    CK(cudaGetLastError());
+    if (full_trace) {
+        PROF("enc_reset_kernel", st, 0.0, enc_reset_kernel<<<dim3(pg(d.maxN, nslots), nslots), 256, 0, st>>>(lv, one));
+        CK(cudaGetLastError());
+    }
     for (int l = 2; l <= d.maxL; l++) {
         long long nb = 3LL * d.h[l] * d.w[l];
         unsigned gx = pg(nb, nslots);

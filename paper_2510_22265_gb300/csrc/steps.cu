@@ -204,7 +204,7 @@ int ebcc_spiht_encode_dev(const int32_t *s, size_t ny, size_t nx, int levels, ui
     BatchDims d;
     batch_dims_init(d);
     batch_dims_add(d, (int)ny, (int)nx, L, 0);
-    RC(spiht_encode_b(kSingle, one, 1, d, st));
+    RC(spiht_encode_b(kSingle, one, 1, d, 1, st));
     FieldScal h;
     CK(cudaMemcpyAsync(&h, sc, sizeof(h), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
