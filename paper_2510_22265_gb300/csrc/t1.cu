@@ -693,12 +693,19 @@ constexpr int MQT = 128;
 // otherwise the interval update is a select (T.800 C.2: the conditional
 // exchange swaps which sub-interval is coded, the state transition depends
 // only on MPS / LPS) and one renormalisation
-__device__ __forceinline__ void mq_encode_t(MQEnc &e, uint8_t *I, uint8_t *M, const uint32_t *mq, const uint8_t *sw,
-                                            int cx, int d) {
-    const int i = I[cx];
-    const uint32_t ent = mq[i], qe = ent & 0xFFFF;
+// One context's whole state in one word: Qe | NMPS << 16 | NLPS << 22 |
+// SWITCH << 28 of its current index, MPS in bit 31, so a symbol reads one
+// word; the fast MPS path (no renormalisation) leaves it unchanged
+__device__ __forceinline__ uint32_t mq_word(uint32_t tab) {
+    return (tab & 0xFFFFu) | (((tab >> 16) & 63u) << 16) | ((tab >> 24) << 22);
+}
+
+__device__ __forceinline__ void mq_encode_w(MQEnc &e, uint32_t *ctx, const uint32_t *stab, int cx, int d) {
+    const uint32_t ent = ctx[cx];
+    const uint32_t qe = ent & 0xFFFFu;
     const uint32_t A = e.A - qe;
-    const bool mps = d == M[cx];
+    const uint32_t mpsb = ent >> 31;
+    const bool mps = (uint32_t)d == mpsb;
     if (mps && (A & 0x8000)) {
         e.A = A;
         e.C += qe;
@@ -706,32 +713,36 @@ __device__ __forceinline__ void mq_encode_t(MQEnc &e, uint8_t *I, uint8_t *M, co
     }
     const bool small = A < qe;
     if (mps != small) { e.A = A; e.C += qe; } else { e.A = qe; }
-    I[cx] = (uint8_t)(mps ? ((ent >> 16) & 0xFF) : (ent >> 24));
-    if (!mps && sw[i]) M[cx] ^= 1;
+    const uint32_t ni = mps ? (ent >> 16) & 63u : (ent >> 22) & 63u;
+    const uint32_t nm = mpsb ^ (uint32_t)(!mps && ((ent >> 28) & 1u));
+    ctx[cx] = stab[ni] | (nm << 31);
     e.renorm();
 }
 
 __global__ void __launch_bounds__(MQT) t1_mq_kernel(int nblk, T1Out o) {
-    __shared__ uint32_t smq[48];
-    __shared__ uint8_t ssw[48];
-    __shared__ uint8_t ctx[MQT][44];  // 11 words per thread: no bank conflicts
-    for (int k = threadIdx.x; k < 47; k += blockDim.x) { smq[k] = c_mq[k]; ssw[k] = c_mqsw[k]; }
+    __shared__ uint32_t stab[48];
+    __shared__ uint32_t ctxw[MQT][19];  // 19 words per thread (odd stride: no bank conflicts)
+    for (int k = threadIdx.x; k < 47; k += blockDim.x) stab[k] = mq_word(c_mq[k]) | ((uint32_t)(c_mqsw[k] & 1) << 28);
     __syncthreads();
     const int b = blockIdx.x * MQT + threadIdx.x;
     if (b >= nblk) return;
     const int np = o.npass[b];
     if (np <= 0) return;
-    uint8_t *I = ctx[threadIdx.x], *M = I + 20;
-    reset_ctx(I, M);
+    uint32_t *ctx = ctxw[threadIdx.x];
+    for (int k = 0; k < 19; k++) ctx[k] = stab[k == 0 ? 4 : (k == 17 ? 3 : (k == 18 ? 46 : 0))];
     MQEnc e;
     e.init(o.bytes + (size_t)b * o.cap, o.cap);
     // one loop over all the block's symbols; a pass end is recorded when the
-    // symbol count reaches it, so lanes are not held together pass by pass
-    const uint8_t *sym = o.sym + (size_t)b * o.sym_cap;
+    // symbol count reaches it, so lanes are not held together pass by pass.
+    // Symbols are read 16 at a time, the next 16 already in flight (the
+    // buffer of a block starts on a 16-byte boundary, sym_cap % 16 == 0)
+    const uint4 *sym4 = (const uint4 *)(o.sym + (size_t)b * o.sym_cap);
     const size_t pb = (size_t)b * o.maxpass;
     const int npp = np < o.maxpass ? np : o.maxpass;
     int total = o.pass_sym[pb + npp - 1];
     if (total > o.sym_cap) total = (int)o.sym_cap;
+    uint4 cur = total > 0 ? sym4[0] : make_uint4(0, 0, 0, 0);
+    uint4 nxt = total > 16 ? sym4[1] : make_uint4(0, 0, 0, 0);
     int pass = 0;
     int end = o.pass_sym[pb];
     for (int k = 0;; k++) {
@@ -745,8 +756,14 @@ __global__ void __launch_bounds__(MQT) t1_mq_kernel(int nblk, T1Out o) {
             if (pass < npp) end = o.pass_sym[pb + pass];
         }
         if (k >= total) break;
-        const int sy = sym[k];
-        mq_encode_t(e, I, M, smq, ssw, sy >> 1, sy & 1);
+        if ((k & 15) == 0 && k > 0) {
+            cur = nxt;
+            if (k + 16 < total) nxt = sym4[(k >> 4) + 1];
+        }
+        const int q = (k >> 2) & 3;
+        const uint32_t wd = q == 0 ? cur.x : (q == 1 ? cur.y : (q == 2 ? cur.z : cur.w));
+        const int sy = (int)((wd >> ((k & 3) * 8)) & 0xFFu);
+        mq_encode_w(e, ctx, stab, sy >> 1, sy & 1);
     }
     if (e.overflow) atomicOr(o.status, 1);
 }
