@@ -296,7 +296,11 @@ struct T1Out {
     uint8_t *sym;
     long long sym_cap;
     int32_t *pass_sym;   // nblk * maxpass
+    // scratch (nblk + MQ_ORDER_BINS + 1 entries, optional): the blocks ordered
+    // by symbol count, so each warp of MQ coders gets blocks of like length
+    int32_t *order;
 };
+constexpr int MQ_ORDER_BINS = 1024;
 // symbol capacity per coefficient of a block: per bit-plane at most 1.5
 // symbols per coefficient (a run-length hit at the first row costs three for
 // one coefficient), planes K <= 26, plus one sign per coefficient

@@ -800,6 +800,7 @@ void layout_compress(Arena &a, Batch &b, const std::vector<int> &ny, const std::
     b.t1.sym = nullptr;
     b.t1.sym_cap = 0;
     b.t1.pass_sym = nullptr;
+    b.t1.order = carve<int32_t>(a, nb + MQ_ORDER_BINS + 1);
     if (cw <= 32 && ch <= 32) {  // the split (model, then MQ) coder
         b.t1.sym_cap = ((long long)SYM_PER_COEF * cw * ch + 15) / 16 * 16;  // whole 16-byte chunks per block
         b.t1.sym = carve<uint8_t>(a, nb * b.t1.sym_cap);

@@ -107,11 +107,12 @@ int ebcc_t1_encode_dev(const int32_t *q, const int32_t *orient, int nblk, int w,
     RC(t.get(&status, 4));
     if (nblk) CK(cudaMemcpy(dbd, bd.data(), nblk * sizeof(BlockDesc), cudaMemcpyHostToDevice));
     CK(cudaMemset(status, 0, 4));
-    T1Out o{bytes, cap, maxpass, K, npass, pass_len, tail, tail_len, dD, D0, status, nullptr, 0, nullptr};
+    T1Out o{bytes, cap, maxpass, K, npass, pass_len, tail, tail_len, dD, D0, status, nullptr, 0, nullptr, nullptr};
     if (w <= 32 && h <= 32) {  // the split (model, then MQ) coder
         o.sym_cap = ((long long)SYM_PER_COEF * w * h + 15) / 16 * 16;  // whole 16-byte chunks per block
         RC(t.get(&o.sym, (size_t)(nblk + 1) * o.sym_cap));
         RC(t.get(&o.pass_sym, (size_t)(nblk + 1) * maxpass));
+        RC(t.get(&o.order, (size_t)nblk + MQ_ORDER_BINS + 1));
     }
     RC(t1_encode_blocks(const_cast<int32_t *>(q), dbd, nblk, w, h, o, 0, spp, (long long)nblk * w * h, st));
     int hs = 0;

@@ -719,13 +719,64 @@ __device__ __forceinline__ void mq_encode_w(MQEnc &e, uint32_t *ctx, const uint3
     e.renorm();
 }
 
+// ---- order of the blocks for the MQ coders: counting sort by symbol count
+// (bins of 32 symbols); the order within a bin does not matter, each block's
+// code is its own
+__device__ __forceinline__ int mq_bin(const T1Out &o, int b) {
+    const int np = o.npass[b];
+    if (np <= 0) return 0;
+    const int npp = np < o.maxpass ? np : o.maxpass;
+    const int t = o.pass_sym[(size_t)b * o.maxpass + npp - 1] >> 5;
+    return t < MQ_ORDER_BINS - 1 ? t : MQ_ORDER_BINS - 1;
+}
+
+__global__ void mq_order_count(int nblk, T1Out o) {
+    int *hist = o.order + nblk;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x)
+        atomicAdd(&hist[MQ_ORDER_BINS - 1 - mq_bin(o, b)], 1);  // longest first
+}
+
+__global__ void __launch_bounds__(MQ_ORDER_BINS) mq_order_scan(int nblk, T1Out o) {
+    __shared__ int ws[MQ_ORDER_BINS / 32];
+    int *hist = o.order + nblk;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int v = hist[t];
+    int x = v;
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) ws[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int z = ws[lane];
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, z, d);
+            if (lane >= d) z += y;
+        }
+        ws[lane] = z;
+    }
+    __syncthreads();
+    hist[t] = x - v + (wid ? ws[wid - 1] : 0);  // exclusive offsets
+}
+
+__global__ void mq_order_place(int nblk, T1Out o) {
+    int *hist = o.order + nblk;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
+        const int at = atomicAdd(&hist[MQ_ORDER_BINS - 1 - mq_bin(o, b)], 1);
+        if (at < nblk) o.order[at] = b;
+    }
+}
+
 __global__ void __launch_bounds__(MQT) t1_mq_kernel(int nblk, T1Out o) {
     __shared__ uint32_t stab[48];
     __shared__ uint32_t ctxw[MQT][19];  // 19 words per thread (odd stride: no bank conflicts)
     for (int k = threadIdx.x; k < 47; k += blockDim.x) stab[k] = mq_word(c_mq[k]) | ((uint32_t)(c_mqsw[k] & 1) << 28);
     __syncthreads();
-    const int b = blockIdx.x * MQT + threadIdx.x;
-    if (b >= nblk) return;
+    const int slot = blockIdx.x * MQT + threadIdx.x;
+    if (slot >= nblk) return;
+    const int b = o.order ? o.order[slot] : slot;
+    if (b < 0 || b >= nblk) return;
     const int np = o.npass[b];
     if (np <= 0) return;
     uint32_t *ctx = ctxw[threadIdx.x];
@@ -1012,6 +1063,14 @@ int t1_encode_blocks(int32_t *qt, const BlockDesc *blk, int nblk, int maxw, int 
         const int g = (nblk + PW - 1) / PW;
         PROF("t1_model_warp", st, 0.0, t1_model_warp<<<g < 152 * 64 ? g : 152 * 64, PW * 32, 0, st>>>(qt, blk, nblk, o, mark_spp_in_q, spp_out, nq));
         CK(cudaGetLastError());
+        if (o.order) {
+            CK(cudaMemsetAsync(o.order + nblk, 0, sizeof(int32_t) * MQ_ORDER_BINS, st));
+            const unsigned g = (unsigned)((nblk + 255) / 256 < 1216 ? (nblk + 255) / 256 : 1216);
+            PROF("mq_order", st, 0.0, mq_order_count<<<g, 256, 0, st>>>(nblk, o));
+            PROF("mq_order", st, 0.0, mq_order_scan<<<1, MQ_ORDER_BINS, 0, st>>>(nblk, o));
+            PROF("mq_order", st, 0.0, mq_order_place<<<g, 256, 0, st>>>(nblk, o));
+            CK(cudaGetLastError());
+        }
         PROF("t1_mq_kernel", st, 0.0, t1_mq_kernel<<<(nblk + MQT - 1) / MQT, MQT, 0, st>>>(nblk, o));
         CK(cudaGetLastError());
         return EBCC_OK;
