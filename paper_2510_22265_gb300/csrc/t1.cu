@@ -458,8 +458,40 @@ struct SymBuf {  // up to 16 symbols of one column in one stripe, byte k = (ctx 
     }
 };
 
+// A warp's symbols pass through a shared-memory stage on their way to the
+// block's symbol buffer: each lane ORs its stripe run (at most 16 bytes) into
+// the stage as words, and the stage goes out in whole 16-byte chunks
+// (coalesced vector stores). st[0] holds the symbol at position sbase (a
+// multiple of 16) of the block's buffer; stage words past the staged symbols
+// are zero.
+constexpr int SYM_STAGE = 2048;
+struct SymStage {
+    uint32_t *st;
+    int sbase;
+};
+
+// write out the staged symbols below position base: the whole 16-byte chunks
+// (all of them, the last one padded, when fin), keeping the partial chunk;
+// the words written out are cleared again
+__device__ __forceinline__ void stage_flush(uint8_t *buf, int cap, int base, SymStage &sg, int lane, bool fin) {
+    __syncwarp();
+    const int n = base - sg.sbase;
+    const int full = fin ? (n + 15) & ~15 : n & ~15;
+    for (int c = lane * 16; c < full; c += 32 * 16)
+        if (sg.sbase + c + 16 <= cap) *(uint4 *)(buf + sg.sbase + c) = *(const uint4 *)(sg.st + c / 4);
+    const int tw = fin ? 0 : (n - full + 3) >> 2;  // words of the kept partial chunk (at most 4)
+    const uint32_t keep = lane < tw ? sg.st[full / 4 + lane] : 0u;
+    __syncwarp();
+    for (int q = lane; q < ((n + 3) >> 2); q += 32) sg.st[q] = 0u;
+    __syncwarp();
+    if (lane < tw) sg.st[lane] = keep;
+    if (!fin) sg.sbase += full;
+    __syncwarp();
+}
+
 // place every lane's symbols of a stripe in scan order (lane = column)
-__device__ __forceinline__ void emit(uint8_t *buf, int cap, int &base, const SymBuf &sb, int lane, int32_t *status) {
+__device__ __forceinline__ void emit(uint8_t *buf, int cap, int &base, const SymBuf &sb, int lane, int32_t *status,
+                                     SymStage &sg) {
     int incl = sb.n;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -467,10 +499,25 @@ __device__ __forceinline__ void emit(uint8_t *buf, int cap, int &base, const Sym
         if (lane >= o) incl += y;
     }
     const int tot = __shfl_sync(0xffffffffu, incl, 31);
+    if (base + tot - sg.sbase > SYM_STAGE) stage_flush(buf, cap, base, sg, lane, false);
     const int at = base + incl - sb.n;
-    for (int k = 0; k < sb.n; k++) {
-        if (at + k < cap) buf[at + k] = (uint8_t)((k < 8 ? sb.lo >> (8 * k) : sb.hi >> (8 * (k - 8))) & 0xFF);
-        else atomicOr(status, 1);
+    if (at + sb.n > cap) atomicOr(status, 1);
+    if (sb.n) {
+        const int off = at - sg.sbase, w0 = off >> 2, sh = (off & 3) * 8;
+        const uint32_t x0 = (uint32_t)sb.lo, x1 = (uint32_t)(sb.lo >> 32), x2 = (uint32_t)sb.hi,
+                       x3 = (uint32_t)(sb.hi >> 32);
+        const uint32_t v0 = x0 << sh;
+        const uint32_t v1 = sh ? (x1 << sh) | (x0 >> (32 - sh)) : x1;
+        const uint32_t v2 = sh ? (x2 << sh) | (x1 >> (32 - sh)) : x2;
+        const uint32_t v3 = sh ? (x3 << sh) | (x2 >> (32 - sh)) : x3;
+        const uint32_t v4 = sh ? x3 >> (32 - sh) : 0u;
+        const int nw = ((off + sb.n + 3) >> 2) - w0;
+        uint32_t *d = sg.st + w0;
+        if (v0) atomicOr(d, v0);
+        if (nw > 1 && v1) atomicOr(d + 1, v1);
+        if (nw > 2 && v2) atomicOr(d + 2, v2);
+        if (nw > 3 && v3) atomicOr(d + 3, v3);
+        if (nw > 4 && v4) atomicOr(d + 4, v4);
     }
     base += tot;
 }
@@ -485,8 +532,10 @@ __global__ void __launch_bounds__(PW * 32, 7) t1_model_warp(int32_t *qt, const B
                                                          int mark_spp_in_q, uint8_t *spp_out, long long nq) {
     __shared__ PWShared tb;
     __shared__ uint32_t smag[PW][32][33];  // each warp's block, column-major by lane (for distortion sums)
+    __shared__ __align__(16) uint32_t stage[PW][SYM_STAGE / 4];
     for (int k = threadIdx.x; k < 4 * 256; k += blockDim.x) tb.sig[k >> 8][k & 255] = c_sigctx[k >> 8][k & 255];
     for (int k = threadIdx.x; k < 256; k += blockDim.x) tb.sgn[k] = c_signctx[k];
+    for (int k = threadIdx.x; k < PW * SYM_STAGE / 4; k += blockDim.x) (&stage[0][0])[k] = 0u;
     __syncthreads();
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t(*mg)[33] = smag[wid];
@@ -541,6 +590,7 @@ __global__ void __launch_bounds__(PW * 32, 7) t1_model_warp(int32_t *qt, const B
             uint8_t *buf = o.sym + (size_t)b * o.sym_cap;
             const int cap = (int)o.sym_cap;
             int pass = 0, base = 0;
+            SymStage sg{stage[wid], 0};
             const size_t pb = (size_t)b * o.maxpass;
             // record the pass's end in the symbol stream and its distortion decrease
             auto code_pass = [&](int64_t dd) {
@@ -595,7 +645,7 @@ __global__ void __launch_bounds__(PW * 32, 7) t1_model_warp(int32_t *qt, const B
                             sb.put(sigt[v.pat(r)], bit);
                             if (bit) sign_sym(sb, v, r);
                         }
-                        emit(buf, cap, base, sb, lane, o.status);
+                        emit(buf, cap, base, sb, lane, o.status, sg);
                     }
                     code_pass(dd);
                     SPPF |= N;
@@ -618,7 +668,7 @@ __global__ void __launch_bounds__(PW * 32, 7) t1_model_warp(int32_t *qt, const B
                             const int cx = ((REF >> r) & 1) ? 16 : (((anyn >> r) & 1) ? 15 : 14);
                             sb.put(cx, (int)((B >> r) & 1));
                         }
-                        emit(buf, cap, base, sb, lane, o.status);
+                        emit(buf, cap, base, sb, lane, o.status, sg);
                     }
                     code_pass(dd);
                     REF |= SIG;
@@ -663,11 +713,12 @@ __global__ void __launch_bounds__(PW * 32, 7) t1_model_warp(int32_t *qt, const B
                         sb.put(sigt[vc.pat(r)], bit);
                         if (bit) sign_sym(sb, vc, r);
                     }
-                    emit(buf, cap, base, sb, lane, o.status);
+                    emit(buf, cap, base, sb, lane, o.status, sg);
                 }
                 code_pass(dd);
                 SIG = S1 | Nc;
             }
+            stage_flush(buf, cap, base, sg, lane, true);
         }
         // trace flags back (bit 30 of the Mallat array, or a byte array)
 #pragma unroll
