@@ -131,23 +131,22 @@ __global__ void __launch_bounds__(RW * 32) recon_kernel(Live lv, const BlockDesc
     if (lb >= r.nblk) return;
     const int b = r.blk0 + lb;
     const int K = Kb[b], np = npb[b];
+    const BlockDesc d = blk[b];  // read alongside the pass counts
     // W already holds this block for np kept passes: nothing to do
     if (done && done[b] == np) return;
-    const BlockDesc d = blk[b];
+    // the whole block lies inside the planes (checked once; 32-bit offsets below)
+    if (d.w <= 0 || d.h <= 0 || d.off < 0 || d.off + (long long)(d.h - 1) * d.stride + d.w > ntot) return;
+    const int32_t *__restrict__ src = qt0 + d.off;
+    float *__restrict__ dst = W0 + d.off;
     const int lane = threadIdx.x & 31;
     for (int c = lane; c < d.w; c += 32) {
         for (int r0 = 0; r0 < d.h; r0 += 8) {  // eight loads in flight per lane
             uint32_t q[8];
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const long long i = d.off + (long long)(r0 + u) * d.stride + c;
-                q[u] = (r0 + u < d.h && INBQ(i, ntot)) ? (uint32_t)qt0[i] : 0u;
-            }
+            for (int u = 0; u < 8; u++) q[u] = r0 + u < d.h ? (uint32_t)src[(r0 + u) * d.stride + c] : 0u;
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const long long i = d.off + (long long)(r0 + u) * d.stride + c;
-                if (r0 + u < d.h && INBQ(i, ntot)) W0[i] = recon_value(q[u], d.delta, K, np);
-            }
+            for (int u = 0; u < 8; u++)
+                if (r0 + u < d.h) dst[(r0 + u) * d.stride + c] = recon_value(q[u], d.delta, K, np);
         }
     }
     if (done && (threadIdx.x & 31) == 0) done[b] = np;
