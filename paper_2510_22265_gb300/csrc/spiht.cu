@@ -444,11 +444,11 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                 // resets the counter for the next wave
                 __syncthreads();
             }
-            // the stayers become the LIS of the next plane
-            const long long ns = sh.nstay;
-            for (long long k = tid; k < ns; k += ET) lis[k] = lis_new[k];
-            __syncthreads();
-            if (tid == 0) sh.nlis = ns;
+            // the stayers are the LIS of the next plane: the two LIS buffers trade places
+            uint2 *t = lis;
+            lis = lis_new;
+            lis_new = t;
+            if (tid == 0) sh.nlis = sh.nstay;
             __syncthreads();
         }
         // ---- refinement pass over the LSP entries of earlier planes
