@@ -358,17 +358,20 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
             while (ncur > 0) {
                 if (tid == 0) sh.nnext = 0;
                 __syncthreads();
+                // each thread's entry of the next chunk is read one chunk ahead
+                uint2 e_next = make_uint2(0, 0);
+                if (tid < ncur && INB(tid, NN)) e_next = cur[tid];
                 for (long long base = 0; base < ncur; base += ET) {
                     const long long k = base + tid;
                     int v[NQ] = {0, 0, 0, 0, 0};
-                    uint2 e = make_uint2(0, 0);
+                    uint2 e = e_next;
+                    if (k + ET < ncur && INB(k + ET, NN)) e_next = cur[k + ET];
                     uint32_t c[9];
                     int32_t sv[9];
                     int nc = 0;
                     bool sg = false;
-                    uint32_t sigmask = 0;
+                    uint32_t sigmask = 0, mlv = 0;
                     if (k < ncur) {
-                        if (INB(k, NN)) e = cur[k];
                         if (!INB(e.x >> 1, NN)) e.x = 0;
                         const uint32_t idx = e.x >> 1;
                         v[0] = 1;
@@ -384,12 +387,19 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                                     v[0] += 1 + cs; v[1] += !cs; v[2] += cs;
                                 }
                                 v[3] = has_L(g, idx);
+                                if (v[3]) mlv = maxl[idx];  // the next wave's type-B entry, read now
                             } else {
                                 v[4] = 1;
                             }
                         } else {  // type B: S_n(L)
-                            if (sg) { nc = children(g, idx, c); v[3] = nc; }
-                            else v[4] = 1;
+                            if (sg) {
+                                nc = children(g, idx, c);
+                                v[3] = nc;
+                                for (int q = 0; q < nc; q++)  // the next wave's type-A entries' maxima, read now
+                                    sv[q] = (int32_t)maxd[INB(c[q], NN) ? c[q] : 0];
+                            } else {
+                                v[4] = 1;
+                            }
                         }
                     }
                     if (tid == 0) sh.wbase = sh.pos >> 5;
@@ -419,13 +429,11 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                                 }
                             }
                             if (has_L(g, idx) && INB(sh.nnext + v[3], NN))
-                                nxt[sh.nnext + v[3]] = make_uint2((idx << 1) | 1, maxl[idx]);
+                                nxt[sh.nnext + v[3]] = make_uint2((idx << 1) | 1, mlv);
                         } else {
                             win_set(sh, bp);
-                            for (int q = 0; q < nc; q++) {
-                                const uint32_t cq = INB(c[q], NN) ? c[q] : 0;
-                                if (INB(sh.nnext + v[3] + q, NN)) nxt[sh.nnext + v[3] + q] = make_uint2(c[q] << 1, maxd[cq]);
-                            }
+                            for (int q = 0; q < nc; q++)
+                                if (INB(sh.nnext + v[3] + q, NN)) nxt[sh.nnext + v[3] + q] = make_uint2(c[q] << 1, (uint32_t)sv[q]);
                         }
                     }
                     __syncthreads();
