@@ -125,12 +125,12 @@ __global__ void maxima_kernel(Live lv, const __grid_constant__ FieldRun one, int
         int n = children(g, idx, c);
         uint32_t md = 0, ml = 0;
         for (int q = 0; q < n; q++) {
-            if (!INB(c[q], (long long)g.ny * g.nx)) continue;
+            if (!INBQ(c[q], (long long)g.ny * g.nx)) continue;
             uint32_t cd = leaf_children ? 0u : maxd[c[q]];  // level-1 nodes have no descendants
             md = max(md, max(absi(s[c[q]]), cd));
             ml = max(ml, cd);
         }
-        if (!INB(idx, (long long)g.ny * g.nx)) continue;
+        if (!INBQ(idx, (long long)g.ny * g.nx)) continue;
         maxd[idx] = md;
         maxl[idx] = ml;
     }
@@ -195,7 +195,7 @@ __device__ __forceinline__ void win_clear(EncShared &sh) {
     for (int k = threadIdx.x; k < WIN_WORDS; k += ET) sh.win[k] = 0;
 }
 __device__ __forceinline__ void win_set(EncShared &sh, unsigned long long b) {
-    if (INB((long long)(b >> 5) - (long long)sh.wbase, WIN_WORDS)) atomicOr(&sh.win[(b >> 5) - sh.wbase], bitmask(b));
+    if (INBQ((long long)(b >> 5) - (long long)sh.wbase, WIN_WORDS)) atomicOr(&sh.win[(b >> 5) - sh.wbase], bitmask(b));
 }
 // The chunk's bits are [start_bit, end_bit).  When start_bit is not on a word
 // boundary the window's first word also holds bits of the chunk before (the
@@ -273,14 +273,14 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
         uint32_t idx = 0;
         if (k < nroot) {
             idx = (uint32_t)(k / wL) * g.nx + (uint32_t)(k % wL);
-            if (INB(k, NN)) lip[k] = make_uint2(idx, smag(s[idx]));
+            if (INBQ(k, NN)) lip[k] = make_uint2(idx, smag(s[idx]));
             uint32_t c[9];
             v[0] = children(g, idx, c) > 0;
         }
         block_scan(v, sh);
         if (k < nroot) {
             uint32_t c[9];
-            if (children(g, idx, c) > 0 && INB(sh.nlis + v[0], NN)) lis[sh.nlis + v[0]] = make_uint2(idx << 1, maxd[idx]);
+            if (children(g, idx, c) > 0 && INBQ(sh.nlis + v[0], NN)) lis[sh.nlis + v[0]] = make_uint2(idx << 1, maxd[idx]);
         }
         __syncthreads();
         if (tid == 0) sh.nlis += sh.tot[0];
@@ -304,8 +304,8 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                     const long long k = k0 + j;
                     uint2 x = make_uint2(0, 0);
                     if (k < nl) {
-                        if (INB(k, NN)) x = lip[k];
-                        if (!INB(x.x, NN)) x.x = 0;
+                        if (INBQ(k, NN)) x = lip[k];
+                        if (!INBQ(x.x, NN)) x.x = 0;
                         const bool sg = (x.y & 0x7FFFFFFFu) >= T;
                         sgm |= (unsigned)sg << j;
                         v[0] += 1 + sg; v[1] += !sg; v[2] += sg;
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                     if ((sgm >> j) & 1) {
                         win_set(sh, bp);
                         if (x.y >> 31) win_set(sh, bp + 1);
-                        if (INB(ls, NN)) {
+                        if (INBQ(ls, NN)) {
                             sig_pos[x.x] = (uint32_t)(bp + 1);
                             lsp_idx[x.x] = (uint32_t)ls;
                             lsp[ls] = make_uint2(x.x, x.y & 0x7FFFFFFFu);
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                         ls++;
                         bp += 2;
                     } else {
-                        if (INB(keep, NN)) lip[keep] = x;
+                        if (INBQ(keep, NN)) lip[keep] = x;
                         keep++;
                         bp += 1;
                     }
@@ -360,19 +360,19 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                 __syncthreads();
                 // each thread's entry of the next chunk is read one chunk ahead
                 uint2 e_next = make_uint2(0, 0);
-                if (tid < ncur && INB(tid, NN)) e_next = cur[tid];
+                if (tid < ncur && INBQ(tid, NN)) e_next = cur[tid];
                 for (long long base = 0; base < ncur; base += ET) {
                     const long long k = base + tid;
                     int v[NQ] = {0, 0, 0, 0, 0};
                     uint2 e = e_next;
-                    if (k + ET < ncur && INB(k + ET, NN)) e_next = cur[k + ET];
+                    if (k + ET < ncur && INBQ(k + ET, NN)) e_next = cur[k + ET];
                     uint32_t c[9];
                     int32_t sv[9];
                     int nc = 0;
                     bool sg = false;
                     uint32_t sigmask = 0, mlv = 0;
                     if (k < ncur) {
-                        if (!INB(e.x >> 1, NN)) e.x = 0;
+                        if (!INBQ(e.x >> 1, NN)) e.x = 0;
                         const uint32_t idx = e.x >> 1;
                         v[0] = 1;
                         sg = e.y >= T;
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                             if (sg) {
                                 nc = children(g, idx, c);
                                 for (int q = 0; q < nc; q++) {
-                                    if (!INB(c[q], NN)) c[q] = 0;
+                                    if (!INBQ(c[q], NN)) c[q] = 0;
                                     sv[q] = s[c[q]];
                                     const bool cs = absi(sv[q]) >= T;
                                     sigmask |= (uint32_t)cs << q;
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                                 nc = children(g, idx, c);
                                 v[3] = nc;
                                 for (int q = 0; q < nc; q++)  // the next wave's type-A entries' maxima, read now
-                                    sv[q] = (int32_t)maxd[INB(c[q], NN) ? c[q] : 0];
+                                    sv[q] = (int32_t)maxd[INBQ(c[q], NN) ? c[q] : 0];
                             } else {
                                 v[4] = 1;
                             }
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                         const uint32_t idx = e.x >> 1;
                         unsigned long long bp = sh.pos + v[0];
                         if (!sg) {
-                            if (INB(sh.nstay + v[4], NN)) lis_new[sh.nstay + v[4]] = e;
+                            if (INBQ(sh.nstay + v[4], NN)) lis_new[sh.nstay + v[4]] = e;
                         } else if ((e.x & 1) == 0) {
                             win_set(sh, bp++);
                             long long li = sh.nlip + v[1], ls = sh.nlsp + v[2];
@@ -419,21 +419,21 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                                     if (sv[q] < 0) win_set(sh, bp + 1);
                                     sig_pos[c[q]] = (uint32_t)(bp + 1);
                                     lsp_idx[c[q]] = (uint32_t)ls;
-                                    if (INB(ls, NN)) lsp[ls] = make_uint2(c[q], absi(sv[q]));
+                                    if (INBQ(ls, NN)) lsp[ls] = make_uint2(c[q], absi(sv[q]));
                                     ls++;
                                     bp += 2;
                                 } else {
-                                    if (INB(li, NN)) lip[li] = make_uint2(c[q], smag(sv[q]));
+                                    if (INBQ(li, NN)) lip[li] = make_uint2(c[q], smag(sv[q]));
                                     li++;
                                     bp += 1;
                                 }
                             }
-                            if (has_L(g, idx) && INB(sh.nnext + v[3], NN))
+                            if (has_L(g, idx) && INBQ(sh.nnext + v[3], NN))
                                 nxt[sh.nnext + v[3]] = make_uint2((idx << 1) | 1, mlv);
                         } else {
                             win_set(sh, bp);
                             for (int q = 0; q < nc; q++)
-                                if (INB(sh.nnext + v[3] + q, NN)) nxt[sh.nnext + v[3] + q] = make_uint2(c[q] << 1, (uint32_t)sv[q]);
+                                if (INBQ(sh.nnext + v[3] + q, NN)) nxt[sh.nnext + v[3] + q] = make_uint2(c[q] << 1, (uint32_t)sv[q]);
                         }
                     }
                     __syncthreads();
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
 #pragma unroll
                 for (int j = 0; j < EPL; j++) {
                     const long long k = k0 + j;
-                    if (k < lsp_before && INB(k, NN) && ((lsp[k].y >> n) & 1)) win_set(sh, sh.pos + k);
+                    if (k < lsp_before && INBQ(k, NN) && ((lsp[k].y >> n) & 1)) win_set(sh, sh.pos + k);
                 }
                 __syncthreads();
                 const long long end = base + (long long)ET * EPL < lsp_before ? base + (long long)ET * EPL : lsp_before;
