@@ -160,7 +160,7 @@ __device__ __forceinline__ void block_count_fail_add(unsigned long long in, unsi
 // the last step of an inverse transform at point gi of field r
 __device__ __forceinline__ void finish_point(const InvFinal &fin, const FieldRun &r, float *dst, float v, long long gi,
                                              unsigned long long &cnt) {
-    if (!INB(gi, r.N)) return;
+    if (!INBQ(gi, r.N)) return;
     if (fin.mode <= 0) {
         if (fin.mode == 0 && fin.add_base) v = v + r.Abase[gi];
         dst[gi] = v;

@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(NT) sprefix_kernel(Live lv, const __grid_const
         if (m && sp != 0xFFFFFFFFu && (long long)sp < T) {
             int ns = 31 - __clz(m), p = ns;
             long long li = lsp_idx[i];
-            while (p > 0 && INB(p - 1, 32) && rs[p - 1] + li < T) p--;
+            while (p > 0 && INBQ(p - 1, 32) && rs[p - 1] + li < T) p--;
             float val = deq((m >> p) << p, p, step);
             o = v < 0 ? -val : val;
         }

@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(WARPS * 32) t1_encode_kernel(int32_t *qt, cons
         uint32_t mx = 0;
         for (int i = lane; i < n; i += 32) {
             int r = i / w, c = i - r * w;
-            int32_t v = INB(d.off + (int64_t)r * d.stride + c, nq) ? qt[d.off + (int64_t)r * d.stride + c] : 0;
+            int32_t v = INBQ(d.off + (int64_t)r * d.stride + c, nq) ? qt[d.off + (int64_t)r * d.stride + c] : 0;
             // sign-magnitude Mallat array (bit 31 sign, bit 30 trace flag) or two's complement
             uint32_t m = mark_spp_in_q ? (uint32_t)v & 0x3FFFFFFFu : (uint32_t)(v < 0 ? -v : v);
             mag[i] = m | (v < 0 ? 0x80000000u : 0);
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(WARPS * 32) t1_encode_kernel(int32_t *qt, cons
                 auto end_pass = [&](int64_t dd) {
                     uint32_t tail;
                     int tl;
-                    if (!INB(pass, o.maxpass)) return;
+                    if (!INBQ(pass, o.maxpass)) return;
                     o.pass_len[pb + pass] = e.trunc(tail, tl);
                     o.tail[pb + pass] = tail;
                     o.tail_len[pb + pass] = tl;
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(WARPS * 32) t1_encode_kernel(int32_t *qt, cons
             uint32_t f = (mag[i] >> 30) & 1;
             if (mark_spp_in_q) {
                 int64_t at = d.off + (int64_t)r * d.stride + c;
-                if (INB(at, nq)) qt[at] = (qt[at] & ~0x40000000) | (int32_t)(f << 30);
+                if (INBQ(at, nq)) qt[at] = (qt[at] & ~0x40000000) | (int32_t)(f << 30);
             }
             if (spp_out) spp_out[(size_t)b * n + i] = (uint8_t)f;
         }
@@ -1006,7 +1006,7 @@ __global__ void __launch_bounds__(WARPS * 32) t1_decode_kernel(const uint8_t *by
             uint32_t m = mag[i];
             if (coef) {
                 float val = p >= 0 ? deq(m, p, d.delta) : 0.0f;
-                if (INB(d.off + (int64_t)r * d.stride + c, nq)) coef[d.off + (int64_t)r * d.stride + c] = ng ? -val : val;
+                if (INBQ(d.off + (int64_t)r * d.stride + c, nq)) coef[d.off + (int64_t)r * d.stride + c] = ng ? -val : val;
             } else {
                 omag[(size_t)b * n + i] = p >= 0 ? (int32_t)m : 0;
                 oplane[(size_t)b * n + i] = (int8_t)p;
