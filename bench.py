@@ -37,7 +37,7 @@ METRIC = "compress/decompress GB/s at 1% rel bound (batched vs plain); CR; p99 l
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) that ncu measured for the
 # dominant kernel on the default workload, averaged over the launches of one compression step
 # (profiles/launches_compress_era5_148x721x1440.md); reported only for that workload
-NCU_TRAFFIC = {"inv_level": 248.4e6}
+NCU_TRAFFIC = {"inv_level": 248.3e6}
 DEFAULT_SHAPE = [4, 37, 721, 1440]
 BOUND = 1e-2
 
