@@ -528,7 +528,7 @@ __device__ __forceinline__ int64_t warp_sum64(int64_t v) {
     return v;
 }
 
-__global__ void __launch_bounds__(PW * 32, 7) t1_model_warp(int32_t *qt, const BlockDesc *blk, int nblk, T1Out o,
+__global__ void __launch_bounds__(PW * 32, 8) t1_model_warp(int32_t *qt, const BlockDesc *blk, int nblk, T1Out o,
                                                          int mark_spp_in_q, uint8_t *spp_out, long long nq) {
     __shared__ PWShared tb;
     __shared__ uint32_t smag[PW][32][33];  // each warp's block, column-major by lane (for distortion sums)
