@@ -29,6 +29,7 @@ struct BaseLoop {
     double q, r0, tol, rmax, N;
     int fallback, phase, iters, done;
     double r_low, r_high, r_mid, qA0, q_last, r_last, r_f, q_f, budget;
+    double sel_lo, sel_hi;  // every budget in [sel_lo, sel_hi) selects sel_eval
     Sel sel_eval, sel_A, sel_f;
 };
 
@@ -135,6 +136,7 @@ struct EvalCache {
     int n, pad;
     Sel sel[EVC];
     unsigned long long count[EVC];
+    double lo[EVC], hi[EVC];  // budgets in [lo, hi) select sel (the search lands on the same segment)
 };
 
 // ---- loop steps, one warp per live field: a selection's searches split their
@@ -158,7 +160,9 @@ __device__ __forceinline__ int warp_last_true(int lo, int hi, int lane, P pred) 
 }
 
 // select_for_budget with the whole warp (same result on every lane)
-__device__ Sel select_field_w(const Hulls &h, const FieldRun &r, double B, int lane) {
+// [lo, hi): the budgets whose search lands on the same segment, so they
+// select the same passes
+__device__ Sel select_field_w(const Hulls &h, const FieldRun &r, double B, int lane, double &lo, double &hi) {
     const long long sb = (long long)r.blk0 * T1_MAXPASS;
     const uint64_t *skey = h.skey + sb;
     const unsigned long long *cum = h.cum + sb;
@@ -166,6 +170,8 @@ __device__ Sel select_field_w(const Hulls &h, const FieldRun &r, double B, int l
     Sel s;
     s.thr = 0; s.mode = 0; s.pad = 0;
     int i = warp_last_true(-1, m, lane, [&](int p) { return (double)cum[p] <= B; });
+    lo = i >= 0 ? (double)cum[i] : -INFINITY;
+    hi = i + 1 < m ? (double)cum[i + 1] : INFINITY;
     if (i < 0) return s;
     if (i + 1 < m && skey[i + 1] == skey[i]) {  // that group does not fit whole
         const unsigned long long kk = skey[i];
@@ -182,6 +188,7 @@ __device__ Sel select_field_w(const Hulls &h, const FieldRun &r, double B, int l
 struct WarpCache {
     Sel sel[EVC / 32];
     unsigned long long count[EVC / 32];
+    double lo[EVC / 32], hi[EVC / 32];
     int n;
 };
 static_assert(EVC % 32 == 0, "cache entries are spread over the lanes");
@@ -191,16 +198,36 @@ __device__ __forceinline__ void wc_load(WarpCache &w, const EvalCache &c, int nc
 #pragma unroll
     for (int q = 0; q < EVC / 32; q++) {
         const int j = q * 32 + lane;
-        if (j < nc) { w.sel[q] = c.sel[j]; w.count[q] = c.count[j]; }
-        else { w.sel[q].mode = -1; w.count[q] = 0; }
+        if (j < nc) { w.sel[q] = c.sel[j]; w.count[q] = c.count[j]; w.lo[q] = c.lo[j]; w.hi[q] = c.hi[j]; }
+        else { w.sel[q].mode = -1; w.count[q] = 0; w.lo[q] = INFINITY; w.hi[q] = -INFINITY; }
     }
 }
 
 __device__ void bl_advance_w(BaseLoop &s, const FieldRun &r, const Hulls &h, const WarpCache &w, int lane) {
     while (!s.done) {
-        s.sel_eval = select_field_w(h, r, s.budget, lane);
         int k = -1;
         unsigned long long cnt = 0;
+        // a budget inside an evaluated selection's interval selects it: no search
+#pragma unroll
+        for (int q = 0; q < EVC / 32; q++) {
+            const bool hit = q * 32 + lane < w.n && w.lo[q] <= s.budget && s.budget < w.hi[q];
+            const unsigned b = __ballot_sync(0xffffffffu, hit);
+            if (k < 0 && b) {
+                const int src = __ffs(b) - 1;
+                k = q * 32 + src;
+                cnt = __shfl_sync(0xffffffffu, w.count[q], src);
+                s.sel_eval.thr = __shfl_sync(0xffffffffu, w.sel[q].thr, src);
+                s.sel_eval.mode = __shfl_sync(0xffffffffu, w.sel[q].mode, src);
+                s.sel_eval.pad = 0;
+                s.sel_lo = __shfl_sync(0xffffffffu, w.lo[q], src);
+                s.sel_hi = __shfl_sync(0xffffffffu, w.hi[q], src);
+            }
+        }
+        if (k >= 0) {
+            bl_step(s, (double)cnt / s.N);
+            continue;
+        }
+        s.sel_eval = select_field_w(h, r, s.budget, lane, s.sel_lo, s.sel_hi);
 #pragma unroll
         for (int q = 0; q < EVC / 32; q++) {
             const bool hit = q * 32 + lane < w.n && w.sel[q].mode == s.sel_eval.mode &&
@@ -280,11 +307,18 @@ __global__ void __launch_bounds__(256) bl_update_w(BaseLoop *bl, EvalCache *evc,
             if (lane == 0) {
                 c.sel[nc] = s.sel_eval;
                 c.count[nc] = cnt;
+                c.lo[nc] = s.sel_lo;
+                c.hi[nc] = s.sel_hi;
                 c.n = nc + 1;
             }
 #pragma unroll
             for (int q = 0; q < EVC / 32; q++)
-                if (q * 32 + lane == nc) { w.sel[q] = s.sel_eval; w.count[q] = cnt; }
+                if (q * 32 + lane == nc) {
+                    w.sel[q] = s.sel_eval;
+                    w.count[q] = cnt;
+                    w.lo[q] = s.sel_lo;
+                    w.hi[q] = s.sel_hi;
+                }
             w.n = nc + 1;
         }
         if (lane == 0) {
