@@ -8,9 +8,12 @@ quantisation, tier-1, both feedback loops, residual SPIHT layer, fallback,
 packing) with the inputs resident in HBM; inputs are larger than L2.
 
 Also reported: decompression GB/s of the produced streams, compression ratio,
-an end-to-end figure through the host C ABI (host buffers, copies inside the
-timed region), the oracle timed on the host cores on a bounded sample, and the
-roofline of the dominant kernel from CUDA events recorded around its launches.
+an end-to-end figure (every step copies the stack in from pinned host memory,
+runs the batch call and copies every stream back, all inside the timed region),
+the single-field host API for context, the oracle timed on the host cores on a
+bounded sample, and the roofline of the dominant kernel from the library's
+CUDA events around its launches, recorded in a profiled pass after the timed
+steps (the timed steps run without them).
 
 --impl reference times the CPU oracle itself on a bounded sample of the same
 workload (the only other place this file runs the oracle).
