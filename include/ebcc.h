@@ -67,7 +67,10 @@ typedef struct {
     long long len_two, len_one;  /* two-layer and base-only stream lengths (0 = none; len_two is also 0
                                     when the base-only stream was proven shorter before the two-layer
                                     stream was finished) */
-    double q_base;               /* q_A of the kept base encoding */
+    double q_base;               /* q_A of the kept base encoding (a lower bound in the one case
+                                    where that encoding missed q -- the r = 1 encoding kept after
+                                    every ratio missed -- since a count stops once a miss is
+                                    certain) */
 } ebcc_stats;
 
 /* Fill *p with the defaults listed above. */
