@@ -62,6 +62,22 @@ def _oracle_one(args):
     return time.perf_counter() - t, x.nbytes, len(s)
 
 
+def max_over_ranks(t_ms, dist, device):
+    """The job's step time: the largest per-step time over the ranks (every
+    rank runs its own replica of the workload; fields need no exchange)."""
+    if dist is None:
+        return t_ms
+    import torch
+    tt = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_gbs(raw_bytes_per_rank, world, t_ms):
+    """Whole-job throughput: the input bytes of all ranks per step time (weak scaling)."""
+    return raw_bytes_per_rank * world / (t_ms / 1e3) / 1e9
+
+
 def per_step(prof, n):
     """Profiler totals over n steps -> per-step figures (ms, launches, bytes)."""
     return [{"name": p["name"], "ms": p["ms"] / n, "launches": p["launches"] / n, "bytes": p["bytes"] / n}
@@ -265,10 +281,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     B.lib().ebcc_profile_enable(0)
     prof = per_step(B.profile_read(), n_prof)
-    if dist:
-        tt = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = max_over_ranks(t_ms, dist, "cuda")
     comp_bytes = sum(r[1] for r in res)
     # the plain path: one field per call (every launch covers one field), on a
     # bounded subset of the same fields
@@ -340,7 +353,7 @@ def run_gpu(args):
         if dist:
             dist.destroy_process_group()
         return
-    value = raw_bytes * world / (t_ms / 1e3) / 1e9
+    value = job_gbs(raw_bytes, world, t_ms)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
     roof = None
