@@ -243,6 +243,29 @@ def t1_trace_value(qv: int, spp: int, K: int, npasses: int) -> float:
     return lib().or_t1_trace_value(int(qv), int(spp), int(K), int(npasses))
 
 
+def _nb9(a) -> np.ndarray:
+    v = np.ascontiguousarray(np.asarray(a, dtype=np.uint8).reshape(9))
+    return v
+
+
+def t1_context_sig(orient: int, sig9) -> int:
+    """Significance context of the centre of a 3x3 neighbourhood (the coder's function)."""
+    v = _nb9(sig9)
+    return lib().or_t1_context_sig(int(orient), _p(v, C.c_uint8))
+
+
+def t1_context_sign(sig9, neg9):
+    """(sign context, XOR bit) of the centre of a 3x3 neighbourhood."""
+    s, n, xr = _nb9(sig9), _nb9(neg9), C.c_int()
+    cx = lib().or_t1_context_sign(_p(s, C.c_uint8), _p(n, C.c_uint8), C.byref(xr))
+    return cx, xr.value
+
+
+def t1_context_ref(first_refinement: bool, sig9) -> int:
+    v = _nb9(sig9)
+    return lib().or_t1_context_ref(int(bool(first_refinement)), _p(v, C.c_uint8))
+
+
 # ---------------------------------------------------------------- PCRD
 def pcrd_hull(t: T1) -> dict:
     h = _Hull()

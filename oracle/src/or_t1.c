@@ -78,6 +78,13 @@ static int any_nbr(const t1st *t, int i, int j) {
     return 0;
 }
 
+/* Table D.4: refinement context (first refinement of the coefficient or not,
+ * and whether any of its eight neighbours is significant) */
+static int ctx_ref(const t1st *t, int i, int j) {
+    if (t->ref[i * t->w + j]) return 16;
+    return any_nbr(t, i, j) ? 15 : 14;
+}
+
 /* doubled-unit reconstruction of magnitude m known down to plane p */
 static int64_t rec2(int64_t m, int p) { return 2 * ((m >> p) << p) + ((int64_t)1 << p); }
 static int64_t sq(int64_t x) { return x * x; }
@@ -144,7 +151,7 @@ int or_t1_encode(const int32_t *q, int w, int h, int orient, uint8_t *stream, lo
                     for (int i = s; i < s + 4 && i < h; i++) {
                         int x = i * w + j;
                         if (!t.sig[x] || t.vis[x]) continue;
-                        int cx = t.ref[x] ? 16 : (any_nbr(&t, i, j) ? 15 : 14);
+                        int cx = ctx_ref(&t, i, j);
                         or_mqenc_encode(&e, cx, (int)((m[x] >> p) & 1));
                         t.ref[x] = 1;
                         dd += sq(2 * m[x] + 1 - rec2(m[x], p + 1)) - sq(2 * m[x] + 1 - rec2(m[x], p));
@@ -236,7 +243,7 @@ int or_t1_decode(const uint8_t *stream, long len, int w, int h, int orient, int 
                     for (int i = s; i < s + 4 && i < h; i++) {
                         int x = i * w + j;
                         if (!t.sig[x] || t.vis[x]) continue;
-                        int cx = t.ref[x] ? 16 : (any_nbr(&t, i, j) ? 15 : 14);
+                        int cx = ctx_ref(&t, i, j);
                         mag[x] |= or_mqdec_decode(&d, cx) << p;
                         plane[x] = (int8_t)p;
                         t.ref[x] = 1;
@@ -297,4 +304,42 @@ double or_t1_trace_value(int32_t qv, int spp, int K, int npasses) {
     }
     double v = (double)((m >> p) << p) + 0.5 * (double)((int64_t)1 << p);
     return qv < 0 ? -v : v;
+}
+
+/* Context labels of the centre of a 3x3 neighbourhood, through the same
+ * functions the coder uses (for the tests that pin them to T.800 Tables D.1,
+ * D.3 and D.4).  sig9[3*r + c] = 1 if the neighbour at row r, column c is
+ * significant, neg9 its sign (1 = negative); the centre entries are ignored. */
+static void t1_from9(t1st *t, uint8_t *sig, uint8_t *neg, uint8_t *zero, const uint8_t *sig9,
+                     const uint8_t *neg9, int orient) {
+    for (int k = 0; k < 9; k++) {
+        sig[k] = k == 4 ? 0 : (sig9[k] != 0);
+        neg[k] = (neg9 && k != 4) ? (neg9[k] != 0) : 0;
+        zero[k] = 0;
+    }
+    t->w = 3; t->h = 3; t->orient = orient;
+    t->sig = sig; t->neg = neg; t->vis = zero; t->ref = zero;
+}
+
+int or_t1_context_sig(int orient, const uint8_t *sig9) {
+    uint8_t sig[9], neg[9], zero[9];
+    t1st t;
+    t1_from9(&t, sig, neg, zero, sig9, NULL, orient);
+    return ctx_sig(&t, 1, 1);
+}
+
+int or_t1_context_sign(const uint8_t *sig9, const uint8_t *neg9, int *xorbit) {
+    uint8_t sig[9], neg[9], zero[9];
+    t1st t;
+    t1_from9(&t, sig, neg, zero, sig9, neg9, 0);
+    return ctx_sign(&t, 1, 1, xorbit);
+}
+
+int or_t1_context_ref(int first_refinement, const uint8_t *sig9) {
+    uint8_t sig[9], neg[9], zero[9], ref[9] = {0};
+    t1st t;
+    t1_from9(&t, sig, neg, zero, sig9, NULL, 0);
+    ref[4] = first_refinement ? 0 : 1;
+    t.ref = ref;
+    return ctx_ref(&t, 1, 1);
 }

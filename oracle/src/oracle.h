@@ -112,6 +112,13 @@ int or_t1_decode(const uint8_t *stream, long len, int w, int h, int orient, int 
                  int32_t *out_mag, int8_t *out_plane, uint8_t *out_neg);
 /* value (in units of the step) implied by npasses passes, from the encoder trace */
 double or_t1_trace_value(int32_t qv, int spp, int K, int npasses);
+/* context labels of the centre of a 3x3 neighbourhood (sig9[3*row + col]
+ * significance, neg9 signs; centre ignored), computed by the coder's own
+ * functions: significance (Table D.1, orient 0 LL, 1 HL, 2 LH, 3 HH), sign
+ * (Table D.3, with its XOR bit) and refinement (Table D.4) */
+int or_t1_context_sig(int orient, const uint8_t *sig9);
+int or_t1_context_sign(const uint8_t *sig9, const uint8_t *neg9, int *xorbit);
+int or_t1_context_ref(int first_refinement, const uint8_t *sig9);
 
 /* ---------- PCRD (or_pcrd.c) ---------- */
 typedef struct {
