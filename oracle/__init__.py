@@ -347,6 +347,24 @@ def compress(x: np.ndarray, bound: float, kind: int = 1, p: _Params | None = Non
     return data, stats
 
 
+_QA_FN = C.CFUNCTYPE(C.c_double, C.c_double)
+
+
+def base_loop_trace(qa, r0=20.0, tol=1e-3, q=0.999, fallback=False, r_max=1e12):
+    """Algorithm 1's base loop against the curve qa(r) -> q_A: returns
+    (evaluated ratios in order, index of the evaluation kept as e_f, r_f, q_f, ok)."""
+    fn = _QA_FN(lambda r: float(qa(r)))
+    seq = np.zeros(4096, np.float64)
+    n, kept, r_f, q_f = C.c_int(), C.c_int(), C.c_double(), C.c_double()
+    L = lib()
+    L.or_base_loop_trace.argtypes = [_QA_FN, C.c_double, C.c_double, C.c_double, C.c_int, C.c_double,
+                                     C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int),
+                                     C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    ok = L.or_base_loop_trace(fn, r0, tol, q, int(fallback), r_max, _p(seq, C.c_double), len(seq),
+                              C.byref(n), C.byref(kept), C.byref(r_f), C.byref(q_f))
+    return list(seq[:n.value]), kept.value, r_f.value, q_f.value, bool(ok)
+
+
 def decompress(data: bytes, ny: int, nx: int) -> np.ndarray:
     buf = np.frombuffer(data, np.uint8).copy()
     out = np.zeros((ny, nx), np.float32)

@@ -162,43 +162,97 @@ static double enc_base(fctx *f, double r, int *np, double *tmp) {
     return (double)ok / (double)f->N;
 }
 
-/* the two bracketing loops and the bisection of Algorithm 1; np_f = e_f */
-static int base_loop(fctx *f, const or_params *p, double q, int fallback, int *np_f, double *r_f,
-                     double *q_f, int *iters) {
-    int *npA = (int *)malloc(sizeof(int) * f->nblocks);
-    double *tmp = (double *)malloc(sizeof(double) * f->N);
-    double r_max = 4.0 * (double)f->N;
+/* One evaluation enc_base(A, r, eps) of Algorithm 1: returns q_A and writes the
+ * encoding e_A (ne ints: passes kept per code-block) for ratio r. */
+typedef double (*enc_base_fn)(void *ctx, double r, int *e_A);
+
+/* The base-layer search of Algorithm 1.  One evaluation at r0 gives q_A0.
+ * While the last q_A is below q, r_low is halved and evaluated again; the last
+ * encoding of that loop (or the one at r0) becomes e_f.  q_A is then reset to
+ * q_A0, and while it exceeds q, r_high is doubled and evaluated.  Finally the
+ * interval is bisected until it is no wider than tol: a midpoint whose q_A is
+ * below q becomes r_high, any other becomes r_low and its encoding e_f.
+ * Readings: r_low is floored at 1 (c14), r_high capped at r_max, and the
+ * q = 1 fallback's upward loop runs while q_A >= q (c17).  e_f (ne ints), the
+ * ratio it was made at and its q_A are returned; the result is 1 when e_f
+ * meets q. */
+static int base_loop_run(enc_base_fn enc, void *ctx, int ne, double r_max, double r0, double tol, double q,
+                         int fallback, int *e_f, double *r_f, double *q_f, int *iters) {
+    int *e_A = (int *)malloc(sizeof(int) * (ne > 0 ? ne : 1));
     int it = 0;
-    double qA0 = enc_base(f, p->r0, npA, tmp); it++;
-    double r_low = p->r0, r_high = p->r0, qA = qA0, qAe = qA0, r_e = p->r0;
+    double qA0 = enc(ctx, r0, e_A); it++;
+    double r_low = r0, r_high = r0, qA = qA0, qAe = qA0, r_e = r0;
     while (qA < q) { /* initial ratio too high */
         if (r_low <= 1.0) break;
         r_low = r_low / 2 < 1.0 ? 1.0 : r_low / 2;
-        qA = enc_base(f, r_low, npA, tmp); it++;
+        qA = enc(ctx, r_low, e_A); it++;
         qAe = qA; r_e = r_low;
     }
-    memcpy(np_f, npA, sizeof(int) * f->nblocks);
+    memcpy(e_f, e_A, sizeof(int) * ne);
     *r_f = r_e; *q_f = qAe;
     qA = qA0;
     while (fallback ? qA >= q : qA > q) { /* initial ratio too low */
         if (r_high * 2 > r_max) break;
         r_high = r_high * 2;
-        qA = enc_base(f, r_high, npA, tmp); it++;
+        qA = enc(ctx, r_high, e_A); it++;
     }
-    while (r_high - r_low > p->tol) {
+    while (r_high - r_low > tol) {
         double r_mid = (r_low + r_high) / 2;
-        qA = enc_base(f, r_mid, npA, tmp); it++;
+        qA = enc(ctx, r_mid, e_A); it++;
         if (qA < q) {
             r_high = r_mid;
         } else {
             r_low = r_mid;
-            memcpy(np_f, npA, sizeof(int) * f->nblocks);
+            memcpy(e_f, e_A, sizeof(int) * ne);
             *r_f = r_mid; *q_f = qA;
         }
     }
     *iters = it;
-    free(npA); free(tmp);
+    free(e_A);
     return *q_f >= q;
+}
+
+typedef struct { fctx *f; double *tmp; } enc_ctx;
+
+static double enc_base_cb(void *c, double r, int *np) {
+    enc_ctx *e = (enc_ctx *)c;
+    return enc_base(e->f, r, np, e->tmp);
+}
+
+static int base_loop(fctx *f, const or_params *p, double q, int fallback, int *np_f, double *r_f,
+                     double *q_f, int *iters) {
+    enc_ctx c = {f, (double *)malloc(sizeof(double) * f->N)};
+    int ok = base_loop_run(enc_base_cb, &c, f->nblocks, 4.0 * (double)f->N, p->r0, p->tol, q, fallback, np_f,
+                           r_f, q_f, iters);
+    free(c.tmp);
+    return ok;
+}
+
+/* The same loop against a caller's q_A(r) curve instead of enc_base (for the
+ * tests that pin Algorithm 1's order of evaluations).  r_seq receives the
+ * evaluated ratios in order (up to max_seq; *n_seq = their count), *kept the
+ * index in r_seq of the evaluation kept as e_f. */
+typedef struct {
+    double (*qa)(double);
+    double *r_seq;
+    int max_seq, n;
+} trace_ctx;
+
+static double enc_trace_cb(void *c, double r, int *e_A) {
+    trace_ctx *t = (trace_ctx *)c;
+    if (t->n < t->max_seq) t->r_seq[t->n] = r;
+    e_A[0] = t->n++;
+    return t->qa(r);
+}
+
+int or_base_loop_trace(double (*qa)(double), double r0, double tol, double q, int fallback, double r_max,
+                       double *r_seq, int max_seq, int *n_seq, int *kept, double *r_f, double *q_f) {
+    trace_ctx t = {qa, r_seq, max_seq, 0};
+    int e_f = -1, iters = 0;
+    int ok = base_loop_run(enc_trace_cb, &t, 1, r_max, r0, tol, q, fallback, &e_f, r_f, q_f, &iters);
+    *n_seq = t.n;
+    *kept = e_f;
+    return ok;
 }
 
 static void put_u32(uint8_t *p, uint32_t v) { memcpy(p, &v, 4); }

@@ -157,6 +157,12 @@ typedef struct {
 } or_stats;
 
 void or_params_default(or_params *p);
+/* Algorithm 1's base-layer loop (bracketing, then bisection) run against a
+ * caller's q_A(r) in place of enc_base: the evaluated ratios in order, the
+ * index of the evaluation kept as e_f, its ratio and q_A; returns 1 when the
+ * kept evaluation meets q */
+int or_base_loop_trace(double (*qa)(double), double r0, double tol, double q, int fallback, double r_max,
+                       double *r_seq, int max_seq, int *n_seq, int *kept, double *r_f, double *q_f);
 int or_compress(const float *x, int ny, int nx, double bound, int kind, const or_params *p,
                 uint8_t **out, long *out_len, or_stats *st);
 int or_decompress(const uint8_t *s, long len, float *out, int ny, int nx);
