@@ -8,13 +8,18 @@
  * list of significant pixels (LSP) found in earlier planes.  The stream is
  * embedded: every prefix decodes.
  *
- * Spatial-orientation trees on a Mallat layout of any size (reading c11): an
- * LL coefficient (i,j) has as children the coefficients at the same position
- * in HL_L, LH_L and HH_L; a level-l detail coefficient at band position (a,b)
- * has as children the 2x2 block (2a..2a+1, 2b..2b+1) of the same orientation at
- * level l-1, the last row / column of a band also taking the one extra row /
- * column an odd-sized finer band can have.  Sign bit 1 = negative; bits are
- * packed most significant first.
+ * Spatial-orientation trees on a Mallat layout of any size (reading c11).  The
+ * LL roots are grouped 2x2 as Said & Pearlman group the coarsest pixels: in
+ * the group at (2a, 2b) the root at offset (0,1) has as offspring the 2x2 block
+ * at band position (2a.., 2b..) of HL_L, the root at (1,0) that of LH_L, the
+ * root at (1,1) that of HH_L, and the root at (0,0) none.  Where an odd LL
+ * extent leaves a group without its second row (column), the offset along that
+ * axis falls back to 0, so the block goes to the group's root that exists (the
+ * blocks are clipped to their band).  A level-l detail coefficient at band
+ * position (a,b) has as children the 2x2 block (2a..2a+1, 2b..2b+1) of the
+ * same orientation at level l-1, the last row / column of a band also taking
+ * the one extra row / column an odd-sized finer band can have.  Sign bit 1 =
+ * negative; bits are packed most significant first.
  */
 #include <stdlib.h>
 #include <string.h>
@@ -59,10 +64,17 @@ static int children(const geom *g, long idx, long *c) {
     if (g->L == 0) return 0;
     locate(g, i, j, &lev, &o);
     if (o == 0) {
+        int hL = g->h[g->L], wL = g->w[g->L];
+        int a2 = i - (i & 1), b2 = j - (j & 1); /* the group's top-left root */
         for (int oo = 1; oo <= 3; oo++) {
+            int di = oo >= 2, dj = oo != 2; /* HL (0,1), LH (1,0), HH (1,1) */
+            int oi = (di && a2 + 1 < hL) ? a2 + 1 : a2;
+            int oj = (dj && b2 + 1 < wL) ? b2 + 1 : b2;
+            if (oi != i || oj != j) continue; /* the block belongs to another root */
             int y0, x0, bh, bw;
             band_box(g, g->L, oo, &y0, &x0, &bh, &bw);
-            if (i < bh && j < bw) c[n++] = (long)(y0 + i) * g->nx + x0 + j;
+            for (int r = a2; r < a2 + 2 && r < bh; r++)
+                for (int s = b2; s < b2 + 2 && s < bw; s++) c[n++] = (long)(y0 + r) * g->nx + x0 + s;
         }
         return n;
     }

@@ -1,11 +1,15 @@
 // SPIHT (Said & Pearlman 1996) on GB300 -- EBCC's residual layer (Materials
 // and Methods; Algorithm 1 enc_SPIHT, dec_SPIHT).
 //
-// Trees: an LL coefficient has as children the coefficients at the same place
-// in the coarsest HL, LH and HH bands; a detail coefficient at band position
-// (a, b) has the 2x2 block (2a.., 2b..) of the same orientation one level
-// finer, the last row / column of a band also taking the extra row / column an
-// odd-sized finer band has.
+// Trees: the LL coefficients form 2x2 groups (Said & Pearlman): in the group
+// whose top-left root is at (2a, 2b), the root to its right owns the 2x2 block
+// at band position (2a.., 2b..) of the coarsest HL band, the root below it that
+// of LH, the diagonal root that of HH, and the top-left root owns nothing; a
+// group cut short by an odd LL extent hands a missing root's block to the root
+// that remains on the same row or column (the offset along the missing axis
+// becomes 0).  A detail coefficient at band position (a, b) has the 2x2 block
+// (2a.., 2b..) of the same orientation one level finer, the last row / column
+// of a band also taking the extra row / column an odd-sized finer band has.
 //
 // Encoder: the set maxima (max |s| over all descendants, and over descendants
 // beyond the children) come from one full-grid kernel per level, bottom up.
@@ -67,10 +71,18 @@ __device__ int children(const SG &g, uint32_t idx, uint32_t *c) {
     int i = (int)(idx / g.nx), j = (int)(idx - (uint32_t)i * g.nx), lev, o, n = 0;
     locate(g, i, j, lev, o);
     if (o == 0) {
+        const int gi = i & ~1, gj = j & ~1;  // the group's top-left root
+        const bool row2 = gi + 1 < g.h[g.L], col2 = gj + 1 < g.w[g.L];
+        // orientation oo's block goes to the root at offset (oo >= 2, oo != 2),
+        // an offset along a missing axis taken as 0
+#pragma unroll
         for (int oo = 1; oo <= 3; oo++) {
+            const int ri = gi + ((oo >= 2 && row2) ? 1 : 0), rj = gj + ((oo != 2 && col2) ? 1 : 0);
+            if (ri != i || rj != j) continue;
             int y0, x0, bh, bw;
             band_box(g, g.L, oo, y0, x0, bh, bw);
-            if (i < bh && j < bw) c[n++] = (uint32_t)(y0 + i) * g.nx + x0 + j;
+            for (int r = gi; r < gi + 2 && r < bh; r++)
+                for (int q = gj; q < gj + 2 && q < bw; q++) c[n++] = (uint32_t)(y0 + r) * g.nx + x0 + q;
         }
         return n;
     }
@@ -92,7 +104,10 @@ __device__ __forceinline__ bool has_L(const SG &g, uint32_t idx) {
     locate(g, i, j, lev, o);
     if (o != 0) return lev >= 3;
     if (g.L < 2) return false;
-    return (j < g.w[g.L - 1] - g.w[g.L]) || (i < g.h[g.L - 1] - g.h[g.L]);
+    // every coarsest-level detail coefficient has children when L >= 2, so an
+    // LL root has grandchildren exactly when it has children
+    uint32_t c[9];
+    return children(g, idx, c) > 0;
 }
 
 __device__ __forceinline__ uint32_t absi(int32_t v) { return (uint32_t)(v < 0 ? -v : v); }

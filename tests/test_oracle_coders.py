@@ -260,3 +260,84 @@ def test_spiht_empty_and_bit_counts():
     parent, nchild = O.spiht_parents(16, 16, L)
     n_sets = int((nchild[:hl, :wl] > 0).sum())
     assert enc.nmax == 0 and enc.nbits == hl * wl + 1 + n_sets
+
+
+def _bits(stream: bytes, n: int) -> str:
+    return "".join(f"{b:08b}" for b in stream)[:n]
+
+
+def test_spiht_said_pearlman_ll_groups():
+    """Said & Pearlman 1996 group the coarsest coefficients 2x2: the top-left
+    root of a group has no descendants and each other root has a 2x2 offspring
+    block in one band (right: HL, below: LH, diagonal: HH) at the group's
+    position.  On a 16x16 field with L = 2 the LL band is 4x4."""
+    parent, nchild = O.spiht_parents(16, 16, 2)
+    for i in range(4):
+        for j in range(4):
+            kids = sorted(int(k) for k in np.flatnonzero(parent.reshape(-1) == i * 16 + j))
+            if i % 2 == 0 and j % 2 == 0:
+                assert kids == []
+                continue
+            band_y = 4 if i % 2 else 0       # LH, HH below LL
+            band_x = 4 if j % 2 else 0       # HL, HH right of LL
+            a2, b2 = i - i % 2, j - j % 2
+            want = sorted((band_y + a2 + r) * 16 + band_x + b2 + c for r in (0, 1) for c in (0, 1))
+            assert kids == want, (i, j, kids, want)
+
+
+def test_spiht_odd_ll_groups():
+    """A 6x6 field with L = 1: LL is 3x3, and every detail band 3x3.  The
+    groups at LL (0,2), (2,0) and (2,2) lack their second column, row or both;
+    the offset along a missing axis falls back to 0, so:
+      (0,2) gets HL (0,5), (1,5);      (1,2) gets LH (3,2), (4,2) and HH (3,5), (4,5);
+      (2,0) gets LH (5,0), (5,1);      (2,1) gets HL (2,3), (2,4) and HH (5,3), (5,4);
+      (2,2) gets HL (2,5), LH (5,2), HH (5,5);
+    and the full groups follow the 2x2 rule."""
+    want = {
+        (0, 1): [(0, 3), (0, 4), (1, 3), (1, 4)],
+        (1, 0): [(3, 0), (3, 1), (4, 0), (4, 1)],
+        (1, 1): [(3, 3), (3, 4), (4, 3), (4, 4)],
+        (0, 2): [(0, 5), (1, 5)],
+        (1, 2): [(3, 2), (4, 2), (3, 5), (4, 5)],
+        (2, 0): [(5, 0), (5, 1)],
+        (2, 1): [(2, 3), (2, 4), (5, 3), (5, 4)],
+        (2, 2): [(2, 5), (5, 2), (5, 5)],
+    }
+    parent, nchild = O.spiht_parents(6, 6, 1)
+    for i in range(3):
+        for j in range(3):
+            kids = sorted(divmod(int(k), 6) for k in np.flatnonzero(parent.reshape(-1) == i * 6 + j))
+            assert kids == sorted(want.get((i, j), [])), (i, j, kids)
+    assert (parent[:3, :3] == -1).all() and (parent.reshape(-1) >= -1).all()
+
+
+def test_spiht_hand_worked_8x8():
+    """8x8, L = 2 (LL 2x2 at rows/cols 0-1; HL_2 rows 0-1 cols 2-3; LH_2 rows
+    2-3 cols 0-1; HH_2 rows 2-3 cols 2-3; HL_1, LH_1, HH_1 the 4x4 quadrants).
+    s = 5 at LL (1,1) and -3 at (6,5) in HH_1, zero elsewhere.  Trees: LL (1,1)
+    owns HH_2 (2..3, 2..3); HH_2 (3,2) owns HH_1 (6..7, 4..5).  nmax = 2.
+    LIP = LL row-major; LIS = (0,1)A, (1,0)A, (1,1)A ((0,0) has no descendants).
+
+    Plane 2 (T = 4): LIP 0,0,0,1 + sign 0; LIS (0,1)A 0, (1,0)A 0, (1,1)A 0
+    (its largest descendant is 3); no refinement.  8 bits.
+    Plane 1 (T = 2): LIP (0,0),(0,1),(1,0): 0,0,0.  LIS (0,1)A 0, (1,0)A 0;
+    (1,1)A 1, its children (2,2),(2,3),(3,2),(3,3) 0,0,0,0 (to the LIP), then
+    (1,1) goes to the end as type B; (1,1)B 1, its children appended as type A;
+    (2,2)A 0, (2,3)A 0, (3,2)A 1 with children (6,4) 0, (6,5) 1 + sign 1,
+    (7,4) 0, (7,5) 0 (level-1 nodes: no type B); (3,3)A 0.  Refinement of
+    (1,1): bit 1 of 5 = 0.  3 + 17 + 1 = 21 bits.
+    Plane 0 (T = 1): LIP of 10 entries, all 0; LIS (0,1)A, (1,0)A, (2,2)A,
+    (2,3)A, (3,3)A all 0; refinement of (1,1), (6,5): bit 0 of 5 = 1, of 3 = 1.
+    10 + 5 + 2 = 17 bits.  Total 46 bits."""
+    s = np.zeros((8, 8), np.int32)
+    s[1, 1] = 5
+    s[6, 5] = -3
+    enc = O.spiht_encode(s, 2)
+    p2 = "0001" + "0" + "000"
+    p1 = "000" + "0" + "0" + "1" + "0000" + "1" + "0" + "0" + "1" + "0" + "11" + "0" + "0" + "0" + "0"
+    p0 = "0" * 10 + "0" * 5 + "11"
+    assert (len(p2), len(p1), len(p0)) == (8, 21, 17)
+    assert enc.nmax == 2 and enc.nbits == 46
+    assert _bits(enc.stream, enc.nbits) == p2 + p1 + p0
+    assert enc.refine_start[2] == 8 and enc.refine_start[1] == 8 + 20 and enc.refine_start[0] == 8 + 21 + 15
+    assert enc.sig_pos[1, 1] == 4 and enc.sig_pos[6, 5] == 8 + 16  # the sign bits
