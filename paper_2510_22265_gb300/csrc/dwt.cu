@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(96) fwd_level(Live lv, const __grid_constant__
     const long long ncoef = r->N;
     const int hl = (hp + 1) >> 1, wl = (wp + 1) >> 1, ls = wl;
     const double mn = r->mn, inv = r->inv_range;
+    int *const gw = guard_word(*r);
     const int tid = threadIdx.x;
     __shared__ float t[EY][EX + 1];
     if (tid < EX) {  // column tid: all loads in flight, the four lifting steps and the scaling in registers
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(96) fwd_level(Live lv, const __grid_constant__
         for (int ly = 0; ly < EY; ly++) {
             const int gy = reflect(ty0 - HALO + ly, hp);
             const long long i = (long long)gy * ss + gx;
-            w[ly] = INBQ(i, (long long)hp * ss) ? src[i] : 0.0f;
+            w[ly] = INBS(i, (long long)hp * ss, gw) ? src[i] : 0.0f;
         }
         if (NORM) {
             const NormK k = make_norm_k(mn, inv);
@@ -117,10 +118,10 @@ __global__ void __launch_bounds__(96) fwd_level(Live lv, const __grid_constant__
         float v = t[HALO + 2 * rr + pv][HALO + 2 * c + ph];
         int oy = (gy >> 1) + (pv ? hl : 0), ox = (gx >> 1) + (ph ? wl : 0);
         if (!pv && !ph) {
-            if (ll && INBQ((long long)oy * ls + ox, (long long)hl * ls)) ll[(size_t)oy * ls + ox] = v;
-            if (last && INBQ((long long)oy * nx + ox, ncoef)) coef[(size_t)oy * nx + ox] = v;
+            if (ll && INBS((long long)oy * ls + ox, (long long)hl * ls, gw)) ll[(size_t)oy * ls + ox] = v;
+            if (last && INBS((long long)oy * nx + ox, ncoef, gw)) coef[(size_t)oy * nx + ox] = v;
         } else {
-            if (INBQ((long long)oy * nx + ox, ncoef)) coef[(size_t)oy * nx + ox] = v;
+            if (INBS((long long)oy * nx + ox, ncoef, gw)) coef[(size_t)oy * nx + ox] = v;
         }
     }
 }
@@ -160,7 +161,7 @@ __device__ __forceinline__ void block_count_fail_add(unsigned long long in, unsi
 // the last step of an inverse transform at point gi of field r
 __device__ __forceinline__ void finish_point(const InvFinal &fin, const FieldRun &r, float *dst, float v, long long gi,
                                              unsigned long long &cnt) {
-    if (!INBQ(gi, r.N)) return;
+    if (!INBS(gi, r.N, guard_word(r))) return;
     if (fin.mode <= 0) {
         if (fin.mode == 0 && fin.add_base) v = v + r.Abase[gi];
         dst[gi] = v;
@@ -217,7 +218,8 @@ __global__ void __launch_bounds__(IT, 12) inv_level(Live lv, const __grid_consta
     float *__restrict__ dst = l == 1 ? plane_ptr(*r, fin.dst) : ((l & 1) ? r->s2 : r->s1);
     const int ds = l == 1 ? nx : wp;
     constexpr int mode = MODE;
-    const int ncoef = (int)r->N;
+    const int ncoef = (int)r->N;  // a field has fewer than 2^31 points (checked on entry)
+    int *const gw = guard_word(*r);
     const int hl = (hp + 1) >> 1, wl = (wp + 1) >> 1;
     __shared__ float t[EY][EX + 1];
     // interior tile: the halo needs no reflection, every index is in range
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(IT, 12) inv_level(Live lv, const __grid_consta
             const int pv = gy & 1, sy = gy >> 1;
             const bool from_ll = !pv && !ph;
             const int i = from_ll ? sy * ls + sx : (sy + (pv ? hl : 0)) * nx + cx;
-            const bool ok = from_ll ? INBQ(i, lim_ll) : INBQ(i, ncoef);
+            const bool ok = from_ll ? INBS(i, lim_ll, gw) : INBS(i, ncoef, gw);
             const float *src = from_ll ? ll : coef;
             v[ly] = ok ? src[i] : 0.0f;
         }
@@ -299,7 +301,7 @@ __global__ void __launch_bounds__(IT, 12) inv_level(Live lv, const __grid_consta
 #pragma unroll
                 for (int rr = 0; rr < TY; rr++) {
                     const int i = (ty0 + rr) * ds + gx;
-                    if (rr < nr && INBQ(i, lim)) dst[i] = w[HALO + rr];
+                    if (rr < nr && INBS(i, lim, gw)) dst[i] = w[HALO + rr];
                 }
             } else if (mode == 1 && nr == TY) {  // base-loop count, full tile column
                 const float2 *__restrict__ bnd = r->bounds + (size_t)ty0 * nx + gx;
@@ -325,7 +327,7 @@ __global__ void __launch_bounds__(IT, 12) inv_level(Live lv, const __grid_consta
                     for (int u = 0; u < 8; u++) {
                         const int rr = g0 + u;
                         const int i = (ty0 + rr) * nx + gx;
-                        const bool ok = rr < nr && INBQ(i, ncoef);
+                        const bool ok = rr < nr && INBS(i, ncoef, gw);
                         bb[u] = ok ? bnd[i] : make_float2(1.0f, 0.0f);
                         av[u] = (mode == 2 && ok) ? ab[i] : 0.0f;
                     }

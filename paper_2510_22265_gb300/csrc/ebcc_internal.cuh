@@ -88,6 +88,7 @@ struct FieldScal {
     int es;                        // SPIHT step exponent of the current attempt
     int nseg;                      // PCRD hull segments of the field
     int ok;                        // decoder consistency flag
+    int guard;                     // bit 0: a range-checked index fell outside its buffer (access skipped)
     long long nbits;               // SPIHT stream length in bits
     long long T;                   // truncation (bits) under evaluation
     unsigned long long cnt[2];     // counters of the base loop and the truncation loop
@@ -290,7 +291,7 @@ struct T1Out {
     int32_t *tail_len;   // nblk * maxpass
     int64_t *dD;         // nblk * maxpass
     int64_t *D0;         // nblk
-    int32_t *status;     // bit 0 byte overflow, bit 1 too many passes
+    int32_t *status;     // bit 0 byte overflow, bit 1 too many passes, bit 2 (T1_GUARD) a range check missed
     // modelled symbols of blocks up to 32 x 32 (byte (ctx << 1) | bit), sym_cap
     // per block, and the symbol count at each pass end; null: serial coder
     uint8_t *sym;
@@ -301,6 +302,7 @@ struct T1Out {
     int32_t *order;
 };
 constexpr int MQ_ORDER_BINS = 1024;
+constexpr int T1_GUARD = 4;
 // symbol capacity per coefficient of a block: per bit-plane at most 1.5
 // symbols per coefficient (a run-length hit at the first row costs three for
 // one coefficient), planes K <= 26, plus one sign per coefficient
@@ -309,7 +311,7 @@ int t1_encode_blocks(int32_t *qt, const BlockDesc *blk, int nblk, int maxw, int 
                      int sign_magnitude_q, uint8_t *spp_out, long long nq, cudaStream_t st);
 int t1_decode_blocks(const uint8_t *bytes, const int64_t *off, const int32_t *len, const BlockDesc *blk,
                      const int32_t *K, const int32_t *npass, int nblk, int maxw, int maxh, float *coef,
-                     int32_t *mag, int8_t *plane, uint8_t *neg, long long nq, cudaStream_t st);
+                     int32_t *mag, int8_t *plane, uint8_t *neg, long long nq, int *guard, cudaStream_t st);
 
 // ------------------------------------------------------------ PCRD
 // Batch-wide arrays, indexed by global code-block (hull points) or by
@@ -447,9 +449,20 @@ __device__ __forceinline__ bool ebcc_inb(long long i, long long n, int line) {
 #else
 #define INB(i, n) true
 #endif
-// quiet form for hot loops (no report, so loads around it can be batched):
-// the caller skips or zero-fills the access when it is false
+// quiet form (no report, so loads around it can be batched): the caller skips
+// or zero-fills the access when it is false
 #define INBQ(i, n) ((unsigned long long)(long long)(i) < (unsigned long long)(long long)(n))
+// the quiet form that also records a miss: on the miss path only, one
+// atomicOr of `bit` into *word (when word is not null); the host turns a
+// recorded miss into a failed field (EBCC_ECUDA) instead of a wrong stream
+__device__ __forceinline__ bool inb_rec(long long i, long long n, int *word, int bit) {
+    if ((unsigned long long)i < (unsigned long long)n) return true;
+    if (word) atomicOr(word, bit);
+    return false;
+}
+#define INBS(i, n, word) inb_rec((long long)(i), (long long)(n), (word), 1)
+// a field's guard word (null for a field passed without its scalars)
+__device__ __forceinline__ int *guard_word(const FieldRun &r) { return r.sc ? &r.sc->guard : nullptr; }
 #endif
 
 // ------------------------------------------------------------ device helpers

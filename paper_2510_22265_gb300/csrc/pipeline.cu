@@ -879,7 +879,9 @@ void layout_compress(Arena &a, Batch &b, const std::vector<int> &ny, const std::
         r.s2 = carve<float>(a, scratch2(ny[f], nx[f]));
         uint8_t *spw = carve<uint8_t>(a, spiht_work_bytes(N));
         if (spw) spiht_work_carve(spw, N, &r.sw);
-        r.sp_cap = (8 * N + 4096 + 15) / 16 * 16;
+        // the encoder's trace holds bit offsets as 32-bit words: a stream
+        // longer than 2^32 bits fails with ECAPACITY instead
+        r.sp_cap = std::min((8 * N + 4096 + 15) / 16 * 16, (1LL << 29) - 16);
         r.sp = carve<uint8_t>(a, r.sp_cap);
         r.esc_cap = 4096;
         r.esc = carve<uint32_t>(a, 2 * r.esc_cap);
@@ -911,6 +913,7 @@ void layout_decompress(Arena &a, Batch &b, const std::vector<int> &ny, const std
     const size_t nb = (size_t)Btot + 1;
     b.t1.K = carve<int32_t>(a, nb);
     b.t1.pass_len = carve<int32_t>(a, nb);  // payload length per block
+    b.t1.status = carve<int32_t>(a, 4);     // T1_GUARD: a range check of the tier-1 decoder missed
     b.npass = carve<int32_t>(a, nb);
     b.addr = carve<int64_t>(a, nb);
     b.d_blk = carve<BlockDesc>(a, nb);
@@ -1230,7 +1233,7 @@ int compress_batch(Engine &e, const ebcc_field_desc *fd, int n, ebcc_out_desc *o
         int32_t *t1st = nullptr;
         RC(download(e, b.t1.status, 1, &t1st, st));
         if (*t1st) {
-            for (int f : A) status[f] = EBCC_ECAPACITY;
+            for (int f : A) status[f] = (*t1st & T1_GUARD) ? EBCC_ECUDA : EBCC_ECAPACITY;
             A.clear();
         }
         for (int f : A)
@@ -1327,12 +1330,20 @@ int compress_batch(Engine &e, const ebcc_field_desc *fd, int n, ebcc_out_desc *o
             PROF("escape_kernel", st, 0.0, escape_kernel<<<(int)X.size(), 1024, 0, st>>>(lv));
             CK(cudaGetLastError());
             RC(download(e, b.d_sc, F, &hs, st));
+            // more escapes than the list holds: the two-layer candidate is
+            // dropped, and the field keeps its base-only stream when it has
+            // one (such a two-layer stream would carry at least 8 bytes per
+            // escape); without one it fails with ECAPACITY
+            std::vector<char> gone(F, 0);
             for (int f : X) {
                 nesc[f] = hs[f].nesc;
-                if (nesc[f] > (unsigned long long)b.run[f].esc_cap) { status[f] = EBCC_ECAPACITY; drop[f] = 1; }
+                if (nesc[f] <= (unsigned long long)b.run[f].esc_cap) continue;
+                gone[f] = 1;
+                if (L1[f] != NOLEN) lost[f] = 1;
+                else { status[f] = EBCC_ECAPACITY; drop[f] = 1; }
             }
             remove_from(A, drop);
-            remove_from(Rl, drop);
+            remove_from(Rl, gone);
         }
     }
     if (!Rl.empty()) {
@@ -1409,6 +1420,11 @@ int compress_batch(Engine &e, const ebcc_field_desc *fd, int n, ebcc_out_desc *o
         CK(cudaGetLastError());
     }
     CK(cudaStreamSynchronize(st));
+    // ---- range checks that missed: such a field fails instead of returning a
+    // stream built around a skipped access
+    RC(download(e, b.d_sc, F, &hs, st));
+    for (int f = 0; f < F; f++)
+        if (hs[f].guard && !status[f]) status[f] = EBCC_ECUDA;
     // ---- outcomes
     for (int f = 0; f < F; f++) {
         ebcc_out_desc &o = od[vin[f]];
@@ -1545,6 +1561,7 @@ int decompress_batch(Engine &e, const ebcc_stream_desc *sd, int n, float *const 
         RC(upload(e, b.d_geom, b.geom.data(), F * sizeof(FieldGeom), st));
         RC(upload(e, b.d_sc, sc.data(), F * sizeof(FieldScal), st));
         RC(upload(e, b.d_blk, b.blk.data(), b.blk.size() * sizeof(BlockDesc), st));
+        CK(cudaMemsetAsync(b.t1.status, 0, sizeof(int32_t), st));
         const Live lv = live_of(b);
         std::vector<char> bad(F, 0);
         if (!D.empty()) {
@@ -1561,7 +1578,7 @@ int decompress_batch(Engine &e, const ebcc_stream_desc *sd, int n, float *const 
             remove_from(E, bad);
             // tier-1 of every code-block of the batch (failed fields decode nothing)
             RC(t1_decode_blocks(nullptr, b.addr, b.t1.pass_len, b.d_blk, b.t1.K, b.npass, blk0, maxw, maxh,
-                                b.run[0].W, nullptr, nullptr, nullptr, b.Ntot, st));
+                                b.run[0].W, nullptr, nullptr, nullptr, b.Ntot, b.t1.status, st));
             STAGE(st, "tier-1 decode");
         }
         if (!B1.empty()) {  // base layer only: IDWT, denormalise
@@ -1589,11 +1606,20 @@ int decompress_batch(Engine &e, const ebcc_stream_desc *sd, int n, float *const 
             PROF("fill_kernel", st, 0.0, fill_kernel<<<grid, 256, 0, st>>>(lv));
             CK(cudaGetLastError());
         }
-        if (!E.empty()) {
+        {
+            // escapes that did not parse, and range checks that missed (a
+            // field whose guard word is set failed instead of decoding wrongly)
             FieldScal *hs = nullptr;
+            int32_t *t1s = nullptr;
             RC(download(e, b.d_sc, F, &hs, st));
+            RC(download(e, b.t1.status, 1, &t1s, st));
             for (int f : E)
                 if (!hs[f].ok) status[vin[f]] = EBCC_ECORRUPT;
+            for (int f = 0; f < F; f++)
+                if (hs[f].guard && !status[vin[f]]) status[vin[f]] = EBCC_ECUDA;
+            if (*t1s & T1_GUARD)
+                for (int f : D)
+                    if (!status[vin[f]]) status[vin[f]] = EBCC_ECUDA;
         }
         CK(cudaStreamSynchronize(st));
     }

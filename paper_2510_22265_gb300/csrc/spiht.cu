@@ -122,6 +122,7 @@ __global__ void maxima_kernel(Live lv, const __grid_constant__ FieldRun one, int
     load_sg(g, *r);
     const int32_t *__restrict__ s = r->s;
     uint32_t *maxd = r->sw.maxd, *maxl = r->sw.maxl;
+    int *const gw = guard_word(*r);
     int nb = l == 0 ? 1 : 3;
     int y0s[3], x0s[3], bhs[3], bws[3];
     long cnt[4] = {0, 0, 0, 0};
@@ -140,12 +141,12 @@ __global__ void maxima_kernel(Live lv, const __grid_constant__ FieldRun one, int
         int n = children(g, idx, c);
         uint32_t md = 0, ml = 0;
         for (int q = 0; q < n; q++) {
-            if (!INBQ(c[q], (long long)g.ny * g.nx)) continue;
+            if (!INBS(c[q], (long long)g.ny * g.nx, gw)) continue;
             uint32_t cd = leaf_children ? 0u : maxd[c[q]];  // level-1 nodes have no descendants
             md = max(md, max(absi(s[c[q]]), cd));
             ml = max(ml, cd);
         }
-        if (!INBQ(idx, (long long)g.ny * g.nx)) continue;
+        if (!INBS(idx, (long long)g.ny * g.nx, gw)) continue;
         maxd[idx] = md;
         maxl[idx] = ml;
     }
@@ -209,8 +210,8 @@ __device__ __forceinline__ uint32_t bitmask(unsigned long long b) {
 __device__ __forceinline__ void win_clear(EncShared &sh) {
     for (int k = threadIdx.x; k < WIN_WORDS; k += ET) sh.win[k] = 0;
 }
-__device__ __forceinline__ void win_set(EncShared &sh, unsigned long long b) {
-    if (INBQ((long long)(b >> 5) - (long long)sh.wbase, WIN_WORDS)) atomicOr(&sh.win[(b >> 5) - sh.wbase], bitmask(b));
+__device__ __forceinline__ void win_set(EncShared &sh, unsigned long long b, int *gw) {
+    if (INBS((long long)(b >> 5) - (long long)sh.wbase, WIN_WORDS, gw)) atomicOr(&sh.win[(b >> 5) - sh.wbase], bitmask(b));
 }
 // The chunk's bits are [start_bit, end_bit).  When start_bit is not on a word
 // boundary the window's first word also holds bits of the chunk before (the
@@ -246,6 +247,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
     __shared__ SG g;
     if (threadIdx.x == 0) r->sc->spiht_status = 0;  // before the barrier in load_sg
     load_sg(g, *r);
+    int *const gw = guard_word(*r);
     const int32_t *__restrict__ s = r->s;
     const uint32_t *__restrict__ maxd = r->sw.maxd;
     const uint32_t *__restrict__ maxl = r->sw.maxl;
@@ -288,14 +290,14 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
         uint32_t idx = 0;
         if (k < nroot) {
             idx = (uint32_t)(k / wL) * g.nx + (uint32_t)(k % wL);
-            if (INBQ(k, NN)) lip[k] = make_uint2(idx, smag(s[idx]));
+            if (INBS(k, NN, gw)) lip[k] = make_uint2(idx, smag(s[idx]));
             uint32_t c[9];
             v[0] = children(g, idx, c) > 0;
         }
         block_scan(v, sh);
         if (k < nroot) {
             uint32_t c[9];
-            if (children(g, idx, c) > 0 && INBQ(sh.nlis + v[0], NN)) lis[sh.nlis + v[0]] = make_uint2(idx << 1, maxd[idx]);
+            if (children(g, idx, c) > 0 && INBS(sh.nlis + v[0], NN, gw)) lis[sh.nlis + v[0]] = make_uint2(idx << 1, maxd[idx]);
         }
         __syncthreads();
         if (tid == 0) sh.nlis += sh.tot[0];
@@ -319,8 +321,8 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                     const long long k = k0 + j;
                     uint2 x = make_uint2(0, 0);
                     if (k < nl) {
-                        if (INBQ(k, NN)) x = lip[k];
-                        if (!INBQ(x.x, NN)) x.x = 0;
+                        if (INBS(k, NN, gw)) x = lip[k];
+                        if (!INBS(x.x, NN, gw)) x.x = 0;
                         const bool sg = (x.y & 0x7FFFFFFFu) >= T;
                         sgm |= (unsigned)sg << j;
                         v[0] += 1 + sg; v[1] += !sg; v[2] += sg;
@@ -337,9 +339,9 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                     if (k0 + j >= nl) break;
                     const uint2 x = xs[j];
                     if ((sgm >> j) & 1) {
-                        win_set(sh, bp);
-                        if (x.y >> 31) win_set(sh, bp + 1);
-                        if (INBQ(ls, NN)) {
+                        win_set(sh, bp, gw);
+                        if (x.y >> 31) win_set(sh, bp + 1, gw);
+                        if (INBS(ls, NN, gw)) {
                             sig_pos[x.x] = (uint32_t)(bp + 1);
                             lsp_idx[x.x] = (uint32_t)ls;
                             lsp[ls] = make_uint2(x.x, x.y & 0x7FFFFFFFu);
@@ -347,7 +349,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                         ls++;
                         bp += 2;
                     } else {
-                        if (INBQ(keep, NN)) lip[keep] = x;
+                        if (INBS(keep, NN, gw)) lip[keep] = x;
                         keep++;
                         bp += 1;
                     }
@@ -375,19 +377,19 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                 __syncthreads();
                 // each thread's entry of the next chunk is read one chunk ahead
                 uint2 e_next = make_uint2(0, 0);
-                if (tid < ncur && INBQ(tid, NN)) e_next = cur[tid];
+                if (tid < ncur && INBS(tid, NN, gw)) e_next = cur[tid];
                 for (long long base = 0; base < ncur; base += ET) {
                     const long long k = base + tid;
                     int v[NQ] = {0, 0, 0, 0, 0};
                     uint2 e = e_next;
-                    if (k + ET < ncur && INBQ(k + ET, NN)) e_next = cur[k + ET];
+                    if (k + ET < ncur && INBS(k + ET, NN, gw)) e_next = cur[k + ET];
                     uint32_t c[9];
                     int32_t sv[9];
                     int nc = 0;
                     bool sg = false;
                     uint32_t sigmask = 0, mlv = 0;
                     if (k < ncur) {
-                        if (!INBQ(e.x >> 1, NN)) e.x = 0;
+                        if (!INBS(e.x >> 1, NN, gw)) e.x = 0;
                         const uint32_t idx = e.x >> 1;
                         v[0] = 1;
                         sg = e.y >= T;
@@ -395,7 +397,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                             if (sg) {
                                 nc = children(g, idx, c);
                                 for (int q = 0; q < nc; q++) {
-                                    if (!INBQ(c[q], NN)) c[q] = 0;
+                                    if (!INBS(c[q], NN, gw)) c[q] = 0;
                                     sv[q] = s[c[q]];
                                     const bool cs = absi(sv[q]) >= T;
                                     sigmask |= (uint32_t)cs << q;
@@ -411,7 +413,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                                 nc = children(g, idx, c);
                                 v[3] = nc;
                                 for (int q = 0; q < nc; q++)  // the next wave's type-A entries' maxima, read now
-                                    sv[q] = (int32_t)maxd[INBQ(c[q], NN) ? c[q] : 0];
+                                    sv[q] = (int32_t)maxd[INBS(c[q], NN, gw) ? c[q] : 0];
                             } else {
                                 v[4] = 1;
                             }
@@ -424,31 +426,31 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                         const uint32_t idx = e.x >> 1;
                         unsigned long long bp = sh.pos + v[0];
                         if (!sg) {
-                            if (INBQ(sh.nstay + v[4], NN)) lis_new[sh.nstay + v[4]] = e;
+                            if (INBS(sh.nstay + v[4], NN, gw)) lis_new[sh.nstay + v[4]] = e;
                         } else if ((e.x & 1) == 0) {
-                            win_set(sh, bp++);
+                            win_set(sh, bp++, gw);
                             long long li = sh.nlip + v[1], ls = sh.nlsp + v[2];
                             for (int q = 0; q < nc; q++) {
                                 if ((sigmask >> q) & 1) {
-                                    win_set(sh, bp);
-                                    if (sv[q] < 0) win_set(sh, bp + 1);
+                                    win_set(sh, bp, gw);
+                                    if (sv[q] < 0) win_set(sh, bp + 1, gw);
                                     sig_pos[c[q]] = (uint32_t)(bp + 1);
                                     lsp_idx[c[q]] = (uint32_t)ls;
-                                    if (INBQ(ls, NN)) lsp[ls] = make_uint2(c[q], absi(sv[q]));
+                                    if (INBS(ls, NN, gw)) lsp[ls] = make_uint2(c[q], absi(sv[q]));
                                     ls++;
                                     bp += 2;
                                 } else {
-                                    if (INBQ(li, NN)) lip[li] = make_uint2(c[q], smag(sv[q]));
+                                    if (INBS(li, NN, gw)) lip[li] = make_uint2(c[q], smag(sv[q]));
                                     li++;
                                     bp += 1;
                                 }
                             }
-                            if (has_L(g, idx) && INBQ(sh.nnext + v[3], NN))
+                            if (has_L(g, idx) && INBS(sh.nnext + v[3], NN, gw))
                                 nxt[sh.nnext + v[3]] = make_uint2((idx << 1) | 1, mlv);
                         } else {
-                            win_set(sh, bp);
+                            win_set(sh, bp, gw);
                             for (int q = 0; q < nc; q++)
-                                if (INBQ(sh.nnext + v[3] + q, NN)) nxt[sh.nnext + v[3] + q] = make_uint2(c[q] << 1, (uint32_t)sv[q]);
+                                if (INBS(sh.nnext + v[3] + q, NN, gw)) nxt[sh.nnext + v[3] + q] = make_uint2(c[q] << 1, (uint32_t)sv[q]);
                         }
                     }
                     __syncthreads();
@@ -485,7 +487,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
 #pragma unroll
                 for (int j = 0; j < EPL; j++) {
                     const long long k = k0 + j;
-                    if (k < lsp_before && INBQ(k, NN) && ((lsp[k].y >> n) & 1)) win_set(sh, sh.pos + k);
+                    if (k < lsp_before && INBS(k, NN, gw) && ((lsp[k].y >> n) & 1)) win_set(sh, sh.pos + k, gw);
                 }
                 __syncthreads();
                 const long long end = base + (long long)ET * EPL < lsp_before ? base + (long long)ET * EPL : lsp_before;

@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(WARPS * 32) t1_encode_kernel(int32_t *qt, cons
         uint32_t mx = 0;
         for (int i = lane; i < n; i += 32) {
             int r = i / w, c = i - r * w;
-            int32_t v = INBQ(d.off + (int64_t)r * d.stride + c, nq) ? qt[d.off + (int64_t)r * d.stride + c] : 0;
+            int32_t v = inb_rec(d.off + (int64_t)r * d.stride + c, nq, o.status, T1_GUARD) ? qt[d.off + (int64_t)r * d.stride + c] : 0;
             // sign-magnitude Mallat array (bit 31 sign, bit 30 trace flag) or two's complement
             uint32_t m = mark_spp_in_q ? (uint32_t)v & 0x3FFFFFFFu : (uint32_t)(v < 0 ? -v : v);
             mag[i] = m | (v < 0 ? 0x80000000u : 0);
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(WARPS * 32) t1_encode_kernel(int32_t *qt, cons
                 auto end_pass = [&](int64_t dd) {
                     uint32_t tail;
                     int tl;
-                    if (!INBQ(pass, o.maxpass)) return;
+                    if (!inb_rec(pass, o.maxpass, o.status, T1_GUARD)) return;
                     o.pass_len[pb + pass] = e.trunc(tail, tl);
                     o.tail[pb + pass] = tail;
                     o.tail_len[pb + pass] = tl;
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(WARPS * 32) t1_encode_kernel(int32_t *qt, cons
             uint32_t f = (mag[i] >> 30) & 1;
             if (mark_spp_in_q) {
                 int64_t at = d.off + (int64_t)r * d.stride + c;
-                if (INBQ(at, nq)) qt[at] = (qt[at] & ~0x40000000) | (int32_t)(f << 30);
+                if (inb_rec(at, nq, o.status, T1_GUARD)) qt[at] = (qt[at] & ~0x40000000) | (int32_t)(f << 30);
             }
             if (spp_out) spp_out[(size_t)b * n + i] = (uint8_t)f;
         }
@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(PW * 32, 8) t1_model_warp(int32_t *qt, const B
             m[r] = 0;
             if (lane < w && r < h) {
                 const long long at = d.off + (long long)r * d.stride + lane;
-                const int32_t v = INBQ(at, nq) ? qt[at] : 0;
+                const int32_t v = inb_rec(at, nq, o.status, T1_GUARD) ? qt[at] : 0;
                 m[r] = mark_spp_in_q ? ((uint32_t)v & 0x3FFFFFFFu) : (uint32_t)(v < 0 ? -v : v);
                 NGM |= (uint64_t)(v < 0) << r;
                 mx = max(mx, m[r]);
@@ -726,7 +726,7 @@ __global__ void __launch_bounds__(PW * 32, 8) t1_model_warp(int32_t *qt, const B
             if (lane < w && r < h) {
                 const uint32_t f = (uint32_t)((SPPF >> r) & 1);
                 const long long at = d.off + (long long)r * d.stride + lane;
-                if (mark_spp_in_q && INBQ(at, nq)) qt[at] = (qt[at] & ~0x40000000) | (int32_t)(f << 30);
+                if (mark_spp_in_q && inb_rec(at, nq, o.status, T1_GUARD)) qt[at] = (qt[at] & ~0x40000000) | (int32_t)(f << 30);
                 if (spp_out) spp_out[(size_t)b * (w * h) + r * w + lane] = (uint8_t)f;
             }
         }
@@ -876,7 +876,8 @@ __global__ void __launch_bounds__(WARPS * 32) t1_decode_kernel(const uint8_t *by
                                                                const int32_t *len, const BlockDesc *blk,
                                                                const int32_t *Kb, const int32_t *npb, int nblk,
                                                                float *coef, int32_t *omag, int8_t *oplane,
-                                                               uint8_t *oneg, SmemLayout SL, int maxh, long long nq) {
+                                                               uint8_t *oneg, SmemLayout SL, int maxh, long long nq,
+                                                               int *guard) {
     extern __shared__ __align__(16) uint8_t sm[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint8_t *base = sm + wid * SL.per_warp;
@@ -1006,7 +1007,7 @@ __global__ void __launch_bounds__(WARPS * 32) t1_decode_kernel(const uint8_t *by
             uint32_t m = mag[i];
             if (coef) {
                 float val = p >= 0 ? deq(m, p, d.delta) : 0.0f;
-                if (INBQ(d.off + (int64_t)r * d.stride + c, nq)) coef[d.off + (int64_t)r * d.stride + c] = ng ? -val : val;
+                if (inb_rec(d.off + (int64_t)r * d.stride + c, nq, guard, T1_GUARD)) coef[d.off + (int64_t)r * d.stride + c] = ng ? -val : val;
             } else {
                 omag[(size_t)b * n + i] = p >= 0 ? (int32_t)m : 0;
                 oplane[(size_t)b * n + i] = (int8_t)p;
@@ -1135,14 +1136,14 @@ int t1_encode_blocks(int32_t *qt, const BlockDesc *blk, int nblk, int maxw, int 
 
 int t1_decode_blocks(const uint8_t *bytes, const int64_t *off, const int32_t *len, const BlockDesc *blk,
                      const int32_t *K, const int32_t *npass, int nblk, int maxw, int maxh, float *coef, int32_t *mag,
-                     int8_t *plane, uint8_t *neg, long long nq, cudaStream_t st) {
+                     int8_t *plane, uint8_t *neg, long long nq, int *guard, cudaStream_t st) {
     int rc = upload_tables();
     if (rc) return rc;
     if (nblk <= 0) return EBCC_OK;
     if (maxw > 64 || maxh > 64) return EBCC_EINVAL;
     SmemLayout SL = smem_layout(maxw * maxh, maxh, true);
     PROF("t1_decode_kernel", st, 0.0, t1_decode_kernel<<<grid_for(nblk), WARPS * 32, WARPS * SL.per_warp, st>>>(bytes, off, len, blk, K, npass, nblk,
-                                                                             coef, mag, plane, neg, SL, maxh, nq););
+                                                                             coef, mag, plane, neg, SL, maxh, nq, guard););
     CK(cudaGetLastError());
     return EBCC_OK;
 }

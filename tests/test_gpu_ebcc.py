@@ -165,3 +165,30 @@ def test_high_resolution_spiky_field(B):
     s, st = B.ebcc_compress(x, 1e-2)
     assert _within(x, B.ebcc_decompress(s, *x.shape), eps)
     assert _within(x, O.decompress(s, *x.shape), eps)
+
+
+def test_output_capacity_reported_per_field(B):
+    """A field whose caller-owned output buffer is too small for its stream
+    fails alone with ECAPACITY; the other fields of the batch are unaffected."""
+    fields = [synth.smooth_field(91, 180, seed=s) for s in (21, 22, 23)]
+    outs = [torch.empty(B.ebcc_max_stream_bytes(91, 180), dtype=torch.uint8, device="cuda") for _ in fields]
+    outs[1] = torch.empty(80, dtype=torch.uint8, device="cuda")  # header + a few bytes
+    rc, res = B.ebcc_compress_batch_dev([torch.from_numpy(f).cuda() for f in fields], [1e-3] * 3, outs=outs)
+    assert rc == B.EBCC_ECAPACITY
+    assert [r[2] for r in res] == [0, B.EBCC_ECAPACITY, 0]
+    for k in (0, 2):
+        assert bytes(res[k][0][:res[k][1]].cpu().numpy()) == B.ebcc_compress(fields[k], 1e-3)[0]
+
+
+def test_escape_overflow_keeps_base_only_stream(B):
+    """A SPIHT step so coarse (guard bits -20) that the residual layer codes
+    nothing leaves tens of thousands of points to the escape list, beyond its
+    4096 entries: the field keeps its base-only (q = 1) stream, which meets
+    the bound, instead of failing or returning a wrong stream."""
+    x = synth.smooth_field(256, 256, seed=11, spikes=0.3)
+    p = B.params(guard_bits=-20, q=0.5)
+    s, st = B.ebcc_compress(x, 1e-3, B.EBCC_BOUND_REL, p)
+    assert st["used_fallback"] == 1 and st["n_escape"] == 0
+    eps = 1e-3 * (float(x.max()) - float(x.min()))
+    assert _within(x, O.decompress(s, *x.shape), eps)
+    assert _within(x, B.ebcc_decompress(s, *x.shape), eps)
