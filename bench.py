@@ -1,22 +1,34 @@
 """Benchmark of the EBCC hot path on GB300 (one JSON line on stdout).
 
-Workload (default): the ERA5-shaped stack -- 4 variables x 37 pressure levels
-of 721 x 1440 float32 fields (614.6 MB) -- compressed at a 1% range-relative
-bound, the configuration the headline metric is quoted on.  A step compresses
-every field of the stack once (the whole hot path: normalisation, DWT,
-quantisation, tier-1, both feedback loops, residual SPIHT layer, fallback,
-packing) with the inputs resident in HBM; inputs are larger than L2.
+Workload (headline): the ERA5-shaped stack -- 4 variables x 37 pressure levels
+of 721 x 1440 float32 fields (614.6 MB, larger than L2) -- compressed at a 1%
+range-relative bound through the device batch call, inputs resident in HBM.
+A step compresses every field of the stack once (the whole hot path:
+normalisation, DWT, quantisation, tier-1, both feedback loops, residual SPIHT
+layer, fallback, packing).
 
-Also reported: decompression GB/s of the produced streams, compression ratio,
-an end-to-end figure (every step copies the stack in from pinned host memory,
-runs the batch call and copies every stream back, all inside the timed region),
-the single-field host API for context, the oracle timed on the host cores on a
-bounded sample, and the roofline of the dominant kernel from the library's
-CUDA events around its launches, recorded in a profiled pass after the timed
-steps (the timed steps run without them).
+Also in the line:
+* e2e: the same stack through the host-buffer batch call (pinned host fields
+  in, streams back to pinned host buffers, every copy inside the call);
+* decompression GB/s of the produced streams; the plain path (one field per
+  call); the stack at the 0.1% and 10% bounds; per-variable CR, residual-layer
+  use and loop iterations;
+* precision per field: max |x - x_hat| / eps and RMSE of the GPU decode, the
+  largest difference between the GPU decode and the FP64 oracle's decode of
+  the same stream (every field), and the GPU CR against the oracle's CR on the
+  fields the oracle compresses for the CPU baseline;
+* the uneven batch (512 fields of 91x180 .. 1441x2880, bounds log-uniform in
+  0.1-10%), the high-resolution batch (24 x 3601x7200 with 1% heavy-tailed
+  spikes) against one field per call, and the single 181x360 field;
+* the q / r0 ablation over the stack (CR relative to q = 1 per field, the
+  per-field best q of the grid, r0 from 5 to 80);
+* the serving leg (Poisson arrivals through the batching server);
+* the roofline of the dominant kernel from the library's CUDA events and its
+  device-counted bytes, in a profiled pass after the timed steps;
+* the oracle timed on the host cores on whole fields of the stack.
 
---impl reference times the CPU oracle itself on a bounded sample of the same
-workload (the only other place this file runs the oracle).
+--impl reference times the CPU oracle itself on the same whole-field sample
+(the only other place this file runs the oracle).
 """
 from __future__ import annotations
 
@@ -37,12 +49,13 @@ sys.path.insert(0, ROOT)
 from paper_2510_22265_gb300 import synth  # noqa: E402
 
 METRIC = "compress/decompress GB/s at 1% rel bound (batched vs plain); CR; p99 latency"
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) that ncu measured for the
-# dominant kernel on the default workload, averaged over the launches of one compression step
-# (profiles/launches_compress_era5_148x721x1440.md); reported only for that workload
-NCU_TRAFFIC = {"inv_level": 248.3e6}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) measured by ncu for the
+# dominant kernel as it stands, averaged over the launches of one compression step of the default
+# workload (profiles/); None until the current kernel has been captured
+NCU_TRAFFIC = {}
 DEFAULT_SHAPE = [4, 37, 721, 1440]
 BOUND = 1e-2
+FALLBACK_HBM_GBS = 6800.0
 
 
 def workload_fields(n_vars=4, n_levels=37, ny=721, nx=1440):
@@ -53,13 +66,39 @@ def workload_fields(n_vars=4, n_levels=37, ny=721, nx=1440):
     return out
 
 
-# ------------------------------------------------------------------ CPU oracle leg
+def sample_ids(cores, n_vars=4, n_levels=37):
+    """Whole fields of the stack the oracle compresses, one per core, spread
+    over the variables and levels: (variable, level) pairs."""
+    return [(k % n_vars, (k * n_levels) // max(1, cores)) for k in range(cores)]
+
+
+def _era5_one(args):
+    v, lev, ny, nx = args
+    return synth.era5_like(v, lev, ny, nx)
+
+
+def _batch_one(args):
+    grid, seed = args
+    return synth.batch_field(grid, seed)
+
+
+def _hires_one(seed):
+    return synth.smooth_field(3601, 7200, seed=seed, kscale=4.0, spikes=0.01)
+
+
+# ------------------------------------------------------------------ CPU oracle work
 def _oracle_one(args):
     x, bound = args
     import oracle as O
     t = time.perf_counter()
-    s, _ = O.compress(x, bound, 1)
+    s, st = O.compress(x, bound, 1)
     return time.perf_counter() - t, x.nbytes, len(s)
+
+
+def _oracle_decode(args):
+    s, ny, nx = args
+    import oracle as O
+    return O.decompress(s, ny, nx)
 
 
 def max_over_ranks(t_ms, dist, device):
@@ -85,7 +124,7 @@ def per_step(prof, n):
 
 
 def workload_config(shape):
-    """The workload both arms name: the stack, its bound and how L2 is kept cold."""
+    """The workload the GPU arm times: the stack, its bound and how L2 is kept cold."""
     n, (ny, nx) = shape[0] * shape[1], shape[2:]
     raw = n * ny * nx * 4
     return {"workload": f"ERA5-shaped stack: {n} fields of {ny}x{nx} float32 at 1% range-relative bound, "
@@ -93,19 +132,25 @@ def workload_config(shape):
             "l2": f"inputs {raw / 1e6:.1f} MB " + ("> 129 MB L2" if raw > 129e6 else "(fit in L2)")}
 
 
-def oracle_sample(fields, bound, cores, crop=(361, 720)):
-    """Oracle compression of a bounded sample: the first `cores` fields of the
-    workload cropped to `crop`, one per process (spawned)."""
-    sample = [np.ascontiguousarray(f[:crop[0], :crop[1]]) for f in fields[:cores]]
-    ctx = mp.get_context("spawn")
+def sample_config(shape, cores):
+    """The workload the oracle times: whole fields of the same stack, one per core."""
+    ids = sample_ids(cores, shape[0], shape[1])
+    ny, nx = shape[2:]
+    return {"workload": f"ERA5-shaped stack sample: {len(ids)} whole {ny}x{nx} float32 fields (variable, level) "
+                        f"{ids} at 1% range-relative bound, FP64 oracle, one field per host core",
+            "fields": len(ids), "raw_bytes": len(ids) * ny * nx * 4, "of_stack": workload_config(shape)["workload"]}
+
+
+def oracle_sample(pool, fields_by_id, ids, bound):
+    """Oracle compression of whole fields, one per process of `pool` (spawned)."""
     t = time.perf_counter()
-    with ctx.Pool(cores) as pool:
-        res = pool.map(_oracle_one, [(x, bound) for x in sample])
+    res = pool.map(_oracle_one, [(fields_by_id[i], bound) for i in ids])
     wall = time.perf_counter() - t
     raw = sum(r[1] for r in res)
-    return {"value": raw / wall / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
-            "sample": f"{len(sample)} fields of the workload cropped to {crop[0]}x{crop[1]}, one per process, "
-                      f"{wall:.1f} s wall", "cr": raw / sum(r[2] for r in res)}
+    return {"value": raw / wall / 1e9, "unit": "GB/s", "cores": len(ids), "kind": "oracle",
+            "sample": f"{len(ids)} whole fields (variable, level) {ids} of the stack, one per process, "
+                      f"{wall:.1f} s wall", "cr": raw / sum(r[2] for r in res),
+            "field_cr": {f"{v},{lev}": r[1] / r[2] for (v, lev), r in zip(ids, res)}}
 
 
 # ------------------------------------------------------------------ clocks
@@ -147,6 +192,104 @@ class Clocks:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+# ------------------------------------------------------------------ helpers
+def timed_batch(B, torch, fields, bounds, outs, steps, stream):
+    """Device time per batch call (CUDA events on the launching stream) and the last result."""
+    rc, res = B.ebcc_compress_batch_dev(fields, bounds, outs=outs, stream=stream.cuda_stream)
+    assert rc == 0, rc
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        rc, res = B.ebcc_compress_batch_dev(fields, bounds, outs=outs, stream=stream.cuda_stream)
+        assert rc == 0, rc
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, res
+
+
+def timed_plain(B, torch, fields, bounds, outs, stream):
+    """One field per call over the given fields; device ms in total."""
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for f, b, o in zip(fields, bounds, outs):
+        rc, _ = B.ebcc_compress_batch_dev([f], [b], outs=[o], stream=stream.cuda_stream)
+        assert rc == 0, rc
+    p1.record(stream)
+    torch.cuda.synchronize()
+    return p0.elapsed_time(p1)
+
+
+def loop_stats(res):
+    """Share of fields whose stream carries a residual layer or is base-only,
+    and mean evaluations of the two base loops and of the truncation search."""
+    st = [r[3] for r in res]
+    return {"residual_frac": float(np.mean([s["res_bytes"] > 0 for s in st])),
+            "fallback_frac": float(np.mean([s["used_fallback"] for s in st])),
+            "iters_base": float(np.mean([s["iters_base"] for s in st])),
+            "iters_base1": float(np.mean([s["iters_base1"] for s in st])),
+            "iters_trunc": float(np.mean([s["iters_trunc"] for s in st]))}
+
+
+def per_variable(res, raw_per_field, n_vars, n_levels):
+    out = {}
+    for v in range(n_vars):
+        rr = res[v * n_levels:(v + 1) * n_levels]
+        out[f"var{v}"] = {"cr": raw_per_field * len(rr) / sum(r[1] for r in rr), **loop_stats(rr)}
+    return out
+
+
+def summary(v):
+    v = np.asarray(v, np.float64)
+    return {"worst": float(v.max()), "median": float(np.median(v))}
+
+
+# ------------------------------------------------------------------ q / r0 ablation
+ABL_Q = [0.999, 0.9995, 0.9999, 0.99995, 0.99999, 1.0]
+ABL_BOUNDS = [1e-3, 1e-2, 1e-1]
+ABL_R0 = [5.0, 10.0, 20.0, 40.0, 80.0]
+
+
+def ablation_leg(B, torch, dfields, outs, stream):
+    """The paper's ablation (Materials and Methods, ablation study): every
+    field compressed with q from 1 - 1e-3 to 1 at 0.1%, 1% and 10% bounds, the
+    CR relative to the base layer alone (q = 1, the fallback's stream) per
+    field (quantiles as in the violin plot: max, 0.999, 0.99, 0.9, median);
+    the per-field best q of the grid (auto-q: the shortest stream over the
+    grid) against the default q; and r0 from 5 to 80 at 1% (CR, loop
+    evaluations)."""
+    n = len(dfields)
+    raw = np.array([f.numel() * 4 for f in dfields], np.float64)
+    out = {"q_grid": ABL_Q, "bounds": {}, "r0": {}}
+    for b in ABL_BOUNDS:
+        lens, base_only = {}, None
+        for q in ABL_Q:
+            rc, res = B.ebcc_compress_batch_dev(dfields, [b] * n, outs=outs, p=B.params(q=q),
+                                                stream=stream.cuda_stream)
+            assert rc == 0, rc
+            lens[q] = np.array([r[1] for r in res], np.float64)
+            if q == 1.0:
+                base_only = np.array([r[3]["len_one"] or r[1] for r in res], np.float64)
+        rel = {f"{q:g}": base_only / lens[q] for q in ABL_Q}
+        best = np.min(np.stack([lens[q] for q in ABL_Q]), axis=0)
+        out["bounds"][f"{b:g}"] = {
+            "cr_base_only": float(raw.sum() / base_only.sum()),
+            "rel_cr_vs_q1": {q: {"max": float(v.max()), "q0.999": float(np.quantile(v, 0.999)),
+                                 "q0.99": float(np.quantile(v, 0.99)), "q0.9": float(np.quantile(v, 0.9)),
+                                 "median": float(np.median(v)), "min": float(v.min())} for q, v in rel.items()},
+            "auto_q_cr": float(raw.sum() / best.sum()),
+            "default_q_cr": float(raw.sum() / lens[0.999].sum()),
+            "auto_q_choice": {f"{q:g}": int(np.sum(lens[q] == best)) for q in ABL_Q}}
+    for r0 in ABL_R0:
+        rc, res = B.ebcc_compress_batch_dev(dfields, [BOUND] * n, outs=outs, p=B.params(r0=r0),
+                                            stream=stream.cuda_stream)
+        assert rc == 0, rc
+        out["r0"][f"{r0:g}"] = {"cr": float(raw.sum() / sum(r[1] for r in res)), **loop_stats(res)}
+    out["what"] = "every field of the stack; relative CR = CR(q) / CR(q = 1) per field"
+    return out
+
+
 # ------------------------------------------------------------------ serving
 def serving_leg(B, fields, rate, window, budget_gb, max_batch):
     """Poisson stream of mixed requests (70% compress, 30% decompress of streams
@@ -186,64 +329,35 @@ def serving_leg(B, fields, rate, window, budget_gb, max_batch):
     return {"rate_req_s": rate, "window_s": window, "requests": len(arrivals),
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "queue_p50_ms": float(np.percentile(np.array(qs) * 1e3, 50)),
-            "sustained_gbs": raw / wall / 1e9, "hbm_budget_gb": budget_gb, "max_batch": max_batch,
+            "sustained_gbs": raw / wall / 1e9, "offered_gbs": raw / window / 1e9,
+            "hbm_budget_gb": budget_gb, "max_batch": max_batch,
             "what": "721x1440 fields, 70% compress / 30% decompress, bounds {0.1,1,10}%, Poisson arrivals, "
                     "latency = submit to result inside the library"}
 
 
-# ------------------------------------------------------------------ uneven batch
-def uneven_leg(B, torch, n, steps, warmup, plain_fields):
-    """Fields of uneven grids (91x180 .. 1441x2880) with log-uniform bounds in
-    [0.1%, 10%], all in one batch call; against one field per call on a subset."""
-    spec = synth.batch_spec(n, seed=3)
-    fields = [torch.from_numpy(synth.batch_field(g, sd)).cuda() for g, _, sd in spec]
-    bounds = [b for _, b, _ in spec]
-    caps = [B.ebcc_max_stream_bytes(*f.shape) for f in fields]
-    outs = [torch.empty(c, dtype=torch.uint8, device="cuda") for c in caps]
-    stream = torch.cuda.current_stream()
-    raw = sum(f.numel() * 4 for f in fields)
-    for _ in range(warmup):
-        rc, res = B.ebcc_compress_batch_dev(fields, bounds, outs=outs, stream=stream.cuda_stream)
-        assert rc == 0, rc
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        rc, res = B.ebcc_compress_batch_dev(fields, bounds, outs=outs, stream=stream.cuda_stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t = e0.elapsed_time(e1) / steps / 1e3
-    k = min(n, plain_fields)
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p0.record(stream)
-    for i in range(k):
-        rc, _ = B.ebcc_compress_batch_dev([fields[i]], [bounds[i]], outs=[outs[i]], stream=stream.cuda_stream)
-    p1.record(stream)
-    torch.cuda.synchronize()
-    praw = sum(f.numel() * 4 for f in fields[:k])
-    return {"fields": n, "raw_bytes": raw, "compress_gbs": raw / t / 1e9, "ms_per_step": t * 1e3,
-            "plain_compress_gbs": praw / (p0.elapsed_time(p1) / 1e3) / 1e9, "plain_fields": k,
-            "cr": raw / sum(r[1] for r in res),
-            "what": "grids drawn from 91x180..1441x2880, bounds log-uniform in [0.1%, 10%], one batch call"}
-
-
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
-    import torch
-    from paper_2510_22265_gb300 import binding as B
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
+    ncpu = os.cpu_count() or 1
+    cores = max(1, min(16, ncpu))
+    # the process pool (spawned) serves input generation and the oracle legs;
+    # it is created before the first GPU call
+    pool = mp.get_context("spawn").Pool(cores)
+    nv, nl, ny, nx = args.shape
+    fields = pool.map(_era5_one, [(v, lev, ny, nx) for v in range(nv) for lev in range(nl)])
+    ids = [(v, lev) for v, lev in sample_ids(cores, nv, nl)]
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = oracle_sample(pool, {(v, lev): fields[v * nl + lev] for v, lev in ids}, ids, BOUND)
+    import torch
+    from paper_2510_22265_gb300 import binding as B
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
-    cores = max(1, min(8, os.cpu_count() or 1))
-    fields = workload_fields(*args.shape)
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = oracle_sample(fields, BOUND, cores)  # before the first GPU call (spawned pool)
     dfields = [torch.from_numpy(f).cuda() for f in fields]
     n = len(dfields)
     raw_bytes = sum(f.numel() * 4 for f in dfields)
@@ -283,105 +397,154 @@ def run_gpu(args):
     prof = per_step(B.profile_read(), n_prof)
     t_ms = max_over_ranks(t_ms, dist, "cuda")
     comp_bytes = sum(r[1] for r in res)
+    streams_host = [bytes(r[0][:r[1]].cpu().numpy()) for r in res]
     # the plain path: one field per call (every launch covers one field), on a
     # bounded subset of the same fields
     n_plain = min(n, args.plain_fields)
-    torch.cuda.synchronize()
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p0.record(stream)
-    for i in range(n_plain):
-        rc, _ = B.ebcc_compress_batch_dev([dfields[i]], [BOUND], outs=[outs[i]], stream=stream.cuda_stream)
-        assert rc == 0, rc
-    p1.record(stream)
-    torch.cuda.synchronize()
-    plain_bytes = sum(f.numel() * 4 for f in dfields[:n_plain])
-    plain_gbs = plain_bytes / (p0.elapsed_time(p1) / 1e3) / 1e9
+    plain_ms = timed_plain(B, torch, dfields[:n_plain], bounds[:n_plain], outs[:n_plain], stream)
+    plain_gbs = sum(f.numel() * 4 for f in dfields[:n_plain]) / (plain_ms / 1e3) / 1e9
     # decompression of the produced streams (device-resident, one batch)
-    step()
-    torch.cuda.synchronize()
     douts = [torch.empty_like(f) for f in dfields]
     lens = [r[1] for r in res]
     shapes = [tuple(f.shape) for f in dfields]
-    assert B.ebcc_decompress_batch_dev([r[0] for r in res], lens, shapes, douts) == 0
+    dstreams = [r[0] for r in res]
+    assert B.ebcc_decompress_batch_dev(dstreams, lens, shapes, douts) == 0
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        assert B.ebcc_decompress_batch_dev([r[0] for r in res], lens, shapes, douts) == 0
+        assert B.ebcc_decompress_batch_dev(dstreams, lens, shapes, douts) == 0
     e1.record(stream)
     torch.cuda.synchronize()
     t_dec = e0.elapsed_time(e1) / args.steps
     B.lib().ebcc_profile_reset()
     B.lib().ebcc_profile_enable(1)
     for _ in range(n_prof):
-        assert B.ebcc_decompress_batch_dev([r[0] for r in res], lens, shapes, douts) == 0
+        assert B.ebcc_decompress_batch_dev(dstreams, lens, shapes, douts) == 0
     torch.cuda.synchronize()
     B.lib().ebcc_profile_enable(0)
     prof_dec = per_step(B.profile_read(), n_prof)
-    max_err = max(float((d - f).abs().max()) / (BOUND * float(f.max() - f.min())) for d, f in zip(douts, dfields))
-    # end to end: every step copies the stack from pinned host memory, runs the
-    # batch call, and copies every stream back (host wall clock around it all)
+    # precision per field: the GPU decode against the original and against
+    # the FP64 oracle's decode of the same stream
+    eps = [BOUND * float(f.max() - f.min()) for f in dfields]
+    gpu_dec = [d.cpu().numpy() for d in douts]
+    err = [float(np.abs(g.astype(np.float64) - f).max()) / e for g, f, e in zip(gpu_dec, fields, eps)]
+    rmse = [float(np.sqrt(np.mean((g.astype(np.float64) - f) ** 2))) / e for g, f, e in zip(gpu_dec, fields, eps)]
+    orc_dec = pool.map(_oracle_decode, [(s, ny, nx) for s in streams_host])
+    vs_orc = [float(np.abs(g.astype(np.float64) - o).max()) / e for g, o, e in zip(gpu_dec, orc_dec, eps)]
+    orc_err = [float(np.abs(o.astype(np.float64) - f).max()) / e for o, f, e in zip(orc_dec, fields, eps)]
+    precision = {"max_err_over_eps": summary(err), "rmse_over_eps": summary(rmse),
+                 "oracle_decode_err_over_eps": summary(orc_err),
+                 "gpu_vs_oracle_decode_over_eps": summary(vs_orc), "fields": n}
+    if cpu:
+        ratios = [(f.nbytes / len(streams_host[v * nl + lev])) / cpu["field_cr"][f"{v},{lev}"]
+                  for (v, lev), f in ((i, fields[i[0] * nl + i[1]]) for i in ids)]
+        precision["cr_gpu_over_oracle"] = {"fields": [f"{v},{lev}" for v, lev in ids],
+                                           "ratios": ratios, **summary(np.abs(np.array(ratios) - 1.0))}
+    # end to end through the host-buffer batch call: pinned host fields in,
+    # streams out to pinned host buffers, every copy inside the call
     hfields = [f.cpu().pin_memory() for f in dfields]
     hstreams = [torch.empty(c, dtype=torch.uint8).pin_memory() for c in caps]
-    torch.cuda.synchronize()
     e2e_times, e2e_out = [], 0
     for it in range(args.warmup + args.steps):
         t = time.perf_counter()
-        for h, d in zip(hfields, dfields):
-            d.copy_(h, non_blocking=True)
-        res_e = step()
-        e2e_out = 0
-        for (st_, ln, _, _), hs in zip(res_e, hstreams):
-            hs[:ln].copy_(st_[:ln], non_blocking=True)
-            e2e_out += ln
-        torch.cuda.synchronize()
+        rc, res_e = B.ebcc_compress_batch(hfields, bounds, outs=hstreams)
+        assert rc == 0, rc
         if it >= args.warmup:
             e2e_times.append(time.perf_counter() - t)
+        e2e_out = sum(r[1] for r in res_e)
     t_e2e = float(np.mean(e2e_times))
-    # the single-field host API (host buffers in, stream out), for context
-    t = time.perf_counter()
-    plain_in = 0
-    for f in hfields[:args.e2e_fields]:
-        B.ebcc_compress(f.numpy(), BOUND, B.EBCC_BOUND_REL)
-        plain_in += f.numel() * 4
-    t_host_plain = time.perf_counter() - t
-    uneven = uneven_leg(B, torch, args.uneven, args.steps, args.warmup, args.plain_fields) if args.uneven else None
+    # the stack at the other two bounds of the survey's grid (0.1% and 10%)
+    other_bounds = {}
+    for bb in (1e-3, 1e-1):
+        tb, rb = timed_batch(B, torch, dfields, [bb] * n, outs, max(1, min(args.steps, 3)), stream)
+        other_bounds[f"{bb:g}"] = {"compress_gbs": raw_bytes / (tb / 1e3) / 1e9, "ms_per_step": tb,
+                                   "cr": raw_bytes / sum(r[1] for r in rb),
+                                   "per_variable": per_variable(rb, ny * nx * 4, nv, nl)}
+    # the single 181x360 field, plain (config of the oracle's own scale)
+    one = None
+    if not args.no_legs:
+        x1 = synth.smooth_field(181, 360, seed=0)
+        d1 = torch.from_numpy(x1).cuda()
+        o1 = torch.empty(B.ebcc_max_stream_bytes(181, 360), dtype=torch.uint8, device="cuda")
+        t1, r1 = timed_batch(B, torch, [d1], [BOUND], [o1], max(3, args.steps), stream)
+        one = {"ms_per_field": t1, "compress_gbs": x1.nbytes / (t1 / 1e3) / 1e9, "cr": x1.nbytes / r1[0][1],
+               "what": "one 181x360 field (seed 0), one call"}
+    # the uneven batch: grids 91x180 .. 1441x2880, bounds log-uniform in 0.1-10%
+    uneven = None
+    if args.uneven and not args.no_legs:
+        spec = synth.batch_spec(args.uneven, seed=3)
+        ufields = [torch.from_numpy(f).cuda() for f in pool.map(_batch_one, [(g, sd) for g, _, sd in spec])]
+        ubounds = [b for _, b, _ in spec]
+        uouts = [torch.empty(B.ebcc_max_stream_bytes(*f.shape), dtype=torch.uint8, device="cuda") for f in ufields]
+        uraw = sum(f.numel() * 4 for f in ufields)
+        tu, ru = timed_batch(B, torch, ufields, ubounds, uouts, max(1, min(args.steps, 3)), stream)
+        k = min(len(ufields), args.plain_fields * 4)
+        pu = timed_plain(B, torch, ufields[:k], ubounds[:k], uouts[:k], stream)
+        uneven = {"fields": len(ufields), "raw_bytes": uraw, "compress_gbs": uraw / (tu / 1e3) / 1e9,
+                  "ms_per_step": tu, "cr": uraw / sum(r[1] for r in ru),
+                  "plain_compress_gbs": sum(f.numel() * 4 for f in ufields[:k]) / (pu / 1e3) / 1e9,
+                  "plain_fields": k, "loops": loop_stats(ru),
+                  "what": "grids drawn from 91x180..1441x2880, bounds log-uniform in [0.1%, 10%], one batch call"}
+        del ufields, uouts
+    # the high-resolution batch: 3601x7200 fields with 1% Student-t spikes at 1%
+    hires = None
+    if args.hires and not args.no_legs:
+        hf = [torch.from_numpy(f).cuda() for f in pool.map(_hires_one, [4000 + i for i in range(args.hires)])]
+        hout = [torch.empty(B.ebcc_max_stream_bytes(*f.shape), dtype=torch.uint8, device="cuda") for f in hf]
+        hraw = sum(f.numel() * 4 for f in hf)
+        th, rh = timed_batch(B, torch, hf, [BOUND] * len(hf), hout, 1, stream)
+        kp = min(len(hf), 2)
+        ph = timed_plain(B, torch, hf[:kp], [BOUND] * kp, hout[:kp], stream)
+        hires = {"fields": len(hf), "raw_bytes": hraw, "compress_gbs": hraw / (th / 1e3) / 1e9, "ms_per_step": th,
+                 "cr": hraw / sum(r[1] for r in rh),
+                 "plain_compress_gbs": sum(f.numel() * 4 for f in hf[:kp]) / (ph / 1e3) / 1e9, "plain_fields": kp,
+                 "loops": loop_stats(rh),
+                 "what": "3601x7200 fields, config-1 generator + 1% Student-t(2) spikes, 1% bound, one batch call"}
+        del hf, hout
+    ablation = ablation_leg(B, torch, dfields, outs, stream) if not args.no_legs else None
     serving = None
     if not args.no_serve:
         serving = serving_leg(B, fields, args.serve_rate, args.serve_window, 40.0, 64)
+    pool.close()
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
     value = job_gbs(raw_bytes, world, t_ms)
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peak, peak_src = float(json.load(open(pk_path))["hbm_gbs"]), "measured copy (MEASURED_PEAKS.json)"
+    else:
+        peak, peak_src = FALLBACK_HBM_GBS, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
     roof = None
     if prof:
         top = max(prof, key=lambda p: p["ms"])
         ach = top["bytes"] / (top["ms"] / 1e3) / 1e9 if top["ms"] > 0 else 0.0
         traffic = NCU_TRAFFIC.get(top["name"]) if list(args.shape) == DEFAULT_SHAPE else None
-        roof = {"bound": "hbm", "kernel": top["name"], "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / peaks["hbm_gbs"], "traffic": traffic,
+        roof = {"bound": "hbm", "kernel": top["name"], "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": traffic,
                 "algorithmic_bytes_per_launch": top["bytes"] / max(1, top["launches"]),
-                "share_of_step": top["ms"] / t_ms, "peak_source": "measured burst copy"}
+                "bytes_counted": "on the device, per tile processed",
+                "share_of_step": top["ms"] / t_ms, "peak_source": peak_src}
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(args.shape),
         "decompress_gbs": raw_bytes / (t_dec / 1e3) / 1e9, "cr": raw_bytes / comp_bytes,
+        "per_variable": per_variable(res, ny * nx * 4, nv, nl),
         "plain": {"compress_gbs": plain_gbs, "fields": n_plain,
                   "what": "same fields, one field per call (every launch covers one field)"},
-        "max_err_over_bound": max_err,
+        "max_err_over_bound": max(err), "precision": precision,
         "e2e": {"value": raw_bytes / t_e2e / 1e9, "unit": "GB/s", "h2d_bytes_per_step": raw_bytes,
                 "d2h_bytes_per_step": e2e_out, "fields": n,
-                "what": "pinned host stack -> device, ebcc_compress_batch_dev, every stream back; host wall clock"},
-        "host_api_plain": {"value": plain_in / t_host_plain / 1e9, "unit": "GB/s",
-                           "fields": min(n, args.e2e_fields),
-                           "what": "ebcc_compress (host buffers, one field per call)"},
+                "what": "ebcc_compress_batch: pinned host fields in, streams to pinned host buffers, "
+                        "copies inside the call; host wall clock"},
+        "bounds": other_bounds, "single_field": one, "uneven_batch": uneven, "high_res": hires,
+        "ablation": ablation,
         "gpu_launches": int(round(sum(p["launches"] for p in prof))) if prof else None,
-        "roofline": roof, "serving": serving, "uneven_batch": uneven, "kernels": prof,
+        "roofline": roof, "serving": serving, "kernels": prof,
         "kernels_unit": "per step (profiled pass after the timed region)",
         "kernels_decompress": prof_dec,
         "clocks": clk.summary(), "cpu_baseline": cpu,
@@ -392,22 +555,26 @@ def run_gpu(args):
 
 
 def run_reference(args):
-    """The oracle as it stands, timed on the host cores on a bounded sample."""
+    """The oracle as it stands, timed on the host cores on whole fields of the stack."""
     rank = int(os.environ.get("RANK", 0))
     if rank != 0:
         return
-    cores = max(1, min(8, os.cpu_count() or 1))
-    fields = workload_fields(1, cores, *args.shape[2:])
+    cores = max(1, min(16, os.cpu_count() or 1))
+    nv, nl, ny, nx = args.shape
+    ids = sample_ids(cores, nv, nl)
+    byid = {(v, lev): synth.era5_like(v, lev, ny, nx) for v, lev in ids}
     vals = []
     cpu = None
-    for _ in range(args.warmup + args.steps):
-        cpu = oracle_sample(fields, BOUND, cores)
-        vals.append(cpu["value"])
+    with mp.get_context("spawn").Pool(cores) as pool:
+        for _ in range(args.warmup + args.steps):
+            cpu = oracle_sample(pool, byid, ids, BOUND)
+            vals.append(cpu["value"])
     v = float(np.mean(vals[args.warmup:])) if args.steps else vals[-1]
+    cpu = dict(cpu, value=v)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args.shape),
+        "config": sample_config(args.shape, cores),
         "cpu_baseline": cpu, "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -420,12 +587,13 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--shape", type=int, nargs=4, default=DEFAULT_SHAPE,
                     help="variables levels ny nx")
-    ap.add_argument("--e2e-fields", type=int, default=16)
     ap.add_argument("--plain-fields", type=int, default=8)
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="serving leg: mean requests per second")
     ap.add_argument("--serve-window", type=float, default=0.5, help="serving leg: seconds of arrivals")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--uneven", type=int, default=0, help="also time a batch of this many uneven-grid fields")
+    ap.add_argument("--uneven", type=int, default=512, help="uneven-grid batch leg: fields (0 = off)")
+    ap.add_argument("--hires", type=int, default=24, help="3601x7200 batch leg: fields (0 = off)")
+    ap.add_argument("--no-legs", action="store_true", help="only the headline, e2e, plain and precision legs")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -145,6 +145,81 @@ int ebcc_decompress_batch_dev(const ebcc_stream_desc *streams, int n, float **ou
 /* Upper bound of a stream's length for an ny x nx field. */
 size_t ebcc_max_stream_bytes(size_t ny, size_t nx);
 
+/* --------------------------------------------------- batched host-buffer API */
+/* The batch calls above with every buffer in host memory (Algorithm 1 KwIn /
+ * KwOut: the arrays in, the byte sequences out).  fields[i].field points to
+ * ny*nx host float32; outs[i].stream is a caller-owned host buffer of
+ * outs[i].capacity bytes that receives the stream (len, status and stats as
+ * in ebcc_compress_batch_dev).  The library copies the fields to device
+ * buffers it keeps between calls (grown to the largest batch seen, so a call
+ * allocates nothing once they have that size), runs the device batch, and
+ * copies every stream back.  Page-locked host buffers (cudaHostAlloc,
+ * cudaHostRegister) are copied by DMA directly; pageable ones go through the
+ * library's pinned staging.  `stream` is a cudaStream_t as void* (NULL = the
+ * legacy default stream); the call is synchronous.  Return value as
+ * ebcc_compress_batch_dev.  Errors: EINVAL, ENONFINITE, ENOMEM, ECAPACITY,
+ * ECUDA (per field in outs[i].status). */
+int ebcc_compress_batch(const ebcc_field_desc *fields, int n, ebcc_out_desc *outs, const ebcc_params *p,
+                        void *stream);
+/* Decompress n host streams into caller-owned host buffers outs[i] (ny*nx
+ * float32 each), through the same device buffers.  Synchronous.  Errors:
+ * EINVAL, ECORRUPT, ENOMEM, ECUDA (the first failing stream's status). */
+int ebcc_decompress_batch(const ebcc_stream_desc *streams, int n, float **outs, void *stream);
+
+/* ------------------------------------------------------- error statistics */
+/* Statistics of a reconstruction x_hat of x (Benchmarks, error statistics:
+ * SSIM against Baker's 0.99995 threshold, histograms of the compression
+ * errors, RMSE), computed on the GPU.  With e = x_hat - x in FP64:
+ * mean_err = mean e, rmse = sqrt(mean e^2), max_abs_err = max |e|; range =
+ * max x - min x; ssim = the mean SSIM (Wang et al. 2004) of x and x_hat both
+ * rescaled by x's min and range (dynamic range 1), 11 x 11 Gaussian window of
+ * standard deviation 1.5, C1 = 0.01^2, C2 = 0.03^2, over the n_ssim windows
+ * that lie inside the field (NaN when there are none: a side below 11, or a
+ * constant x). */
+typedef struct {
+    long long n, n_ssim;
+    double mean_err, rmse, max_abs_err, range, ssim;
+} ebcc_error_stats;
+/* x, x_hat: device ny*nx float32.  hist (device, nbins uint64, nbins <= 4096,
+ * NULL when nbins = 0): counts of the errors in nbins equal bins over
+ * [-eps, eps], point i in bin floor((e_i + eps) * (nbins / (2 eps))) clamped
+ * to [0, nbins - 1], computed in FP64.  Synchronous on `stream` (the library
+ * keeps its accumulators between calls).  Errors: EINVAL, ECUDA. */
+int ebcc_error_stats_dev(const float *x, const float *x_hat, size_t ny, size_t nx, double eps, int nbins,
+                         unsigned long long *hist, ebcc_error_stats *out, void *stream);
+
+/* ------------------------------------------------------------- N-D chunks */
+/* The N-D front end (Materials and Methods, first paragraph): a 4-D float32
+ * array of shape[4] = (T, P, H, W) -- time, level, latitude, longitude --
+ * row-major (W contiguous), is split into chunks of chunk[4] = (cT, cP, cH,
+ * cW) (an extent that is not a multiple of the chunk leaves smaller chunks at
+ * the end of that axis); each chunk is flattened to a 2-D field of
+ * (cT*cP*cH) rows by cW columns and compressed as a field of its own, with
+ * its own range-relative or absolute bound.  Chunks are numbered row-major
+ * over the chunk grid (the W chunk index fastest).
+ * ebcc_chunk_count: the number of chunks, or EINVAL (a zero extent, or more
+ * than 2^24 chunks).
+ * ebcc_chunk_info: chunk k's origin and extent in the array (either may be
+ * NULL) and its flattened 2-D shape ny x nx. */
+long long ebcc_chunk_count(const size_t shape[4], const size_t chunk[4]);
+int ebcc_chunk_info(const size_t shape[4], const size_t chunk[4], long long k, size_t origin[4], size_t extent[4],
+                    size_t *ny, size_t *nx);
+/* Compress every chunk of the device array `array` as one batch: the chunks
+ * are flattened on the device into a buffer the library owns (kept between
+ * calls), with no host copy; outs[k] (ebcc_chunk_count entries, caller-owned
+ * device buffers of at least ebcc_max_stream_bytes(ny, nx) bytes) receives
+ * chunk k's stream, status and stats as in ebcc_compress_batch_dev.
+ * Synchronises `stream`.  Errors: EINVAL, ENONFINITE, ENOMEM, ECAPACITY,
+ * ECUDA (the first failing chunk's status). */
+int ebcc_compress_chunks_dev(const float *array, const size_t shape[4], const size_t chunk[4], double bound,
+                             int bound_kind, const ebcc_params *p, ebcc_out_desc *outs, void *stream);
+/* Decompress the streams of every chunk (device, streams[k].ny / nx the
+ * chunk's flattened shape) back into the device array of shape[4] (each chunk
+ * written in place).  Synchronises `stream`.  Errors: EINVAL (a chunk's shape
+ * does not match), ECORRUPT, ENOMEM, ECUDA. */
+int ebcc_decompress_chunks_dev(const ebcc_stream_desc *streams, const size_t shape[4], const size_t chunk[4],
+                               float *array, void *stream);
+
 /* ---------------------------------------------------------------- serving */
 /* A device-resident request loop with continuous batching: requests that
  * arrive while others are on the GPU are admitted as slots and memory free up

@@ -365,6 +365,94 @@ def base_loop_trace(qa, r0=20.0, tol=1e-3, q=0.999, fallback=False, r_max=1e12):
     return list(seq[:n.value]), kept.value, r_f.value, q_f.value, bool(ok)
 
 
+# ---------------------------------------------------------------- error statistics
+def gauss_window(radius: int = 5, sigma: float = 1.5) -> np.ndarray:
+    """The normalised 1-D Gaussian taps of the SSIM window (Wang et al. 2004)."""
+    t = np.arange(-radius, radius + 1, dtype=np.float64)
+    w = np.exp(-t * t / (2.0 * sigma * sigma))
+    return w / w.sum()
+
+
+def _window_sum(a: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """Weighted sums over every 2-D window (outer product of w with itself)
+    that lies inside `a`, as two 1-D passes (valid positions only)."""
+    k = len(w)
+    rows = sum(w[t] * a[:, t:a.shape[1] - k + 1 + t] for t in range(k))
+    return sum(w[t] * rows[t:rows.shape[0] - k + 1 + t, :] for t in range(k))
+
+
+def ssim(x: np.ndarray, y: np.ndarray) -> float:
+    """Mean SSIM (Wang et al. 2004) of two fields, both rescaled by the first's
+    minimum and range (dynamic range 1), with the 11 x 11 Gaussian window of
+    standard deviation 1.5 and C1 = 0.01^2, C2 = 0.03^2, over the windows that
+    lie inside the field (Benchmarks, error statistics: the SSIM the paper
+    reports against Baker's threshold).  FP64."""
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    mn, rng = x.min(), x.max() - x.min()
+    X, Y = (x - mn) / rng, (y - mn) / rng
+    w = gauss_window()
+    mx, my = _window_sum(X, w), _window_sum(Y, w)
+    sxx = _window_sum(X * X, w) - mx * mx
+    syy = _window_sum(Y * Y, w) - my * my
+    sxy = _window_sum(X * Y, w) - mx * my
+    C1, C2 = 0.01 ** 2, 0.03 ** 2
+    m = ((2 * mx * my + C1) * (2 * sxy + C2)) / ((mx * mx + my * my + C1) * (sxx + syy + C2))
+    return float(m.mean())
+
+
+def error_stats(x: np.ndarray, x_hat: np.ndarray, eps: float, nbins: int = 0) -> dict:
+    """Compression-error statistics (Benchmarks, error statistics and the error
+    histograms): with e = x_hat - x in FP64, mean, RMSE, max |e|, the SSIM
+    above, and the counts of e in nbins equal bins over [-eps, eps] (point in
+    bin floor((e + eps) * (nbins / (2 eps))), clamped)."""
+    e = np.asarray(x_hat, np.float64) - np.asarray(x, np.float64)
+    out = {"n": e.size, "mean_err": float(e.mean()), "rmse": float(np.sqrt(np.mean(e * e))),
+           "max_abs_err": float(np.abs(e).max()), "range": float(np.float64(x.max()) - np.float64(x.min()))}
+    ok = min(x.shape) >= 11 and out["range"] > 0
+    out["ssim"] = ssim(x, x_hat) if ok else float("nan")
+    out["n_ssim"] = (x.shape[0] - 10) * (x.shape[1] - 10) if ok else 0
+    if nbins:
+        b = np.floor((e + eps) * (nbins / (2.0 * eps)))
+        out["hist"] = np.bincount(np.clip(b, 0, nbins - 1).astype(np.int64).ravel(), minlength=nbins)
+    return out
+
+
+# ---------------------------------------------------------------- N-D chunks
+def chunk_boxes(shape, chunk):
+    """Chunks of a (T, P, H, W) array (Materials and Methods, first paragraph):
+    origin and extent of each, row-major over the chunk grid; edge chunks are
+    smaller when an extent is not a multiple of the chunk."""
+    n = [-(-int(s) // int(min(c, s))) for s, c in zip(shape, chunk)]
+    ch = [int(min(c, s)) for s, c in zip(shape, chunk)]
+    out = []
+    for idx in np.ndindex(*n):
+        o = [i * c for i, c in zip(idx, ch)]
+        e = [min(c, s - oo) for c, s, oo in zip(ch, shape, o)]
+        out.append((tuple(o), tuple(e)))
+    return out
+
+
+def flatten_chunk(a: np.ndarray, origin, extent) -> np.ndarray:
+    """The chunk of `a` at origin/extent as a 2-D field of (T*P*H, W) rows."""
+    sl = tuple(slice(o, o + e) for o, e in zip(origin, extent))
+    c = a[sl]
+    return np.ascontiguousarray(c.reshape(extent[0] * extent[1] * extent[2], extent[3]))
+
+
+def compress_chunks(a: np.ndarray, chunk, bound: float, kind: int = 1, p=None):
+    """Every chunk flattened and compressed with Algorithm 1: list of streams."""
+    return [compress(flatten_chunk(a, o, e), bound, kind, p)[0] for o, e in chunk_boxes(a.shape, chunk)]
+
+
+def decompress_chunks(streams, shape, chunk) -> np.ndarray:
+    out = np.zeros(shape, np.float32)
+    for s, (o, e) in zip(streams, chunk_boxes(shape, chunk)):
+        y = decompress(s, e[0] * e[1] * e[2], e[3])
+        out[tuple(slice(oo, oo + ee) for oo, ee in zip(o, e))] = y.reshape(e)
+    return out
+
+
 def decompress(data: bytes, ny: int, nx: int) -> np.ndarray:
     buf = np.frombuffer(data, np.uint8).copy()
     out = np.zeros((ny, nx), np.float32)

@@ -28,6 +28,8 @@ ERRORS = {-1: "EINVAL", -2: "ENONFINITE", -3: "ECORRUPT", -4: "ENOMEM", -5: "EBU
 EXPORTS = [
     "ebcc_params_default", "ebcc_strerror", "ebcc_free", "ebcc_compress", "ebcc_decompress",
     "ebcc_stream_info", "ebcc_compress_batch_dev", "ebcc_decompress_batch_dev", "ebcc_max_stream_bytes",
+    "ebcc_compress_batch", "ebcc_decompress_batch", "ebcc_chunk_count", "ebcc_chunk_info",
+    "ebcc_compress_chunks_dev", "ebcc_decompress_chunks_dev", "ebcc_error_stats_dev",
     "ebcc_server_create", "ebcc_server_submit", "ebcc_server_poll", "ebcc_server_cancel",
     "ebcc_server_destroy", "ebcc_dwt_fwd_dev", "ebcc_dwt_fwd_static_dev", "ebcc_dwt_inv_dev", "ebcc_effective_levels",
     "ebcc_quantise_dev", "ebcc_band_step", "ebcc_t1_encode_dev", "ebcc_t1_decode_dev", "ebcc_pcrd_dev",
@@ -55,6 +57,11 @@ class ebcc_stats(C.Structure):
                 ("res_bytes", C.c_longlong), ("total_bytes", C.c_longlong),
                 ("spiht_len_bytes", C.c_longlong), ("len_two", C.c_longlong), ("len_one", C.c_longlong),
                 ("q_base", C.c_double)]
+
+
+class ebcc_error_stats(C.Structure):
+    _fields_ = [("n", C.c_longlong), ("n_ssim", C.c_longlong), ("mean_err", C.c_double), ("rmse", C.c_double),
+                ("max_abs_err", C.c_double), ("range", C.c_double), ("ssim", C.c_double)]
 
 
 class ebcc_field_desc(C.Structure):
@@ -108,6 +115,22 @@ def lib():
                                               C.POINTER(ebcc_params), C.c_void_p]
         L.ebcc_decompress_batch_dev.argtypes = [C.POINTER(ebcc_stream_desc), C.c_int, C.POINTER(C.c_void_p),
                                                 C.c_void_p]
+        L.ebcc_error_stats_dev.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_size_t, C.c_double, C.c_int,
+                                           C.c_void_p, C.POINTER(ebcc_error_stats), C.c_void_p]
+        L.ebcc_chunk_count.restype = C.c_longlong
+        L.ebcc_chunk_count.argtypes = [C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
+        L.ebcc_chunk_info.argtypes = [C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.c_longlong,
+                                      C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.POINTER(C.c_size_t),
+                                      C.POINTER(C.c_size_t)]
+        L.ebcc_compress_chunks_dev.argtypes = [C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.c_double,
+                                               C.c_int, C.POINTER(ebcc_params), C.POINTER(ebcc_out_desc),
+                                               C.c_void_p]
+        L.ebcc_decompress_chunks_dev.argtypes = [C.POINTER(ebcc_stream_desc), C.POINTER(C.c_size_t),
+                                                 C.POINTER(C.c_size_t), C.c_void_p, C.c_void_p]
+        L.ebcc_compress_batch.argtypes = [C.POINTER(ebcc_field_desc), C.c_int, C.POINTER(ebcc_out_desc),
+                                          C.POINTER(ebcc_params), C.c_void_p]
+        L.ebcc_decompress_batch.argtypes = [C.POINTER(ebcc_stream_desc), C.c_int, C.POINTER(C.c_void_p),
+                                            C.c_void_p]
         L.ebcc_dwt_fwd_dev.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_size_t, C.c_int, C.c_double,
                                        C.c_double, C.c_void_p]
         L.ebcc_dwt_fwd_static_dev.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_size_t, C.c_int,
@@ -240,6 +263,120 @@ def ebcc_compress_batch_dev(fields, bounds, kinds=None, p: ebcc_params | None = 
     rc = lib().ebcc_compress_batch_dev(fd, n, od, C.byref(p) if p else None, C.c_void_p(_stream(stream)))
     res = [(bufs[i], od[i].len, od[i].status, stats_dict(od[i].stats)) for i in range(n)]
     return rc, res
+
+
+def _host_addr(a):
+    """Address of a host buffer: a numpy array or a CPU torch tensor (pinned or not)."""
+    return a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr()
+
+
+def ebcc_compress_batch(fields, bounds, kinds=None, p: ebcc_params | None = None, outs=None, stream=None):
+    """Host-buffer batch: fields are host float32 arrays (numpy, or CPU torch
+    tensors, pinned or pageable); outs (optional) host uint8 buffers for the
+    streams.  Returns (rc, [(out buffer, length, status, stats dict)])."""
+    n = len(fields)
+    kinds = kinds or [EBCC_BOUND_REL] * n
+    fd = (ebcc_field_desc * max(n, 1))()
+    od = (ebcc_out_desc * max(n, 1))()
+    bufs = []
+    for i, f in enumerate(fields):
+        ny, nx = f.shape
+        fd[i] = ebcc_field_desc(_host_addr(f), ny, nx, float(bounds[i]), int(kinds[i]))
+        b = outs[i] if outs is not None else np.empty(ebcc_max_stream_bytes(ny, nx), np.uint8)
+        bufs.append(b)
+        od[i].stream = _host_addr(b)
+        od[i].capacity = b.nbytes if isinstance(b, np.ndarray) else b.numel()
+    rc = lib().ebcc_compress_batch(fd, n, od, C.byref(p) if p else None,
+                                   C.c_void_p(stream if stream is not None else 0))
+    return rc, [(bufs[i], od[i].len, od[i].status, stats_dict(od[i].stats)) for i in range(n)]
+
+
+def ebcc_decompress_batch(streams, shapes, outs=None, stream=None):
+    """Host-buffer batch decompression: streams are bytes or host uint8 arrays;
+    returns (rc, list of host float32 arrays or the given outs)."""
+    n = len(streams)
+    sd = (ebcc_stream_desc * max(n, 1))()
+    op = (C.c_void_p * max(n, 1))()
+    keep, res = [], []
+    for i in range(n):
+        s = np.frombuffer(streams[i], np.uint8) if isinstance(streams[i], (bytes, bytearray)) else streams[i]
+        keep.append(s)
+        sd[i] = ebcc_stream_desc(_host_addr(s), int(s.nbytes if isinstance(s, np.ndarray) else s.numel()),
+                                 shapes[i][0], shapes[i][1])
+        o = outs[i] if outs is not None else np.empty(shapes[i], np.float32)
+        res.append(o)
+        op[i] = _host_addr(o)
+    rc = lib().ebcc_decompress_batch(sd, n, op, C.c_void_p(stream if stream is not None else 0))
+    return rc, res
+
+
+def ebcc_error_stats_dev(x, x_hat, eps: float, nbins: int = 0, hist=None, stream=None) -> dict:
+    """Error statistics of x_hat against x (2-D float32 CUDA tensors); the
+    histogram, when nbins > 0, goes to `hist` (a uint64 CUDA tensor of nbins)
+    or a new one, returned under "hist"."""
+    import torch
+    ny, nx = x.shape
+    if nbins and hist is None:
+        hist = torch.zeros(nbins, dtype=torch.int64, device=x.device)
+    st = ebcc_error_stats()
+    _check(lib().ebcc_error_stats_dev(_ptr(x), _ptr(x_hat), ny, nx, float(eps), int(nbins),
+                                      C.c_void_p(hist.data_ptr() if nbins else 0), C.byref(st),
+                                      C.c_void_p(_stream(stream))), "ebcc_error_stats_dev")
+    out = {f: getattr(st, f) for f, _ in ebcc_error_stats._fields_}
+    out["hist"] = hist
+    return out
+
+
+def _size4(v):
+    return (C.c_size_t * 4)(*[int(x) for x in v])
+
+
+def ebcc_chunk_count(shape, chunk) -> int:
+    return lib().ebcc_chunk_count(_size4(shape), _size4(chunk))
+
+
+def ebcc_chunk_info(shape, chunk, k: int):
+    """(origin, extent, (ny, nx)) of chunk k."""
+    o, e = (C.c_size_t * 4)(), (C.c_size_t * 4)()
+    ny, nx = C.c_size_t(), C.c_size_t()
+    _check(lib().ebcc_chunk_info(_size4(shape), _size4(chunk), int(k), o, e, C.byref(ny), C.byref(nx)),
+           "ebcc_chunk_info")
+    return tuple(o), tuple(e), (ny.value, nx.value)
+
+
+def ebcc_compress_chunks_dev(array, chunk, bound: float, kind: int = EBCC_BOUND_REL, p: ebcc_params | None = None,
+                             stream=None):
+    """array: 4-D float32 CUDA tensor (T, P, H, W); returns (rc, [(stream
+    buffer, length, status, stats, (ny, nx))] per chunk, row-major)."""
+    import torch
+    shape = tuple(array.shape)
+    n = ebcc_chunk_count(shape, chunk)
+    if n < 0:
+        raise EbccError(n, "ebcc_chunk_count")
+    od = (ebcc_out_desc * max(n, 1))()
+    bufs, shapes = [], []
+    for k in range(n):
+        _, _, (ny, nx) = ebcc_chunk_info(shape, chunk, k)
+        b = torch.empty(ebcc_max_stream_bytes(ny, nx), dtype=torch.uint8, device=array.device)
+        bufs.append(b)
+        shapes.append((ny, nx))
+        od[k].stream = b.data_ptr()
+        od[k].capacity = b.numel()
+    rc = lib().ebcc_compress_chunks_dev(C.c_void_p(array.data_ptr()), _size4(shape), _size4(chunk), float(bound),
+                                        int(kind), C.byref(p) if p else None, od, C.c_void_p(_stream(stream)))
+    return rc, [(bufs[k], od[k].len, od[k].status, stats_dict(od[k].stats), shapes[k]) for k in range(n)]
+
+
+def ebcc_decompress_chunks_dev(streams, lens, shape, chunk, out, stream=None):
+    """streams: per-chunk uint8 CUDA tensors (row-major chunk order); out: the
+    4-D float32 CUDA tensor to fill."""
+    n = len(streams)
+    sd = (ebcc_stream_desc * max(n, 1))()
+    for k in range(n):
+        _, _, (ny, nx) = ebcc_chunk_info(shape, chunk, k)
+        sd[k] = ebcc_stream_desc(streams[k].data_ptr(), int(lens[k]), ny, nx)
+    return lib().ebcc_decompress_chunks_dev(sd, _size4(shape), _size4(chunk), C.c_void_p(out.data_ptr()),
+                                            C.c_void_p(_stream(stream)))
 
 
 def ebcc_decompress_batch_dev(streams, lens, shapes, outs, stream=None):

@@ -40,6 +40,20 @@ __device__ __forceinline__ int reflect(int i, int n) {
 
 __device__ __forceinline__ int ceil_sh(int n, int l) { return (int)(((long long)n + (1LL << l) - 1) >> l); }
 
+// Every index of the level kernels is in range by construction: reflect()
+// keeps a tile's halo inside [0, hp) x [0, wp); an LL sample (sy, sx) lies in
+// [0, ceil(hp/2)) x [0, ceil(wp/2)), the extent of the LL scratch of the level;
+// a detail sample lies in [0, hp) x [0, wp) of the Mallat array, and hp <= ny,
+// wp <= nx.  So the kernels check these extents once per CTA (a failure is
+// recorded in the field's guard word and the CTA touches nothing) instead of
+// every access.
+__device__ __forceinline__ bool level_extents_ok(const FieldRun &r, int l, int hp, int wp) {
+    const bool ok = l >= 1 && hp >= 1 && wp >= 1 && hp <= r.ny && wp <= r.nx &&
+                    hp == ceil_sh(r.ny, l - 1) && wp == ceil_sh(r.nx, l - 1);
+    if (!ok && threadIdx.x == 0) guard_flush(true, guard_word(r));
+    return ok;
+}
+
 // forward level l of the field in grid slot blockIdx.z: the level's input
 // (plane `src` at level 1, else the LL scratch of level l - 1) -> detail bands
 // into W, LL into the scratch of level l (into W at the last level)
@@ -57,10 +71,9 @@ __global__ void __launch_bounds__(96) fwd_level(Live lv, const __grid_constant__
     const bool last = l == L;
     float *__restrict__ ll = last ? nullptr : ((l & 1) ? r->s1 : r->s2);
     float *__restrict__ coef = r->W;
-    const long long ncoef = r->N;
     const int hl = (hp + 1) >> 1, wl = (wp + 1) >> 1, ls = wl;
     const double mn = r->mn, inv = r->inv_range;
-    int *const gw = guard_word(*r);
+    if (!level_extents_ok(*r, l, hp, wp)) return;
     const int tid = threadIdx.x;
     __shared__ float t[EY][EX + 1];
     if (tid < EX) {  // column tid: all loads in flight, the four lifting steps and the scaling in registers
@@ -70,7 +83,7 @@ __global__ void __launch_bounds__(96) fwd_level(Live lv, const __grid_constant__
         for (int ly = 0; ly < EY; ly++) {
             const int gy = reflect(ty0 - HALO + ly, hp);
             const long long i = (long long)gy * ss + gx;
-            w[ly] = INBS(i, (long long)hp * ss, gw) ? src[i] : 0.0f;
+            w[ly] = src[i];
         }
         if (NORM) {
             const NormK k = make_norm_k(mn, inv);
@@ -118,10 +131,10 @@ __global__ void __launch_bounds__(96) fwd_level(Live lv, const __grid_constant__
         float v = t[HALO + 2 * rr + pv][HALO + 2 * c + ph];
         int oy = (gy >> 1) + (pv ? hl : 0), ox = (gx >> 1) + (ph ? wl : 0);
         if (!pv && !ph) {
-            if (ll && INBS((long long)oy * ls + ox, (long long)hl * ls, gw)) ll[(size_t)oy * ls + ox] = v;
-            if (last && INBS((long long)oy * nx + ox, ncoef, gw)) coef[(size_t)oy * nx + ox] = v;
+            if (ll) ll[(size_t)oy * ls + ox] = v;
+            if (last) coef[(size_t)oy * nx + ox] = v;
         } else {
-            if (INBS((long long)oy * nx + ox, ncoef, gw)) coef[(size_t)oy * nx + ox] = v;
+            coef[(size_t)oy * nx + ox] = v;
         }
     }
 }
@@ -161,7 +174,6 @@ __device__ __forceinline__ void block_count_fail_add(unsigned long long in, unsi
 // the last step of an inverse transform at point gi of field r
 __device__ __forceinline__ void finish_point(const InvFinal &fin, const FieldRun &r, float *dst, float v, long long gi,
                                              unsigned long long &cnt) {
-    if (!INBS(gi, r.N, guard_word(r))) return;
     if (fin.mode <= 0) {
         if (fin.mode == 0 && fin.add_base) v = v + r.Abase[gi];
         dst[gi] = v;
@@ -188,9 +200,11 @@ constexpr int IT = 96;  // threads of an inverse-level CTA (72 stage the tile's 
 // column is lifted in registers by one thread.
 // MODE: the finish this launch applies (fin.mode at level 1, -1 above), as a
 // template parameter so each instantiation carries only its own finish
+// per_pt > 0 (profiling): each tile processed adds its algorithmic bytes,
+// per_pt per point of the tile, to its field's sc->prof_bytes
 template <int MODE>
 __global__ void __launch_bounds__(IT, 12) inv_level(Live lv, const __grid_constant__ FieldRun one, int l, int src_plane,
-                                                InvFinal fin) {
+                                                InvFinal fin, float per_pt) {
     int f;
     const FieldRun *r = pick(lv, one, blockIdx.x, f);
     if (!r || l > r->L) return;
@@ -212,14 +226,17 @@ __global__ void __launch_bounds__(IT, 12) inv_level(Live lv, const __grid_consta
         __syncthreads();
         if (quit) return;
     }
+    if (per_pt > 0.0f && tid == 0 && r->sc) {
+        const int th = hp - ty0 < TY ? hp - ty0 : TY, tw = wp - tx0 < TX ? wp - tx0 : TX;
+        atomicAdd(&r->sc->prof_bytes, (unsigned long long)(per_pt * (float)(th * tw)));
+    }
     const float *__restrict__ coef = plane_ptr(*r, src_plane);
     const float *__restrict__ ll = l < L ? (((l + 1) & 1) ? r->s2 : r->s1) : coef;
     const int ls = l < L ? ceil_sh(nx, l) : nx;
     float *__restrict__ dst = l == 1 ? plane_ptr(*r, fin.dst) : ((l & 1) ? r->s2 : r->s1);
     const int ds = l == 1 ? nx : wp;
     constexpr int mode = MODE;
-    const int ncoef = (int)r->N;  // a field has fewer than 2^31 points (checked on entry)
-    int *const gw = guard_word(*r);
+    if (!level_extents_ok(*r, l, hp, wp)) return;
     const int hl = (hp + 1) >> 1, wl = (wp + 1) >> 1;
     __shared__ float t[EY][EX + 1];
     // interior tile: the halo needs no reflection, every index is in range
@@ -243,7 +260,6 @@ __global__ void __launch_bounds__(IT, 12) inv_level(Live lv, const __grid_consta
         const int gx = reflect(tx0 - HALO + tid, wp);
         const int ph = gx & 1, sx = gx >> 1;
         const int cx = sx + (ph ? wl : 0);  // column of the coefficient in the Mallat array
-        const int lim_ll = hl * ls;
         float v[EY];
 #pragma unroll
         for (int ly = 0; ly < EY; ly++) {
@@ -251,9 +267,8 @@ __global__ void __launch_bounds__(IT, 12) inv_level(Live lv, const __grid_consta
             const int pv = gy & 1, sy = gy >> 1;
             const bool from_ll = !pv && !ph;
             const int i = from_ll ? sy * ls + sx : (sy + (pv ? hl : 0)) * nx + cx;
-            const bool ok = from_ll ? INBS(i, lim_ll, gw) : INBS(i, ncoef, gw);
             const float *src = from_ll ? ll : coef;
-            v[ly] = ok ? src[i] : 0.0f;
+            v[ly] = src[i];
         }
 #pragma unroll
         for (int ly = 0; ly < EY; ly++) t[ly][tid] = v[ly];
@@ -297,11 +312,10 @@ __global__ void __launch_bounds__(IT, 12) inv_level(Live lv, const __grid_consta
             const int nr = hp - ty0 < TY ? hp - ty0 : TY;
             npts = nr;
             if (mode < 0) {
-                const int lim = l == 1 ? ncoef : hp * ds;
 #pragma unroll
                 for (int rr = 0; rr < TY; rr++) {
                     const int i = (ty0 + rr) * ds + gx;
-                    if (rr < nr && INBS(i, lim, gw)) dst[i] = w[HALO + rr];
+                    if (rr < nr) dst[i] = w[HALO + rr];
                 }
             } else if (mode == 1 && nr == TY) {  // base-loop count, full tile column
                 const float2 *__restrict__ bnd = r->bounds + (size_t)ty0 * nx + gx;
@@ -327,7 +341,7 @@ __global__ void __launch_bounds__(IT, 12) inv_level(Live lv, const __grid_consta
                     for (int u = 0; u < 8; u++) {
                         const int rr = g0 + u;
                         const int i = (ty0 + rr) * nx + gx;
-                        const bool ok = rr < nr && INBS(i, ncoef, gw);
+                        const bool ok = rr < nr;
                         bb[u] = ok ? bnd[i] : make_float2(1.0f, 0.0f);
                         av[u] = (mode == 2 && ok) ? ab[i] : 0.0f;
                     }
@@ -447,12 +461,18 @@ int dwt_inverse_b(const Live &lv, const FieldRun &one, int nslots, const BatchDi
         else if (fin.mode == 2) per += 12.0;
         else per += fin.add_base ? 8.0 : 4.0;
         const int mode = l == 1 ? fin.mode : -1;
+        // while profiling, a batched launch counts the bytes of the tiles it
+        // processes on the device (tiles of finished fields and skipped
+        // counting tiles move nothing); otherwise the launch's whole extent
+        const bool dev = prof_enabled() && lv.tab != nullptr;
+        const double hb = dev ? 0.0 : per * hp * wp * nslots;
+        const float pp = dev ? (float)per : 0.0f;
         switch (mode) {
-        case -1: PROF("inv_level", st, per * hp * wp * nslots, inv_level<-1><<<grid, IT, 0, st>>>(lv, one, l, src, fin)); break;
-        case 0: PROF("inv_level", st, per * hp * wp * nslots, inv_level<0><<<grid, IT, 0, st>>>(lv, one, l, src, fin)); break;
-        case 1: PROF("inv_level", st, per * hp * wp * nslots, inv_level<1><<<grid, IT, 0, st>>>(lv, one, l, src, fin)); break;
-        case 2: PROF("inv_level", st, per * hp * wp * nslots, inv_level<2><<<grid, IT, 0, st>>>(lv, one, l, src, fin)); break;
-        default: PROF("inv_level", st, per * hp * wp * nslots, inv_level<3><<<grid, IT, 0, st>>>(lv, one, l, src, fin)); break;
+        case -1: PROF("inv_level", st, hb, inv_level<-1><<<grid, IT, 0, st>>>(lv, one, l, src, fin, pp)); break;
+        case 0: PROF("inv_level", st, hb, inv_level<0><<<grid, IT, 0, st>>>(lv, one, l, src, fin, pp)); break;
+        case 1: PROF("inv_level", st, hb, inv_level<1><<<grid, IT, 0, st>>>(lv, one, l, src, fin, pp)); break;
+        case 2: PROF("inv_level", st, hb, inv_level<2><<<grid, IT, 0, st>>>(lv, one, l, src, fin, pp)); break;
+        default: PROF("inv_level", st, hb, inv_level<3><<<grid, IT, 0, st>>>(lv, one, l, src, fin, pp)); break;
         }
         CK(cudaGetLastError());
     }

@@ -76,6 +76,15 @@ int engine_decompress(EbccEngine *e, const ebcc_stream_desc *sd, int n, float *c
                       cudaStream_t st);
 // device workspace of one field in a compression batch
 size_t ebcc_compress_footprint(size_t ny, size_t nx, const ebcc_params &p);
+// the engine behind the library's synchronous entry points, and the lock that
+// serialises them
+#include <mutex>
+std::mutex &ebcc_api_mutex();
+EbccEngine *ebcc_api_engine();
+int api_check_shape(size_t ny, size_t nx);
+int api_validate_params(const ebcc_params &p);
+// shape of a stream from its header (host memory); ECORRUPT if it does not parse
+int api_stream_shape(const uint8_t *h, size_t len, size_t *ny, size_t *nx);
 
 // ------------------------------------------------------------ batches
 // Per-field device scalars (results and counters of the pipeline steps).
@@ -97,6 +106,7 @@ struct FieldScal {
     unsigned long long fail_thr;   // a count below q N is certain once fail reaches this (0: count everything)
     unsigned long long tot[2];     // base section: metadata bytes, payload bytes
     long long refine_start[32];    // SPIHT: bit offset of each plane's refinement pass
+    unsigned long long prof_bytes; // while profiling: algorithmic bytes of the inverse-DWT tiles processed
 };
 
 struct SpihtWork {  // per-field device lists and maxima
@@ -420,6 +430,9 @@ int ebcc_debug_sync_enabled();
 int prof_id(const char *name);
 void *prof_begin(int id, cudaStream_t st);
 void prof_end(void *tok, cudaStream_t st, double bytes);
+// profiler on?  And bytes counted on the device, added to a kernel's entry
+int prof_enabled();
+void prof_add_bytes(const char *name, double bytes);
 #define PROF(name, st, bytes, ...)                    \
     do {                                             \
         static int pid_ = prof_id(name);             \
@@ -461,6 +474,18 @@ __device__ __forceinline__ bool inb_rec(long long i, long long n, int *word, int
     return false;
 }
 #define INBS(i, n, word) inb_rec((long long)(i), (long long)(n), (word), 1)
+// the quiet form that notes a miss in a per-thread flag (an OR, no branch,
+// so loads around it still batch); the kernel reports a noted miss once, at
+// its end, with guard_flush
+__device__ __forceinline__ bool inb_note(long long i, long long n, bool &miss) {
+    const bool ok = (unsigned long long)i < (unsigned long long)n;
+    miss |= !ok;
+    return ok;
+}
+#define INBN(i, n, miss) inb_note((long long)(i), (long long)(n), (miss))
+__device__ __forceinline__ void guard_flush(bool miss, int *word, int bit = 1) {
+    if (miss && word) atomicOr(word, bit);
+}
 // a field's guard word (null for a field passed without its scalars)
 __device__ __forceinline__ int *guard_word(const FieldRun &r) { return r.sc ? &r.sc->guard : nullptr; }
 #endif

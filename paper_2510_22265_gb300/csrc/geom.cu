@@ -264,6 +264,14 @@ void *prof_begin(int id, cudaStream_t st) {
     return p;
 }
 
+int prof_enabled() { return g_prof_on ? 1 : 0; }
+
+void prof_add_bytes(const char *name, double bytes) {
+    const int id = prof_id(name);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof[id].bytes += bytes;
+}
+
 void prof_end(void *tok, cudaStream_t st, double bytes) {
     if (!tok) return;
     ProfPending *p = (ProfPending *)tok;

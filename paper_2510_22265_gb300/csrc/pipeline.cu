@@ -1425,6 +1425,11 @@ int compress_batch(Engine &e, const ebcc_field_desc *fd, int n, ebcc_out_desc *o
     RC(download(e, b.d_sc, F, &hs, st));
     for (int f = 0; f < F; f++)
         if (hs[f].guard && !status[f]) status[f] = EBCC_ECUDA;
+    if (prof_enabled()) {
+        double pb = 0;
+        for (int f = 0; f < F; f++) pb += (double)hs[f].prof_bytes;
+        prof_add_bytes("inv_level", pb);
+    }
     // ---- outcomes
     for (int f = 0; f < F; f++) {
         ebcc_out_desc &o = od[vin[f]];
@@ -1617,6 +1622,11 @@ int decompress_batch(Engine &e, const ebcc_stream_desc *sd, int n, float *const 
                 if (!hs[f].ok) status[vin[f]] = EBCC_ECORRUPT;
             for (int f = 0; f < F; f++)
                 if (hs[f].guard && !status[vin[f]]) status[vin[f]] = EBCC_ECUDA;
+            if (prof_enabled()) {
+                double pb = 0;
+                for (int f = 0; f < F; f++) pb += (double)hs[f].prof_bytes;
+                prof_add_bytes("inv_level", pb);
+            }
             if (*t1s & T1_GUARD)
                 for (int f : D)
                     if (!status[vin[f]]) status[vin[f]] = EBCC_ECUDA;
@@ -1727,51 +1737,24 @@ EbccEngine *g_engine() {
 }
 }  // namespace
 
+std::mutex &ebcc_api_mutex() { return g_mu; }
+EbccEngine *ebcc_api_engine() { return g_engine(); }
+int api_check_shape(size_t ny, size_t nx) { return check_shape(ny, nx); }
+int api_validate_params(const ebcc_params &p) { return validate_params(p); }
+int api_stream_shape(const uint8_t *h, size_t len, size_t *ny, size_t *nx) {
+    ParsedHeader ph;
+    RC(parse_header(h, len, ph));
+    *ny = (size_t)ph.ny;
+    *nx = (size_t)ph.nx;
+    return EBCC_OK;
+}
+
 extern "C" {
 
 size_t ebcc_max_stream_bytes(size_t ny, size_t nx) {
     size_t N = ny * nx;
     size_t nblk = N / 64 + 64 * 64;  // generous: every block of every band
     return HDR_BYTES + 8 * N + 4096 + nblk * 8 + 8 * 4096 + 6 * N;
-}
-
-int ebcc_compress(const float *field, size_t ny, size_t nx, double bound, int bound_kind, const ebcc_params *pp,
-                  uint8_t **out, size_t *out_len, ebcc_stats *stats) {
-    if (!field || !out || !out_len) return EBCC_EINVAL;
-    *out = nullptr;
-    *out_len = 0;
-    RC(check_shape(ny, nx));
-    if (!(bound > 0) || !isfinite(bound) || (bound_kind != EBCC_BOUND_ABS && bound_kind != EBCC_BOUND_REL))
-        return EBCC_EINVAL;
-    ebcc_params p;
-    if (pp) p = *pp; else ebcc_params_default(&p);
-    RC(validate_params(p));
-    std::lock_guard<std::mutex> lk(g_mu);
-    EbccEngine *eng = g_engine();
-    if (!eng) return EBCC_ENOMEM;
-    const size_t cap = ebcc_max_stream_bytes(ny, nx);
-    float *d_in = nullptr;
-    uint8_t *d_out = nullptr;
-    CK(cudaMalloc(&d_in, ny * nx * sizeof(float)));
-    if (cudaMalloc(&d_out, cap) != cudaSuccess) { cudaFree(d_in); return EBCC_ENOMEM; }
-    int rc = EBCC_OK;
-    if (cudaMemcpy(d_in, field, ny * nx * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) rc = EBCC_ECUDA;
-    ebcc_field_desc fd{d_in, ny, nx, bound, bound_kind};
-    ebcc_out_desc od;
-    memset(&od, 0, sizeof(od));
-    od.stream = d_out;
-    od.capacity = cap;
-    if (!rc) rc = engine_compress(eng, &fd, 1, &od, p, 0);
-    if (!rc) rc = od.status;
-    if (!rc) {
-        uint8_t *h = (uint8_t *)malloc(od.len);
-        if (!h) rc = EBCC_ENOMEM;
-        else if (cudaMemcpy(h, d_out, od.len, cudaMemcpyDeviceToHost) != cudaSuccess) { free(h); rc = EBCC_ECUDA; }
-        else { *out = h; *out_len = od.len; if (stats) *stats = od.stats; }
-    }
-    cudaFree(d_in);
-    cudaFree(d_out);
-    return rc;
 }
 
 int ebcc_stream_info(const uint8_t *stream, size_t len, size_t *ny, size_t *nx, double *bound_abs) {
@@ -1782,30 +1765,6 @@ int ebcc_stream_info(const uint8_t *stream, size_t len, size_t *ny, size_t *nx, 
     if (nx) *nx = h.nx;
     if (bound_abs) *bound_abs = h.eps;
     return EBCC_OK;
-}
-
-int ebcc_decompress(const uint8_t *stream, size_t len, float *out, size_t ny, size_t nx) {
-    if (!stream || !out) return EBCC_EINVAL;
-    RC(check_shape(ny, nx));
-    ParsedHeader h;
-    RC(parse_header(stream, len, h));
-    if ((size_t)h.ny != ny || (size_t)h.nx != nx) return EBCC_EINVAL;
-    std::lock_guard<std::mutex> lk(g_mu);
-    EbccEngine *eng = g_engine();
-    if (!eng) return EBCC_ENOMEM;
-    uint8_t *d_s = nullptr;
-    float *d_o = nullptr;
-    CK(cudaMalloc(&d_s, len + 16));
-    if (cudaMalloc(&d_o, ny * nx * sizeof(float)) != cudaSuccess) { cudaFree(d_s); return EBCC_ENOMEM; }
-    int rc = EBCC_OK, s1 = EBCC_OK;
-    if (cudaMemcpy(d_s, stream, len, cudaMemcpyHostToDevice) != cudaSuccess) rc = EBCC_ECUDA;
-    ebcc_stream_desc sd{d_s, len, ny, nx};
-    if (!rc) rc = engine_decompress(eng, &sd, 1, &d_o, &s1, 0);
-    if (!rc) rc = s1;
-    if (!rc && cudaMemcpy(out, d_o, ny * nx * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess) rc = EBCC_ECUDA;
-    cudaFree(d_s);
-    cudaFree(d_o);
-    return rc;
 }
 
 int ebcc_compress_batch_dev(const ebcc_field_desc *fields, int n, ebcc_out_desc *outs, const ebcc_params *pp,

@@ -122,7 +122,7 @@ __global__ void maxima_kernel(Live lv, const __grid_constant__ FieldRun one, int
     load_sg(g, *r);
     const int32_t *__restrict__ s = r->s;
     uint32_t *maxd = r->sw.maxd, *maxl = r->sw.maxl;
-    int *const gw = guard_word(*r);
+    bool miss = false;
     int nb = l == 0 ? 1 : 3;
     int y0s[3], x0s[3], bhs[3], bws[3];
     long cnt[4] = {0, 0, 0, 0};
@@ -141,15 +141,16 @@ __global__ void maxima_kernel(Live lv, const __grid_constant__ FieldRun one, int
         int n = children(g, idx, c);
         uint32_t md = 0, ml = 0;
         for (int q = 0; q < n; q++) {
-            if (!INBS(c[q], (long long)g.ny * g.nx, gw)) continue;
+            if (!INBN(c[q], (long long)g.ny * g.nx, miss)) continue;
             uint32_t cd = leaf_children ? 0u : maxd[c[q]];  // level-1 nodes have no descendants
             md = max(md, max(absi(s[c[q]]), cd));
             ml = max(ml, cd);
         }
-        if (!INBS(idx, (long long)g.ny * g.nx, gw)) continue;
+        if (!INBN(idx, (long long)g.ny * g.nx, miss)) continue;
         maxd[idx] = md;
         maxl[idx] = ml;
     }
+    guard_flush(miss, guard_word(*r));
 }
 
 constexpr int ET = 1024;
@@ -210,8 +211,8 @@ __device__ __forceinline__ uint32_t bitmask(unsigned long long b) {
 __device__ __forceinline__ void win_clear(EncShared &sh) {
     for (int k = threadIdx.x; k < WIN_WORDS; k += ET) sh.win[k] = 0;
 }
-__device__ __forceinline__ void win_set(EncShared &sh, unsigned long long b, int *gw) {
-    if (INBS((long long)(b >> 5) - (long long)sh.wbase, WIN_WORDS, gw)) atomicOr(&sh.win[(b >> 5) - sh.wbase], bitmask(b));
+__device__ __forceinline__ void win_set(EncShared &sh, unsigned long long b, bool &miss) {
+    if (INBN((long long)(b >> 5) - (long long)sh.wbase, WIN_WORDS, miss)) atomicOr(&sh.win[(b >> 5) - sh.wbase], bitmask(b));
 }
 // The chunk's bits are [start_bit, end_bit).  When start_bit is not on a word
 // boundary the window's first word also holds bits of the chunk before (the
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
     __shared__ SG g;
     if (threadIdx.x == 0) r->sc->spiht_status = 0;  // before the barrier in load_sg
     load_sg(g, *r);
-    int *const gw = guard_word(*r);
+    bool miss = false;
     const int32_t *__restrict__ s = r->s;
     const uint32_t *__restrict__ maxd = r->sw.maxd;
     const uint32_t *__restrict__ maxl = r->sw.maxl;
@@ -290,14 +291,14 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
         uint32_t idx = 0;
         if (k < nroot) {
             idx = (uint32_t)(k / wL) * g.nx + (uint32_t)(k % wL);
-            if (INBS(k, NN, gw)) lip[k] = make_uint2(idx, smag(s[idx]));
+            if (INBN(k, NN, miss)) lip[k] = make_uint2(idx, smag(s[idx]));
             uint32_t c[9];
             v[0] = children(g, idx, c) > 0;
         }
         block_scan(v, sh);
         if (k < nroot) {
             uint32_t c[9];
-            if (children(g, idx, c) > 0 && INBS(sh.nlis + v[0], NN, gw)) lis[sh.nlis + v[0]] = make_uint2(idx << 1, maxd[idx]);
+            if (children(g, idx, c) > 0 && INBN(sh.nlis + v[0], NN, miss)) lis[sh.nlis + v[0]] = make_uint2(idx << 1, maxd[idx]);
         }
         __syncthreads();
         if (tid == 0) sh.nlis += sh.tot[0];
@@ -321,8 +322,8 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                     const long long k = k0 + j;
                     uint2 x = make_uint2(0, 0);
                     if (k < nl) {
-                        if (INBS(k, NN, gw)) x = lip[k];
-                        if (!INBS(x.x, NN, gw)) x.x = 0;
+                        if (INBN(k, NN, miss)) x = lip[k];
+                        if (!INBN(x.x, NN, miss)) x.x = 0;
                         const bool sg = (x.y & 0x7FFFFFFFu) >= T;
                         sgm |= (unsigned)sg << j;
                         v[0] += 1 + sg; v[1] += !sg; v[2] += sg;
@@ -339,9 +340,9 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                     if (k0 + j >= nl) break;
                     const uint2 x = xs[j];
                     if ((sgm >> j) & 1) {
-                        win_set(sh, bp, gw);
-                        if (x.y >> 31) win_set(sh, bp + 1, gw);
-                        if (INBS(ls, NN, gw)) {
+                        win_set(sh, bp, miss);
+                        if (x.y >> 31) win_set(sh, bp + 1, miss);
+                        if (INBN(ls, NN, miss)) {
                             sig_pos[x.x] = (uint32_t)(bp + 1);
                             lsp_idx[x.x] = (uint32_t)ls;
                             lsp[ls] = make_uint2(x.x, x.y & 0x7FFFFFFFu);
@@ -349,7 +350,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                         ls++;
                         bp += 2;
                     } else {
-                        if (INBS(keep, NN, gw)) lip[keep] = x;
+                        if (INBN(keep, NN, miss)) lip[keep] = x;
                         keep++;
                         bp += 1;
                     }
@@ -377,19 +378,19 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                 __syncthreads();
                 // each thread's entry of the next chunk is read one chunk ahead
                 uint2 e_next = make_uint2(0, 0);
-                if (tid < ncur && INBS(tid, NN, gw)) e_next = cur[tid];
+                if (tid < ncur && INBN(tid, NN, miss)) e_next = cur[tid];
                 for (long long base = 0; base < ncur; base += ET) {
                     const long long k = base + tid;
                     int v[NQ] = {0, 0, 0, 0, 0};
                     uint2 e = e_next;
-                    if (k + ET < ncur && INBS(k + ET, NN, gw)) e_next = cur[k + ET];
+                    if (k + ET < ncur && INBN(k + ET, NN, miss)) e_next = cur[k + ET];
                     uint32_t c[9];
                     int32_t sv[9];
                     int nc = 0;
                     bool sg = false;
                     uint32_t sigmask = 0, mlv = 0;
                     if (k < ncur) {
-                        if (!INBS(e.x >> 1, NN, gw)) e.x = 0;
+                        if (!INBN(e.x >> 1, NN, miss)) e.x = 0;
                         const uint32_t idx = e.x >> 1;
                         v[0] = 1;
                         sg = e.y >= T;
@@ -397,7 +398,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                             if (sg) {
                                 nc = children(g, idx, c);
                                 for (int q = 0; q < nc; q++) {
-                                    if (!INBS(c[q], NN, gw)) c[q] = 0;
+                                    if (!INBN(c[q], NN, miss)) c[q] = 0;
                                     sv[q] = s[c[q]];
                                     const bool cs = absi(sv[q]) >= T;
                                     sigmask |= (uint32_t)cs << q;
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                                 nc = children(g, idx, c);
                                 v[3] = nc;
                                 for (int q = 0; q < nc; q++)  // the next wave's type-A entries' maxima, read now
-                                    sv[q] = (int32_t)maxd[INBS(c[q], NN, gw) ? c[q] : 0];
+                                    sv[q] = (int32_t)maxd[INBN(c[q], NN, miss) ? c[q] : 0];
                             } else {
                                 v[4] = 1;
                             }
@@ -426,31 +427,31 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                         const uint32_t idx = e.x >> 1;
                         unsigned long long bp = sh.pos + v[0];
                         if (!sg) {
-                            if (INBS(sh.nstay + v[4], NN, gw)) lis_new[sh.nstay + v[4]] = e;
+                            if (INBN(sh.nstay + v[4], NN, miss)) lis_new[sh.nstay + v[4]] = e;
                         } else if ((e.x & 1) == 0) {
-                            win_set(sh, bp++, gw);
+                            win_set(sh, bp++, miss);
                             long long li = sh.nlip + v[1], ls = sh.nlsp + v[2];
                             for (int q = 0; q < nc; q++) {
                                 if ((sigmask >> q) & 1) {
-                                    win_set(sh, bp, gw);
-                                    if (sv[q] < 0) win_set(sh, bp + 1, gw);
+                                    win_set(sh, bp, miss);
+                                    if (sv[q] < 0) win_set(sh, bp + 1, miss);
                                     sig_pos[c[q]] = (uint32_t)(bp + 1);
                                     lsp_idx[c[q]] = (uint32_t)ls;
-                                    if (INBS(ls, NN, gw)) lsp[ls] = make_uint2(c[q], absi(sv[q]));
+                                    if (INBN(ls, NN, miss)) lsp[ls] = make_uint2(c[q], absi(sv[q]));
                                     ls++;
                                     bp += 2;
                                 } else {
-                                    if (INBS(li, NN, gw)) lip[li] = make_uint2(c[q], smag(sv[q]));
+                                    if (INBN(li, NN, miss)) lip[li] = make_uint2(c[q], smag(sv[q]));
                                     li++;
                                     bp += 1;
                                 }
                             }
-                            if (has_L(g, idx) && INBS(sh.nnext + v[3], NN, gw))
+                            if (has_L(g, idx) && INBN(sh.nnext + v[3], NN, miss))
                                 nxt[sh.nnext + v[3]] = make_uint2((idx << 1) | 1, mlv);
                         } else {
-                            win_set(sh, bp, gw);
+                            win_set(sh, bp, miss);
                             for (int q = 0; q < nc; q++)
-                                if (INBS(sh.nnext + v[3] + q, NN, gw)) nxt[sh.nnext + v[3] + q] = make_uint2(c[q] << 1, (uint32_t)sv[q]);
+                                if (INBN(sh.nnext + v[3] + q, NN, miss)) nxt[sh.nnext + v[3] + q] = make_uint2(c[q] << 1, (uint32_t)sv[q]);
                         }
                     }
                     __syncthreads();
@@ -487,7 +488,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
 #pragma unroll
                 for (int j = 0; j < EPL; j++) {
                     const long long k = k0 + j;
-                    if (k < lsp_before && INBS(k, NN, gw) && ((lsp[k].y >> n) & 1)) win_set(sh, sh.pos + k, gw);
+                    if (k < lsp_before && INBN(k, NN, miss) && ((lsp[k].y >> n) & 1)) win_set(sh, sh.pos + k, miss);
                 }
                 __syncthreads();
                 const long long end = base + (long long)ET * EPL < lsp_before ? base + (long long)ET * EPL : lsp_before;
@@ -503,6 +504,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
         *nmax_out = nmax;
         if (((sh.pos + 7) >> 3) > cap_words * 4) atomicOr(status, 1);
     }
+    guard_flush(miss, guard_word(*r));
 }
 
 // ------------------------------------------------------------ decoder

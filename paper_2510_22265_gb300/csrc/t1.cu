@@ -212,6 +212,7 @@ __host__ __device__ inline SmemLayout smem_layout(int maxn, int maxh, bool dec) 
 __global__ void __launch_bounds__(WARPS * 32) t1_encode_kernel(int32_t *qt, const BlockDesc *blk, int nblk, T1Out o,
                                                                int mark_spp_in_q, uint8_t *spp_out, SmemLayout SL,
                                                                int maxh, long long nq) {
+    bool miss = false;
     extern __shared__ __align__(16) uint8_t sm[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint8_t *base = sm + wid * SL.per_warp;
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(WARPS * 32) t1_encode_kernel(int32_t *qt, cons
         uint32_t mx = 0;
         for (int i = lane; i < n; i += 32) {
             int r = i / w, c = i - r * w;
-            int32_t v = inb_rec(d.off + (int64_t)r * d.stride + c, nq, o.status, T1_GUARD) ? qt[d.off + (int64_t)r * d.stride + c] : 0;
+            int32_t v = INBN(d.off + (int64_t)r * d.stride + c, nq, miss) ? qt[d.off + (int64_t)r * d.stride + c] : 0;
             // sign-magnitude Mallat array (bit 31 sign, bit 30 trace flag) or two's complement
             uint32_t m = mark_spp_in_q ? (uint32_t)v & 0x3FFFFFFFu : (uint32_t)(v < 0 ? -v : v);
             mag[i] = m | (v < 0 ? 0x80000000u : 0);
@@ -382,12 +383,13 @@ __global__ void __launch_bounds__(WARPS * 32) t1_encode_kernel(int32_t *qt, cons
             uint32_t f = (mag[i] >> 30) & 1;
             if (mark_spp_in_q) {
                 int64_t at = d.off + (int64_t)r * d.stride + c;
-                if (inb_rec(at, nq, o.status, T1_GUARD)) qt[at] = (qt[at] & ~0x40000000) | (int32_t)(f << 30);
+                if (INBN(at, nq, miss)) qt[at] = (qt[at] & ~0x40000000) | (int32_t)(f << 30);
             }
             if (spp_out) spp_out[(size_t)b * n + i] = (uint8_t)f;
         }
         __syncwarp();
     }
+    guard_flush(miss, o.status, T1_GUARD);
 }
 
 // ------------------------------------------------------------ warp-parallel encoder
@@ -530,6 +532,7 @@ __device__ __forceinline__ int64_t warp_sum64(int64_t v) {
 
 __global__ void __launch_bounds__(PW * 32, 8) t1_model_warp(int32_t *qt, const BlockDesc *blk, int nblk, T1Out o,
                                                          int mark_spp_in_q, uint8_t *spp_out, long long nq) {
+    bool miss = false;
     __shared__ PWShared tb;
     __shared__ uint32_t smag[PW][32][33];  // each warp's block, column-major by lane (for distortion sums)
     __shared__ __align__(16) uint32_t stage[PW][SYM_STAGE / 4];
@@ -559,7 +562,7 @@ __global__ void __launch_bounds__(PW * 32, 8) t1_model_warp(int32_t *qt, const B
             m[r] = 0;
             if (lane < w && r < h) {
                 const long long at = d.off + (long long)r * d.stride + lane;
-                const int32_t v = inb_rec(at, nq, o.status, T1_GUARD) ? qt[at] : 0;
+                const int32_t v = INBN(at, nq, miss) ? qt[at] : 0;
                 m[r] = mark_spp_in_q ? ((uint32_t)v & 0x3FFFFFFFu) : (uint32_t)(v < 0 ? -v : v);
                 NGM |= (uint64_t)(v < 0) << r;
                 mx = max(mx, m[r]);
@@ -726,12 +729,13 @@ __global__ void __launch_bounds__(PW * 32, 8) t1_model_warp(int32_t *qt, const B
             if (lane < w && r < h) {
                 const uint32_t f = (uint32_t)((SPPF >> r) & 1);
                 const long long at = d.off + (long long)r * d.stride + lane;
-                if (mark_spp_in_q && inb_rec(at, nq, o.status, T1_GUARD)) qt[at] = (qt[at] & ~0x40000000) | (int32_t)(f << 30);
+                if (mark_spp_in_q && INBN(at, nq, miss)) qt[at] = (qt[at] & ~0x40000000) | (int32_t)(f << 30);
                 if (spp_out) spp_out[(size_t)b * (w * h) + r * w + lane] = (uint8_t)f;
             }
         }
         __syncwarp();
     }
+    guard_flush(miss, o.status, T1_GUARD);
 }
 
 // MQ coding of the modelled symbols: one thread per code-block, so a warp
@@ -878,6 +882,7 @@ __global__ void __launch_bounds__(WARPS * 32) t1_decode_kernel(const uint8_t *by
                                                                float *coef, int32_t *omag, int8_t *oplane,
                                                                uint8_t *oneg, SmemLayout SL, int maxh, long long nq,
                                                                int *guard) {
+    bool miss = false;
     extern __shared__ __align__(16) uint8_t sm[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint8_t *base = sm + wid * SL.per_warp;
@@ -1007,7 +1012,7 @@ __global__ void __launch_bounds__(WARPS * 32) t1_decode_kernel(const uint8_t *by
             uint32_t m = mag[i];
             if (coef) {
                 float val = p >= 0 ? deq(m, p, d.delta) : 0.0f;
-                if (inb_rec(d.off + (int64_t)r * d.stride + c, nq, guard, T1_GUARD)) coef[d.off + (int64_t)r * d.stride + c] = ng ? -val : val;
+                if (INBN(d.off + (int64_t)r * d.stride + c, nq, miss)) coef[d.off + (int64_t)r * d.stride + c] = ng ? -val : val;
             } else {
                 omag[(size_t)b * n + i] = p >= 0 ? (int32_t)m : 0;
                 oplane[(size_t)b * n + i] = (int8_t)p;
@@ -1016,6 +1021,7 @@ __global__ void __launch_bounds__(WARPS * 32) t1_decode_kernel(const uint8_t *by
         }
         __syncwarp();
     }
+    guard_flush(miss, guard, T1_GUARD);
 }
 
 bool g_tables_ready[64];

@@ -23,17 +23,21 @@ def _axes(ny: int, nx: int):
 
 
 def _modes(rng, ny, nx, nmodes=40, kmax=8, kscale=1.0):
+    """Sum of nmodes separable modes a cos(ky theta + psi) sin(kx lambda + phi),
+    a = 1 / (kx^2 + ky^2), as one (ny x nmodes) by (nmodes x nx) product."""
     lam, theta = _axes(ny, nx)
-    out = np.zeros((ny, nx), np.float64)
+    col = np.empty((ny, nmodes), np.float64)
+    row = np.empty((nmodes, nx), np.float64)
     amax = 0.0
-    for _ in range(nmodes):
+    for m in range(nmodes):
         kx = int(rng.integers(1, kmax + 1))
         ky = int(rng.integers(1, kmax + 1))
         a = 1.0 / (kx * kx + ky * ky)
         amax = max(amax, a)
         phi, psi = rng.uniform(0, 2 * np.pi, 2)
-        out += a * np.outer(np.cos(ky * kscale * theta + psi), np.sin(kx * kscale * lam + phi))
-    return out, amax
+        col[:, m] = a * np.cos(ky * kscale * theta + psi)
+        row[m] = np.sin(kx * kscale * lam + phi)
+    return col @ row, amax
 
 
 def _vortex(out, rng, sigma, amp):

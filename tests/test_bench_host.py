@@ -23,6 +23,14 @@ def test_workload_config_names_the_stack():
     assert small["fields"] == 2 and "fit in L2" in small["l2"]
 
 
+def test_oracle_sample_spreads_over_the_stack():
+    ids = bench.sample_ids(8)
+    assert len(ids) == 8 and {v for v, _ in ids} == {0, 1, 2, 3}
+    assert all(0 <= lev < 37 for _, lev in ids) and len(set(ids)) == 8
+    c = bench.sample_config(bench.DEFAULT_SHAPE, 8)
+    assert c["fields"] == 8 and c["raw_bytes"] == 8 * 721 * 1440 * 4 and "whole 721x1440" in c["workload"]
+
+
 def test_per_step_divides_profile_totals():
     prof = [{"name": "k", "ms": 8.0, "launches": 20, "bytes": 4e9}]
     p = bench.per_step(prof, 4)
@@ -77,7 +85,9 @@ def test_reference_arm_prints_one_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "GB/s"
     assert d["higher_is_better"] is True and d["value"] > 0
-    assert d["config"] == bench.workload_config([1, 2, 91, 180])
+    cores = d["cpu_baseline"]["cores"]
+    assert d["config"] == bench.sample_config([1, 2, 91, 180], cores)
+    assert d["config"]["fields"] == cores and "whole 91x180" in d["config"]["workload"]
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

@@ -192,3 +192,50 @@ def test_escape_overflow_keeps_base_only_stream(B):
     eps = 1e-3 * (float(x.max()) - float(x.min()))
     assert _within(x, O.decompress(s, *x.shape), eps)
     assert _within(x, B.ebcc_decompress(s, *x.shape), eps)
+
+
+def test_host_batch_api(B):
+    """ebcc_compress_batch / ebcc_decompress_batch on host buffers: pageable
+    numpy arrays and page-locked torch tensors give the streams of the device
+    batch call, and decode to the device batch's output.  The 3000 x 3000
+    field (36 MB) crosses the 32 MB staging chunks in both directions."""
+    fields = [synth.smooth_field(91, 180, seed=s) for s in range(3)] + [synth.smooth_field(3000, 3000, seed=9)]
+    bounds = [1e-2, 1e-3, 5e-2, 1e-2]
+    rc, dev = B.ebcc_compress_batch_dev([torch.from_numpy(f).cuda() for f in fields], bounds)
+    assert rc == 0
+    want = [bytes(r[0][:r[1]].cpu().numpy()) for r in dev]
+    rc, host = B.ebcc_compress_batch(fields, bounds)
+    assert rc == 0 and [r[2] for r in host] == [0] * 4
+    assert [bytes(r[0][:r[1]]) for r in host] == want
+    pinned = [torch.from_numpy(f).pin_memory() for f in fields]
+    pouts = [torch.empty(B.ebcc_max_stream_bytes(*f.shape), dtype=torch.uint8).pin_memory() for f in fields]
+    rc, host2 = B.ebcc_compress_batch(pinned, bounds, outs=pouts)
+    assert rc == 0
+    assert [bytes(r[0][:r[1]].numpy()) for r in host2] == want
+    rc, ys = B.ebcc_decompress_batch(want, [f.shape for f in fields])
+    assert rc == 0
+    douts = [torch.empty(f.shape, dtype=torch.float32, device="cuda") for f in fields]
+    assert B.ebcc_decompress_batch_dev([r[0] for r in dev], [r[1] for r in dev], [f.shape for f in fields],
+                                       douts) == 0
+    for f, y, d, b in zip(fields, ys, douts, bounds):
+        assert np.array_equal(y, d.cpu().numpy())
+        assert _within(f, y, b * (float(f.max()) - float(f.min())))
+    # a bad entry fails alone
+    rc, host3 = B.ebcc_compress_batch([fields[0], fields[1]], [1e-2, -1.0])
+    assert rc == B.EBCC_EINVAL and host3[0][2] == 0 and host3[1][2] == B.EBCC_EINVAL
+
+
+@pytest.mark.parametrize("q", [0.999, 0.9999, 0.99999, 1.0])
+def test_q_parameter_against_oracle(B, q):
+    """The ablation's parameter (Materials and Methods, ablation study): at
+    every q the GPU CR is within 1% of the oracle's, the oracle decodes the
+    stream within the bound, and the stream is never longer than the base
+    layer alone at q = 1 (the fallback keeps that one when it is shorter)."""
+    for x in (synth.smooth_field(181, 360, seed=12, spikes=0.002), synth.era5_like(2, 11, 181, 360)):
+        p = B.params(q=q)
+        s, st = B.ebcc_compress(x, 1e-2, B.EBCC_BOUND_REL, p)
+        so, _ = O.compress(x, 1e-2, 1, O.params(q=q))
+        assert abs(len(so) / len(s) - 1) <= 0.01, (q, len(s), len(so))
+        eps = 1e-2 * (float(x.max()) - float(x.min()))
+        assert _within(x, O.decompress(s, *x.shape), eps)
+        assert st["len_one"] > 0 and len(s) <= st["len_one"]
