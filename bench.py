@@ -22,7 +22,9 @@ Also in the line:
   spikes) against one field per call, and the single 181x360 field;
 * the q / r0 ablation over the stack (CR relative to q = 1 per field, the
   per-field best q of the grid, r0 from 5 to 80);
-* the serving leg (Poisson arrivals through the batching server);
+* the serving leg (Poisson arrivals through the batching server: an
+  overloaded stream measures its capacity, then 10 s streams at 25%, 50% and
+  75% of it give p50 / p99 latency below capacity);
 * the roofline of the dominant kernel from the library's CUDA events and its
   device-counted bytes, in a profiled pass after the timed steps;
 * the oracle timed on the host cores on whole fields of the stack.
@@ -291,48 +293,67 @@ def ablation_leg(B, torch, dfields, outs, stream):
 
 
 # ------------------------------------------------------------------ serving
-def serving_leg(B, fields, rate, window, budget_gb, max_batch):
-    """Poisson stream of mixed requests (70% compress, 30% decompress of streams
-    made beforehand) over the workload's fields, bounds drawn from {0.1, 1, 10}%,
-    admitted by the server under an HBM budget; latency from submit to result."""
-    arrivals = synth.poisson_arrivals(rate, window, seed=5)
+def serving_run(B, srv, pool, made, rate, window, seed):
+    """One Poisson stream through an open server: mean `rate` requests/s for
+    `window` seconds, 70% compressions of the pool's fields and 30%
+    decompressions of streams made beforehand, bounds drawn from {0.1, 1, 10}%;
+    latency from submit to result inside the library."""
+    arrivals = synth.poisson_arrivals(rate, window, seed=seed)
+    lat, qs, raw, done_t, tickets = [], [], 0, [], []
+    t0 = time.perf_counter()
+    for k, (t, is_c, b) in enumerate(arrivals):
+        now = time.perf_counter() - t0
+        if t > now:
+            time.sleep(t - now)
+        i = k % len(pool)
+        if is_c:
+            tickets.append((srv.submit_compress(pool[i], b), pool[i].shape))
+        else:
+            tickets.append((srv.submit_decompress(made[(i, b)], *pool[i].shape), pool[i].shape))
+        raw += pool[i].nbytes
+    t_sub = time.perf_counter() - t0
+    for tk, shape in tickets:
+        r = None
+        while r is None:
+            r = srv.poll(tk, 1.0, shape=shape)
+        assert r["status"] == 0, r["status"]
+        lat.append(r["latency_s"])
+        qs.append(r["queue_s"])
+        done_t.append(time.perf_counter() - t0)
+    wall = max(done_t)
+    lat = np.array(lat) * 1e3
+    return {"rate_req_s": rate, "window_s": window, "requests": len(arrivals),
+            "offered_gbs": raw / max(window, t_sub) / 1e9, "sustained_gbs": raw / wall / 1e9,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "queue_p50_ms": float(np.percentile(np.array(qs) * 1e3, 50))}
+
+
+def serving_leg(B, fields, rate, budget_gb, max_batch, over_window=5.0, window=10.0):
+    """Serving under an HBM budget: first an overloaded stream (mean `rate`
+    requests/s, above what the server sustains) measures its capacity C in
+    GB/s; then 10 s streams offered at 25%, 50% and 75% of C give latency
+    below capacity."""
     pool = fields[:16]
     made = {}
     for i, f in enumerate(pool):
         for b in (1e-3, 1e-2, 1e-1):
             made[(i, b)] = B.ebcc_compress(f, b)[0]
-    lat, qs, raw = [], [], 0
-    done_t = []
+    mean_bytes = float(np.mean([f.nbytes for f in pool]))
+    out = {"hbm_budget_gb": budget_gb, "max_batch": max_batch,
+           "what": "721x1440 fields, 70% compress / 30% decompress, bounds {0.1,1,10}%, Poisson arrivals, "
+                   "latency = submit to result inside the library", "loads": []}
     with B.Server(int(budget_gb * (1 << 30)), max_batch) as srv:
-        tickets = []
-        t0 = time.perf_counter()
-        for k, (t, is_c, b) in enumerate(arrivals):
-            now = time.perf_counter() - t0
-            if t > now:
-                time.sleep(t - now)
-            i = k % len(pool)
-            if is_c:
-                tickets.append((srv.submit_compress(pool[i], b), pool[i].shape))
-            else:
-                tickets.append((srv.submit_decompress(made[(i, b)], *pool[i].shape), pool[i].shape))
-            raw += pool[i].nbytes
-        for tk, shape in tickets:
-            r = None
-            while r is None:
-                r = srv.poll(tk, 1.0, shape=shape)
-            assert r["status"] == 0, r["status"]
-            lat.append(r["latency_s"])
-            qs.append(r["queue_s"])
-            done_t.append(time.perf_counter() - t0)
-        wall = max(done_t)
-    lat = np.array(lat) * 1e3
-    return {"rate_req_s": rate, "window_s": window, "requests": len(arrivals),
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "queue_p50_ms": float(np.percentile(np.array(qs) * 1e3, 50)),
-            "sustained_gbs": raw / wall / 1e9, "offered_gbs": raw / window / 1e9,
-            "hbm_budget_gb": budget_gb, "max_batch": max_batch,
-            "what": "721x1440 fields, 70% compress / 30% decompress, bounds {0.1,1,10}%, Poisson arrivals, "
-                    "latency = submit to result inside the library"}
+        serving_run(B, srv, pool, made, 200.0, 1.0, seed=50)  # warm the workers' buffers
+        over = serving_run(B, srv, pool, made, rate, over_window, seed=5)
+        over["load"] = "overload"
+        cap = over["sustained_gbs"]
+        out["capacity_gbs"] = cap
+        for k, frac in enumerate((0.25, 0.5, 0.75)):
+            r = serving_run(B, srv, pool, made, frac * cap * 1e9 / mean_bytes, window, seed=51 + k)
+            r["load"] = f"{frac:.0%} of capacity"
+            out["loads"].append(r)
+        out["loads"].append(over)
+    return out
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -505,7 +526,7 @@ def run_gpu(args):
     ablation = ablation_leg(B, torch, dfields, outs, stream) if not args.no_legs else None
     serving = None
     if not args.no_serve:
-        serving = serving_leg(B, fields, args.serve_rate, args.serve_window, 40.0, 64)
+        serving = serving_leg(B, fields, args.serve_rate, 40.0, 64, over_window=args.serve_window)
     pool.close()
     if rank != 0:
         if dist:
@@ -589,7 +610,7 @@ def main():
                     help="variables levels ny nx")
     ap.add_argument("--plain-fields", type=int, default=8)
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="serving leg: mean requests per second")
-    ap.add_argument("--serve-window", type=float, default=0.5, help="serving leg: seconds of arrivals")
+    ap.add_argument("--serve-window", type=float, default=5.0, help="serving leg: seconds of the overloaded stream")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--uneven", type=int, default=512, help="uneven-grid batch leg: fields (0 = off)")
     ap.add_argument("--hires", type=int, default=24, help="3601x7200 batch leg: fields (0 = off)")

@@ -221,10 +221,14 @@ int ebcc_decompress_chunks_dev(const ebcc_stream_desc *streams, const size_t sha
                                float *array, void *stream);
 
 /* ---------------------------------------------------------------- serving */
-/* A device-resident request loop with continuous batching: requests that
- * arrive while others are on the GPU are admitted as slots and memory free up
- * (HBM budget), and each admitted group runs as one batch on the server's own
- * stream.  Thread-safe per handle. */
+/* A request loop with continuous batching: requests that arrive while others
+ * are on the GPU are admitted as slots and memory free up (HBM budget); two
+ * workers, each with its own stream and device buffers (kept between groups,
+ * no allocation per request), run admitted groups as batches, so groups
+ * overlap on the device.  A group's requests enter the device through a
+ * request ring in page-locked host memory, read by an intake kernel that
+ * waits on the ring's doorbell for at most 2 s (EBCC_ETIMEOUT for the group's
+ * requests if it runs out).  Thread-safe per handle. */
 typedef struct ebcc_server ebcc_server;
 
 #define EBCC_REQ_COMPRESS 0
@@ -266,6 +270,16 @@ int ebcc_server_poll(ebcc_server *s, uint64_t ticket, double timeout_s, ebcc_res
 int ebcc_server_cancel(ebcc_server *s, uint64_t ticket);
 /* Drain and destroy. */
 int ebcc_server_destroy(ebcc_server *s);
+/* Diagnostic of the server's request intake (the device-side wait the
+ * serving loop runs for every group): `bytes` bytes written into a request
+ * ring of page-locked host memory are copied to the device by the intake
+ * kernel, which waits for the ring's doorbell for at most wait_s seconds
+ * (0 < wait_s <= 60).  publish = 1: the host rings the doorbell after writing
+ * the ring, as the server does; returns EBCC_OK when the bytes arrived
+ * unchanged (ECORRUPT otherwise).  publish = 0: nothing rings it, the wait
+ * runs out and the call returns EBCC_ETIMEOUT, with the device still usable.
+ * Synchronous on `stream`.  Errors: EINVAL, ENOMEM, ECUDA. */
+int ebcc_intake_check(size_t bytes, double wait_s, int publish, void *stream);
 
 /* ------------------------------------------------ hot-path step entry points
  * Each runs one step of the device pipeline on caller-owned device buffers,

@@ -29,7 +29,7 @@ EXPORTS = [
     "ebcc_params_default", "ebcc_strerror", "ebcc_free", "ebcc_compress", "ebcc_decompress",
     "ebcc_stream_info", "ebcc_compress_batch_dev", "ebcc_decompress_batch_dev", "ebcc_max_stream_bytes",
     "ebcc_compress_batch", "ebcc_decompress_batch", "ebcc_chunk_count", "ebcc_chunk_info",
-    "ebcc_compress_chunks_dev", "ebcc_decompress_chunks_dev", "ebcc_error_stats_dev",
+    "ebcc_compress_chunks_dev", "ebcc_decompress_chunks_dev", "ebcc_error_stats_dev", "ebcc_intake_check",
     "ebcc_server_create", "ebcc_server_submit", "ebcc_server_poll", "ebcc_server_cancel",
     "ebcc_server_destroy", "ebcc_dwt_fwd_dev", "ebcc_dwt_fwd_static_dev", "ebcc_dwt_inv_dev", "ebcc_effective_levels",
     "ebcc_quantise_dev", "ebcc_band_step", "ebcc_t1_encode_dev", "ebcc_t1_decode_dev", "ebcc_pcrd_dev",
@@ -155,6 +155,7 @@ def lib():
         L.ebcc_server_poll.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.POINTER(ebcc_result)]
         L.ebcc_server_cancel.argtypes = [C.c_void_p, C.c_uint64]
         L.ebcc_server_destroy.argtypes = [C.c_void_p]
+        L.ebcc_intake_check.argtypes = [C.c_size_t, C.c_double, C.c_int, C.c_void_p]
         L.ebcc_profile_enable.argtypes = [C.c_int]
         L.ebcc_profile_get.argtypes = [C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
                                        C.POINTER(C.c_longlong), C.POINTER(C.c_double)]
@@ -459,6 +460,12 @@ def ebcc_count_within_dev(x, an_hat, mn, rng, eps_abs, guard, count_out, stream=
 
 # ------------------------------------------------------------------ serving
 EBCC_REQ_COMPRESS, EBCC_REQ_DECOMPRESS = 0, 1
+
+
+def ebcc_intake_check(nbytes: int, wait_s: float, publish: bool, stream=None) -> int:
+    """Status of one round of the server's request intake (EBCC_OK, or
+    EBCC_ETIMEOUT when the doorbell is left unset)."""
+    return lib().ebcc_intake_check(int(nbytes), float(wait_s), int(bool(publish)), C.c_void_p(_stream(stream)))
 
 
 class Server:

@@ -51,3 +51,44 @@ def test_server_rejects_request_beyond_budget():
     with B.Server(hbm_budget_bytes=1 << 20) as srv:
         with pytest.raises(B.EbccError):
             srv.submit_compress(f, 1e-2)
+
+
+def test_server_cancel_queued_request():
+    """A request still queued can be cancelled: its ticket is gone, the others
+    finish.  Three 3601 x 7200 fields (about 3 GB of workspace each) go first
+    under a 7 GiB budget: two run, the third waits at the head of the queue,
+    and admission is first come first served, so the small requests behind it
+    are certainly still queued when one of them is cancelled."""
+    from paper_2510_22265_gb300 import binding as B
+    big = synth.smooth_field(3601, 7200, seed=2)
+    small = [synth.smooth_field(91, 180, seed=10 + k) for k in range(3)]
+    with B.Server(hbm_budget_bytes=7 << 30, max_batch=1) as srv:
+        tb = [srv.submit_compress(big, 1e-2) for _ in range(3)]
+        ts = [srv.submit_compress(f, 1e-2) for f in small]
+        assert B.lib().ebcc_server_cancel(srv.h, ts[1]) == 0
+        assert B.lib().ebcc_server_cancel(srv.h, ts[1]) == B.EBCC_EINVAL  # already gone
+        with pytest.raises(B.EbccError):
+            srv.poll(ts[1], 0.0)
+        for t, f in [(tb[0], big), (tb[1], big), (tb[2], big), (ts[0], small[0]), (ts[2], small[2])]:
+            r = None
+            for _ in range(240):
+                r = srv.poll(t, 0.5, shape=f.shape)
+                if r is not None:
+                    break
+            assert r is not None and r["status"] == 0
+
+
+def test_intake_wait_times_out_and_device_stays_usable():
+    """The server's request intake waits on a doorbell with a time limit: left
+    unset, the wait runs out and reports ETIMEOUT (no hang); rung, the bytes
+    arrive unchanged; the device keeps working after the timeout."""
+    from paper_2510_22265_gb300 import binding as B
+    import time
+    t = time.perf_counter()
+    assert B.ebcc_intake_check(1 << 20, 0.05, False) == B.EBCC_ETIMEOUT
+    assert time.perf_counter() - t < 10.0
+    assert B.ebcc_intake_check(1 << 20, 2.0, True) == B.EBCC_OK
+    assert B.ebcc_intake_check(12345, 2.0, True) == B.EBCC_OK
+    f = synth.smooth_field(91, 180, seed=3)
+    s, _ = B.ebcc_compress(f, 1e-2)
+    assert np.abs(B.ebcc_decompress(s, *f.shape).astype(np.float64) - f).max() <= 1e-2 * float(f.max() - f.min())
