@@ -462,6 +462,19 @@ def decompress(data: bytes, ny: int, nx: int) -> np.ndarray:
     return out
 
 
+# ---------------------------------------------------------------- process-pool jobs
+def compress_job(args):
+    """(field, bound, kind, params dict or None) -> stream; for spawned pools."""
+    x, bound, kind, pd = args
+    return compress(x, bound, kind, params(**pd) if pd else None)[0]
+
+
+def decompress_job(args):
+    """(stream, ny, nx) -> field; for spawned pools."""
+    s, ny, nx = args
+    return decompress(s, ny, nx)
+
+
 class OracleError(RuntimeError):
     def __init__(self, code):
         super().__init__(f"oracle status {code}")
