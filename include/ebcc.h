@@ -145,6 +145,32 @@ int ebcc_decompress_batch_dev(const ebcc_stream_desc *streams, int n, float **ou
 /* Upper bound of a stream's length for an ny x nx field. */
 size_t ebcc_max_stream_bytes(size_t ny, size_t nx);
 
+/* ----------------------------------------------------- code-block autotuner */
+/* Code-block shape per grid class for batches of uneven fields.  The shape
+ * (cblk_w x cblk_h, stored in each stream's header; the paper leaves it to the
+ * JPEG 2000 codec) changes how the tier-1 work is cut and, slightly, which
+ * rate-distortion points the base layer can choose.  ebcc_autotune_cblk
+ * compresses the n probe fields (device, all of one shape) with each of
+ * 32x32, 64x64, 32x64 and 64x32 (after an untimed warm-up call each), timing
+ * them with CUDA events on `stream`, and picks the fastest shape whose total
+ * stream length is within 1% of the shortest; the choice is cached for that
+ * (ny, nx) for the life of the process.  ms[4] and bytes[4] (either may be
+ * NULL) receive each candidate's time and total length (-1: the candidate
+ * failed on these fields).  Synchronous.  Errors: EINVAL (no probe, mixed
+ * shapes, bad params), ENOMEM, ECUDA.
+ * ebcc_autotune_lookup: the cached shape of a grid class (EINVAL if none).
+ * ebcc_autotune_reset: forget every cached choice.
+ * ebcc_compress_batch_tuned_dev: ebcc_compress_batch_dev with the code-block
+ * shape of each field's grid class taken from the cache, tuning (on up to 4
+ * fields of the batch) the classes not cached yet; fields that share a shape
+ * are compressed as one batch.  p's cblk_w / cblk_h are ignored. */
+int ebcc_autotune_cblk(const ebcc_field_desc *probe, int n, const ebcc_params *p, int *cblk_w, int *cblk_h,
+                       double *ms, long long *bytes, void *stream);
+int ebcc_autotune_lookup(size_t ny, size_t nx, int *cblk_w, int *cblk_h);
+void ebcc_autotune_reset(void);
+int ebcc_compress_batch_tuned_dev(const ebcc_field_desc *fields, int n, ebcc_out_desc *outs, const ebcc_params *p,
+                                  void *stream);
+
 /* --------------------------------------------------- batched host-buffer API */
 /* The batch calls above with every buffer in host memory (Algorithm 1 KwIn /
  * KwOut: the arrays in, the byte sequences out).  fields[i].field points to
@@ -300,13 +326,15 @@ int ebcc_dwt_fwd_dev(const float *in, float *out, size_t ny, size_t nx, int leve
  * device memory is fully committed to its own pools -- call this one instead.
  * Its scratch is one static device array of EBCC_DWT_STATIC_SCRATCH_FLOATS
  * floats (8 MiB) per device, owned by the library; the call needs
- * ceil(ny/2)*ceil(nx/2) + 16 floats (rounded up to 64) plus
- * ceil(ny/4)*ceil(nx/4) + 16, i.e. fields up to about 6.7 M points
- * (1441 x 2880 fits), and returns EBCC_ECAPACITY, touching nothing, beyond
- * that.  Nothing in the scratch has to start at zero.  The first call on a
- * device looks up the array's address (cudaGetSymbolAddress, with that device
- * current) and may load the module, so make it before any latency-critical
- * or captured region.  All calls on one device share the scratch: calls that
+ * ceil(ny/2) * r4(ceil(nx/2)) + 16 floats (rounded up to 64) plus
+ * ceil(ny/4) * r4(ceil(nx/4)) + 16, r4 rounding up to a multiple of 4, i.e.
+ * fields up to about 6.7 M points (1441 x 2880 fits), and returns
+ * EBCC_ECAPACITY, touching nothing, beyond that.  Nothing in the scratch has
+ * to start at zero.  The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress, with that device current) and may load the module,
+ * so make it before any latency-critical region; the address is kept for the
+ * life of the process, so the call must not be used after a cudaDeviceReset
+ * of that device.  All calls on one device share the scratch: calls that
  * can overlap in time (different streams, or threads without ordering) race
  * on it and must be serialised by the caller.  Asynchronous on `stream`: the
  * caller synchronises before reading `out`.  Arguments and errors otherwise as

@@ -30,6 +30,7 @@ EXPORTS = [
     "ebcc_stream_info", "ebcc_compress_batch_dev", "ebcc_decompress_batch_dev", "ebcc_max_stream_bytes",
     "ebcc_compress_batch", "ebcc_decompress_batch", "ebcc_chunk_count", "ebcc_chunk_info",
     "ebcc_compress_chunks_dev", "ebcc_decompress_chunks_dev", "ebcc_error_stats_dev", "ebcc_intake_check",
+    "ebcc_autotune_cblk", "ebcc_autotune_lookup", "ebcc_autotune_reset", "ebcc_compress_batch_tuned_dev",
     "ebcc_server_create", "ebcc_server_submit", "ebcc_server_poll", "ebcc_server_cancel",
     "ebcc_server_destroy", "ebcc_dwt_fwd_dev", "ebcc_dwt_fwd_static_dev", "ebcc_dwt_inv_dev", "ebcc_effective_levels",
     "ebcc_quantise_dev", "ebcc_band_step", "ebcc_t1_encode_dev", "ebcc_t1_decode_dev", "ebcc_pcrd_dev",
@@ -117,6 +118,13 @@ def lib():
                                                 C.c_void_p]
         L.ebcc_error_stats_dev.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_size_t, C.c_double, C.c_int,
                                            C.c_void_p, C.POINTER(ebcc_error_stats), C.c_void_p]
+        L.ebcc_autotune_cblk.argtypes = [C.POINTER(ebcc_field_desc), C.c_int, C.POINTER(ebcc_params),
+                                         C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                         C.POINTER(C.c_longlong), C.c_void_p]
+        L.ebcc_autotune_lookup.argtypes = [C.c_size_t, C.c_size_t, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.ebcc_autotune_reset.argtypes = []
+        L.ebcc_compress_batch_tuned_dev.argtypes = [C.POINTER(ebcc_field_desc), C.c_int, C.POINTER(ebcc_out_desc),
+                                                    C.POINTER(ebcc_params), C.c_void_p]
         L.ebcc_chunk_count.restype = C.c_longlong
         L.ebcc_chunk_count.argtypes = [C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
         L.ebcc_chunk_info.argtypes = [C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.c_longlong,
@@ -378,6 +386,46 @@ def ebcc_decompress_chunks_dev(streams, lens, shape, chunk, out, stream=None):
         sd[k] = ebcc_stream_desc(streams[k].data_ptr(), int(lens[k]), ny, nx)
     return lib().ebcc_decompress_chunks_dev(sd, _size4(shape), _size4(chunk), C.c_void_p(out.data_ptr()),
                                             C.c_void_p(_stream(stream)))
+
+
+def ebcc_compress_batch_tuned_dev(fields, bounds, kinds=None, p: ebcc_params | None = None, stream=None,
+                                  outs=None):
+    """ebcc_compress_batch_dev with autotuned code-block shapes per grid class."""
+    import torch
+    n = len(fields)
+    kinds = kinds or [EBCC_BOUND_REL] * n
+    fd = (ebcc_field_desc * max(n, 1))()
+    od = (ebcc_out_desc * max(n, 1))()
+    bufs = []
+    for i, f in enumerate(fields):
+        ny, nx = f.shape
+        fd[i] = ebcc_field_desc(f.data_ptr(), ny, nx, float(bounds[i]), int(kinds[i]))
+        b = outs[i] if outs is not None else torch.empty(ebcc_max_stream_bytes(ny, nx), dtype=torch.uint8,
+                                                        device=f.device)
+        bufs.append(b)
+        od[i].stream = b.data_ptr()
+        od[i].capacity = b.numel()
+    rc = lib().ebcc_compress_batch_tuned_dev(fd, n, od, C.byref(p) if p else None, C.c_void_p(_stream(stream)))
+    return rc, [(bufs[i], od[i].len, od[i].status, stats_dict(od[i].stats)) for i in range(n)]
+
+
+def ebcc_autotune_cblk(fields, bounds, p: ebcc_params | None = None, stream=None):
+    """Tune the code-block shape on probe fields of one shape: ((w, h), ms[4], bytes[4])."""
+    n = len(fields)
+    fd = (ebcc_field_desc * n)()
+    for i, f in enumerate(fields):
+        fd[i] = ebcc_field_desc(f.data_ptr(), f.shape[0], f.shape[1], float(bounds[i]), EBCC_BOUND_REL)
+    w, h = C.c_int(), C.c_int()
+    ms, by = (C.c_double * 4)(), (C.c_longlong * 4)()
+    _check(lib().ebcc_autotune_cblk(fd, n, C.byref(p) if p else None, C.byref(w), C.byref(h), ms, by,
+                                    C.c_void_p(_stream(stream))), "ebcc_autotune_cblk")
+    return (w.value, h.value), list(ms), list(by)
+
+
+def ebcc_autotune_lookup(ny: int, nx: int):
+    w, h = C.c_int(), C.c_int()
+    rc = lib().ebcc_autotune_lookup(ny, nx, C.byref(w), C.byref(h))
+    return (w.value, h.value) if rc == EBCC_OK else None
 
 
 def ebcc_decompress_batch_dev(streams, lens, shapes, outs, stream=None):

@@ -39,6 +39,10 @@ __device__ __forceinline__ int reflect(int i, int n) {
 }
 
 __device__ __forceinline__ int ceil_sh(int n, int l) { return (int)(((long long)n + (1LL << l) - 1) >> l); }
+// row stride of the LL scratch of level l: its width rounded up to 4 floats,
+// so every row starts on a 16-byte boundary (the tensor-memory-access path
+// copies whole rows)
+__device__ __forceinline__ int lstride(int nx, int l) { return (ceil_sh(nx, l) + 3) & ~3; }
 
 // Every index of the level kernels is in range by construction: reflect()
 // keeps a tile's halo inside [0, hp) x [0, wp); an LL sample (sy, sx) lies in
@@ -67,11 +71,11 @@ __global__ void __launch_bounds__(96) fwd_level(Live lv, const __grid_constant__
     const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
     if (ty0 >= hp || tx0 >= wp) return;
     const float *__restrict__ src = l == 1 ? plane_ptr(*r, src_plane) : (((l - 1) & 1) ? r->s1 : r->s2);
-    const int ss = l == 1 ? nx : wp;
+    const int ss = l == 1 ? nx : lstride(nx, l - 1);
     const bool last = l == L;
     float *__restrict__ ll = last ? nullptr : ((l & 1) ? r->s1 : r->s2);
     float *__restrict__ coef = r->W;
-    const int hl = (hp + 1) >> 1, wl = (wp + 1) >> 1, ls = wl;
+    const int hl = (hp + 1) >> 1, wl = (wp + 1) >> 1, ls = lstride(nx, l);
     const double mn = r->mn, inv = r->inv_range;
     if (!level_extents_ok(*r, l, hp, wp)) return;
     const int tid = threadIdx.x;
@@ -232,9 +236,9 @@ __global__ void __launch_bounds__(IT, 12) inv_level(Live lv, const __grid_consta
     }
     const float *__restrict__ coef = plane_ptr(*r, src_plane);
     const float *__restrict__ ll = l < L ? (((l + 1) & 1) ? r->s2 : r->s1) : coef;
-    const int ls = l < L ? ceil_sh(nx, l) : nx;
+    const int ls = l < L ? lstride(nx, l) : nx;
     float *__restrict__ dst = l == 1 ? plane_ptr(*r, fin.dst) : ((l & 1) ? r->s2 : r->s1);
-    const int ds = l == 1 ? nx : wp;
+    const int ds = l == 1 ? nx : lstride(nx, l - 1);
     constexpr int mode = MODE;
     if (!level_extents_ok(*r, l, hp, wp)) return;
     const int hl = (hp + 1) >> 1, wl = (wp + 1) >> 1;
@@ -446,6 +450,7 @@ int dwt_inverse_b(const Live &lv, const FieldRun &one, int nslots, const BatchDi
         PROF("inv_identity", st, 0.0, inv_identity<<<dim3(pgrid(d.maxN, nslots), nslots), NT, 0, st>>>(lv, one, src, fin));
         CK(cudaGetLastError());
     }
+    if (d.tma && lv.tab && d.tma_err) return dwt_inverse_tma(lv, nslots, d, src, fin, d.tma_err, st);
     for (int l = d.maxL; l >= 1; l--) {
         const int hp = d.h[l - 1], wp = d.w[l - 1];
         // field slot fastest: the tiles of a field are spread over the launch,

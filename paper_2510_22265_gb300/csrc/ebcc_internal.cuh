@@ -146,6 +146,7 @@ struct FieldRun {
     long long in_len;
     long long base_len, res_len, n_esc;  // decoder: section sizes from the header
     FieldScal *sc;
+    const void *tm;                // device tensor maps of the staged inverse DWT (null: not used)
 };
 
 // Which fields a launch covers: grid slot k serves table entry idx[k] while
@@ -265,6 +266,8 @@ struct BatchDims {
     int maxnblk;
     int h[EBCC_MAX_LEVELS + 1], w[EBCC_MAX_LEVELS + 1];
     bool any_L0;
+    bool tma;       // every field of the batch has tensor maps: the inverse levels use the staged kernel
+    int *tma_err;   // device word the staged kernel sets when a wait runs out
 };
 void batch_dims_add(BatchDims &d, int ny, int nx, int L, int nblk);
 void batch_dims_init(BatchDims &d);
@@ -285,11 +288,24 @@ int dwt_forward_b(const Live &lv, const FieldRun &one, int nslots, const BatchDi
 // inverse: plane `src` (W or R), finished per fin
 int dwt_inverse_b(const Live &lv, const FieldRun &one, int nslots, const BatchDims &d, int src, InvFinal fin,
                   cudaStream_t st);
-// single-field forms on plain pointers (scratch s1 >= ceil(ny/2)*ceil(nx/2)+16
-// floats, s2 >= ceil(ny/4)*ceil(nx/4)+16)
+// floats of the DWT's two LL scratch regions of an ny x nx field: which = 1
+// holds the LL bands of odd levels, which = 2 those of even levels; rows are
+// padded to a multiple of 4 floats
+inline size_t dwt_scratch_floats(size_t ny, size_t nx, int which) {
+    const size_t d = which == 1 ? 2 : 4;
+    return ((ny + d - 1) / d) * ((((nx + d - 1) / d) + 3) & ~(size_t)3) + 16;
+}
+// single-field forms on plain pointers (scratch s1 >= dwt_scratch_floats(ny,
+// nx, 1) floats, s2 >= dwt_scratch_floats(ny, nx, 2))
 int dwt_forward(const float *in, float *coef, float *s1, float *s2, int ny, int nx, int L, double norm_min,
                 double norm_inv_range, cudaStream_t st);
 int dwt_inverse_plain(const float *coef, float *out, float *s1, float *s2, int ny, int nx, int L, cudaStream_t st);
+// staged (tensor-memory-access) inverse: bytes of a map table for n fields;
+// maps of the listed fields (host table, device copy) -- true when all of
+// them can use it; the inverse levels of a batch on that path
+size_t tma_table_bytes(int nfields);
+bool tma_build_maps(std::vector<FieldRun> &run, const std::vector<int> &use, void *host_table, void *dev_table);
+int dwt_inverse_tma(const Live &lv, int nslots, const BatchDims &d, int src, InvFinal fin, int *err, cudaStream_t st);
 
 // ------------------------------------------------------------ tier-1
 struct T1Out {

@@ -43,11 +43,12 @@ extern "C" int ebcc_dwt_fwd_static_dev(const float *in, float *out, size_t ny, s
                                        double norm_min, double norm_range, void *stream) {
     if (ny == 0 || nx == 0 || ny > (1u << 30) || nx > (1u << 30) || ny * nx >= 0x7FFFFFFFull) return EBCC_EINVAL;
     if (levels < 0 || !in || !out) return EBCC_EINVAL;
-    // region 1 holds ceil(ny/2) x ceil(nx/2) floats, region 2 ceil(ny/4) x
-    // ceil(nx/4), each with 16 floats of slack; region 2 starts 256-byte aligned
-    const size_t n1 = ((ny + 1) / 2) * ((nx + 1) / 2) + 16;
+    // region 1 holds ceil(ny/2) rows of ceil(nx/2) floats, region 2 ceil(ny/4)
+    // rows of ceil(nx/4), each row padded to a multiple of 4 floats, each
+    // region with 16 floats of slack; region 2 starts 256-byte aligned
+    const size_t n1 = dwt_scratch_floats(ny, nx, 1);
     const size_t n1a = (n1 + 63) / 64 * 64;
-    const size_t n2 = ((ny + 3) / 4) * ((nx + 3) / 4) + 16;
+    const size_t n2 = dwt_scratch_floats(ny, nx, 2);
     if (n1a + n2 > kScratchFloats) return EBCC_ECAPACITY;
     float *s = nullptr;
     RC(scratch_address(&s));

@@ -684,8 +684,8 @@ int arena_reserve(Arena &a, size_t bytes) {
 namespace {
 
 // DWT scratch: the level-1 and level-2 LL bands
-size_t scratch1(size_t ny, size_t nx) { return ((ny + 1) / 2) * ((nx + 1) / 2) + 16; }
-size_t scratch2(size_t ny, size_t nx) { return ((ny + 3) / 4) * ((nx + 3) / 4) + 16; }
+size_t scratch1(size_t ny, size_t nx) { return dwt_scratch_floats(ny, nx, 1); }
+size_t scratch2(size_t ny, size_t nx) { return dwt_scratch_floats(ny, nx, 2); }
 
 // bump allocation in an arena; with a null base it only measures
 template <typename T>
@@ -782,6 +782,8 @@ struct Batch {
     long long Ntot = 0;
     int Btot = 0;
     int cap_blk = 0;
+    void *tmaps = nullptr;          // tensor maps of the staged inverse DWT, TM_PER_FIELD per field
+    int *tma_err = nullptr;         // set by the staged inverse when one of its waits ran out
 };
 
 Live live_of(const Batch &b) { return Live{b.d_run, b.live + 1, b.live}; }
@@ -795,6 +797,30 @@ int set_list(Engine &e, Batch &b, const std::vector<int> &lst, cudaStream_t st) 
 }
 
 const FieldRun kNone{};  // placeholder `one` argument of batched launches
+
+// tensor maps of the staged inverse DWT for the fields in L (pointers of the
+// table already laid out); the batch uses that path when every one has them
+int stage_maps(Engine &e, Batch &b, const std::vector<int> &L, cudaStream_t st) {
+    b.dims.tma = false;
+    b.dims.tma_err = b.tma_err;
+    static const bool off = [] {
+        // the staged kernel is opt-in ("1") while it is slower than the
+        // register-staged one on the benchmarked batches
+        const char *v = getenv("EBCC_INV_TMA");
+        return !(v && v[0] == '1');
+    }();
+    if (L.empty() || !b.tmaps || off) return EBCC_OK;
+    const size_t bytes = tma_table_bytes(b.F);
+    uint8_t *ht = stage_take<uint8_t>(e, bytes + 128);
+    if (!ht) return EBCC_OK;  // no staging room: the plain inverse kernels run
+    ht = (uint8_t *)(((uintptr_t)ht + 127) & ~(uintptr_t)127);
+    if (tma_build_maps(b.run, L, ht, b.tmaps)) {
+        CK(cudaMemcpyAsync(b.tmaps, ht, bytes, cudaMemcpyHostToDevice, st));
+        b.dims.tma = true;
+    }
+    CK(cudaMemsetAsync(b.tma_err, 0, sizeof(int), st));
+    return EBCC_OK;
+}
 
 // Shapes of the fields of a compression batch: lays out every buffer (a dry
 // run with a null arena measures it) and fills the pointers of the table.
@@ -858,6 +884,8 @@ void layout_compress(Arena &a, Batch &b, const std::vector<int> &ny, const std::
     b.d_run = carve<FieldRun>(a, F);
     b.d_geom = carve<FieldGeom>(a, F);
     b.d_sc = carve<FieldScal>(a, F);
+    b.tmaps = carve<uint8_t>(a, tma_table_bytes(F));
+    b.tma_err = carve<int>(a, 4);
     b.bl = carve<BaseLoop>(a, F);
     b.evc = carve<EvalCache>(a, F);
     b.tl = carve<TruncLoop>(a, F);
@@ -920,6 +948,8 @@ void layout_decompress(Arena &a, Batch &b, const std::vector<int> &ny, const std
     b.d_run = carve<FieldRun>(a, F);
     b.d_geom = carve<FieldGeom>(a, F);
     b.d_sc = carve<FieldScal>(a, F);
+    b.tmaps = carve<uint8_t>(a, tma_table_bytes(F));
+    b.tma_err = carve<int>(a, 4);
     b.live = carve<int>(a, F + 1);
     b.list = carve<int>(a, F + 1);
     for (int f = 0; f < F; f++) {
@@ -1198,6 +1228,7 @@ int compress_batch(Engine &e, const ebcc_field_desc *fd, int n, ebcc_out_desc *o
         batch_dims_add(b.dims, ny[f], nx[f], L[f], r.nblk);
     }
     const int Bact = blk0;
+    RC(stage_maps(e, b, A, st));
     RC(upload(e, b.d_run, b.run.data(), F * sizeof(FieldRun), st));
     RC(upload(e, b.d_geom, b.geom.data(), F * sizeof(FieldGeom), st));
     RC(upload(e, b.d_blk, b.blk.data(), b.blk.size() * sizeof(BlockDesc), st));
@@ -1423,8 +1454,10 @@ int compress_batch(Engine &e, const ebcc_field_desc *fd, int n, ebcc_out_desc *o
     // ---- range checks that missed: such a field fails instead of returning a
     // stream built around a skipped access
     RC(download(e, b.d_sc, F, &hs, st));
+    int *terr = nullptr;
+    RC(download(e, b.tma_err, 1, &terr, st));
     for (int f = 0; f < F; f++)
-        if (hs[f].guard && !status[f]) status[f] = EBCC_ECUDA;
+        if ((hs[f].guard || (b.dims.tma && *terr)) && !status[f]) status[f] = EBCC_ECUDA;
     if (prof_enabled()) {
         double pb = 0;
         for (int f = 0; f < F; f++) pb += (double)hs[f].prof_bytes;
@@ -1562,6 +1595,7 @@ int decompress_batch(Engine &e, const ebcc_stream_desc *sd, int n, float *const 
             if (h.ne) E.push_back(f);
         }
         for (int f : T) batch_dims_add(b.dims, ny[f], nx[f], 0, 0);
+        RC(stage_maps(e, b, D, st));
         RC(upload(e, b.d_run, b.run.data(), F * sizeof(FieldRun), st));
         RC(upload(e, b.d_geom, b.geom.data(), F * sizeof(FieldGeom), st));
         RC(upload(e, b.d_sc, sc.data(), F * sizeof(FieldScal), st));
@@ -1620,8 +1654,10 @@ int decompress_batch(Engine &e, const ebcc_stream_desc *sd, int n, float *const 
             RC(download(e, b.t1.status, 1, &t1s, st));
             for (int f : E)
                 if (!hs[f].ok) status[vin[f]] = EBCC_ECORRUPT;
+            int *terr = nullptr;
+            RC(download(e, b.tma_err, 1, &terr, st));
             for (int f = 0; f < F; f++)
-                if (hs[f].guard && !status[vin[f]]) status[vin[f]] = EBCC_ECUDA;
+                if ((hs[f].guard || (b.dims.tma && *terr)) && !status[vin[f]]) status[vin[f]] = EBCC_ECUDA;
             if (prof_enabled()) {
                 double pb = 0;
                 for (int f = 0; f < F; f++) pb += (double)hs[f].prof_bytes;

@@ -47,8 +47,8 @@ int ebcc_dwt_fwd_dev(const float *in, float *out, size_t ny, size_t nx, int leve
     int L = effective_levels((int)ny, (int)nx, levels);
     Tmp t;
     float *s1, *s2;
-    RC(t.get(&s1, ((ny + 1) / 2) * ((nx + 1) / 2) + 16));
-    RC(t.get(&s2, ((ny + 3) / 4) * ((nx + 3) / 4) + 16));
+    RC(t.get(&s1, dwt_scratch_floats(ny, nx, 1)));
+    RC(t.get(&s2, dwt_scratch_floats(ny, nx, 2)));
     double inv = norm_range > 0 ? 1.0 / norm_range : 0.0;
     RC(dwt_forward(in, out, s1, s2, (int)ny, (int)nx, L, norm_min, inv, (cudaStream_t)stream));
     CK(cudaStreamSynchronize((cudaStream_t)stream));
@@ -61,8 +61,8 @@ int ebcc_dwt_inv_dev(const float *in, float *out, size_t ny, size_t nx, int leve
     int L = effective_levels((int)ny, (int)nx, levels);
     Tmp t;
     float *s1, *s2;
-    RC(t.get(&s1, ((ny + 1) / 2) * ((nx + 1) / 2) + 16));
-    RC(t.get(&s2, ((ny + 3) / 4) * ((nx + 3) / 4) + 16));
+    RC(t.get(&s1, dwt_scratch_floats(ny, nx, 1)));
+    RC(t.get(&s2, dwt_scratch_floats(ny, nx, 2)));
     RC(dwt_inverse_plain(in, out, s1, s2, (int)ny, (int)nx, L, (cudaStream_t)stream));
     CK(cudaStreamSynchronize((cudaStream_t)stream));
     return EBCC_OK;
