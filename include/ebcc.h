@@ -214,6 +214,30 @@ typedef struct {
 int ebcc_error_stats_dev(const float *x, const float *x_hat, size_t ny, size_t nx, double eps, int nbins,
                          unsigned long long *hist, ebcc_error_stats *out, void *stream);
 
+/* --------------------------------------------------- JPEG 2000 codestream */
+/* The base layer of an EBCC stream rewritten as a JPEG 2000 Part 1
+ * codestream (Materials and Methods: the base layer is a JPEG 2000 image; the
+ * syntax is ITU-T T.800 Annex A markers and Annex B packets).  No coding pass
+ * is re-encoded: each code-block's kept passes and MQ codeword are copied.
+ * The codestream has one tile, one signed 16-bit component, one quality
+ * layer, LRCP progression, one precinct per resolution, the stream's
+ * code-block size, default code-block style and the 9/7 irreversible
+ * transform with scalar expounded quantisation.  A sample s stands for
+ * mn + s / 16384 * (mx - mn) of the field (the stream's minimum and maximum,
+ * also written as text in a COM marker): band b's step is 16384 times the
+ * base layer's normalised step, i.e. exponent epsilon_b = 2 + gain_b + e_b
+ * (gain_b = 0, 1, 1, 2 for LL, HL, LH, HH) and the same 11-bit mantissa; the
+ * guard bits are the fewest (at least 1) that give every block's bit-planes
+ * room, and a block's zero bit-planes are G + epsilon_b - 1 - K.  The residual
+ * layer and the escape list are not part of it.
+ * stream/len: a host EBCC stream.  *out: a host buffer the library allocates
+ * and the caller releases with ebcc_free; *out_len its length.  Host code only
+ * (no device work, callable without a GPU).
+ * Errors: EINVAL (NULL argument, or a constant field: no base layer),
+ * ECORRUPT (malformed stream), ECAPACITY (a step exponent outside 0..31 or
+ * more than 7 guard bits needed), ENOMEM. */
+int ebcc_j2k_codestream(const uint8_t *stream, size_t len, uint8_t **out, size_t *out_len);
+
 /* ------------------------------------------------------------- N-D chunks */
 /* The N-D front end (Materials and Methods, first paragraph): a 4-D float32
  * array of shape[4] = (T, P, H, W) -- time, level, latitude, longitude --

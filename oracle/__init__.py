@@ -453,6 +453,17 @@ def decompress_chunks(streams, shape, chunk) -> np.ndarray:
     return out
 
 
+def base_decode(data: bytes, ny: int, nx: int) -> np.ndarray:
+    """The base layer alone of a stream, reconstructed in normalised units
+    (FP64): kept passes, midpoint dequantisation, inverse DWT."""
+    buf = np.frombuffer(data, np.uint8).copy()
+    out = np.zeros((ny, nx), np.float64)
+    st = lib().or_base_decode(_p(buf, C.c_uint8), C.c_long(len(data)), ny, nx, _p(out, C.c_double))
+    if st != 0:
+        raise OracleError(st)
+    return out
+
+
 def decompress(data: bytes, ny: int, nx: int) -> np.ndarray:
     buf = np.frombuffer(data, np.uint8).copy()
     out = np.zeros((ny, nx), np.float32)

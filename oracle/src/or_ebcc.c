@@ -506,26 +506,10 @@ static long get_varint(const uint8_t *p, long avail, unsigned long *v) {
     return -1;
 }
 
-int or_decompress(const uint8_t *s, long len, float *out, int ny, int nx) {
-    if (len < HDR || memcmp(s, "EBC1", 4) != 0 || s[4] != 1) return OR_ECORRUPT;
-    int flags = s[5], L = s[6], lw = s[7], lh = s[8], P = s[9];
-    int es = (int8_t)s[10], nmax = (int8_t)s[11];
-    if ((int)get_u32(s + 12) != ny || (int)get_u32(s + 16) != nx) return OR_EINVAL;
-    long bl = get_u32(s + 20), rl = get_u32(s + 24), ne = get_u32(s + 28);
-    double mn = get_f64(s + 32), mx = get_f64(s + 40);
-    long N = (long)ny * nx;
-    if (flags & FLAG_CONST) {
-        for (long i = 0; i < N; i++) out[i] = (float)mn;
-        return OR_OK;
-    }
-    if (HDR + bl + rl + 8 * ne != len || lw < 2 || lw > 6 || lh < 2 || lh > 6) return OR_ECORRUPT;
-    if (L != or_effective_levels(ny, nx, L)) return OR_ECORRUPT;
-    fctx F;
-    memset(&F, 0, sizeof(F));
-    fctx *f = &F;
-    setup_geometry(f, ny, nx, L, 1 << lw, 1 << lh, P);
-    double range = mx - mn;
-    double *W = (double *)calloc(N, sizeof(double));
+/* the base section of a stream decoded and inverse-transformed into W
+ * (normalised units, FP64): the kept passes of every code-block, midpoint
+ * dequantisation (reading c5), the inverse DWT */
+static int decode_base(const uint8_t *s, long bl, fctx *f, double *W) {
     const uint8_t *b = s + HDR;
     long pos = 0;
     int *np = (int *)malloc(sizeof(int) * f->nblocks), *K = (int *)malloc(sizeof(int) * f->nblocks);
@@ -557,15 +541,57 @@ int or_decompress(const uint8_t *s, long len, float *out, int ny, int nx) {
             for (int xx = 0; xx < B->w; xx++) {
                 int j = y * B->w + xx;
                 double v = pl[j] < 0 ? 0.0 : ((double)mg[j] + 0.5 * ldexp(1.0, pl[j])) * d;
-                W[(long)(B->y0 + y) * nx + B->x0 + xx] = ng[j] ? -v : v;
+                W[(long)(B->y0 + y) * f->nx + B->x0 + xx] = ng[j] ? -v : v;
             }
         free(mg); free(pl); free(ng);
         pos += bl_k[k];
     }
     if (st == OR_OK && pos != bl) st = OR_ECORRUPT;
+    if (st == OR_OK) or_dwt_inv(W, f->ny, f->nx, f->L);
+    free(np); free(K); free(bl_k);
+    return st;
+}
+
+int or_base_decode(const uint8_t *s, long len, int ny, int nx, double *out) {
+    if (len < HDR || memcmp(s, "EBC1", 4) != 0 || s[4] != 1) return OR_ECORRUPT;
+    int flags = s[5], L = s[6], lw = s[7], lh = s[8], P = s[9];
+    if ((int)get_u32(s + 12) != ny || (int)get_u32(s + 16) != nx) return OR_EINVAL;
+    if (flags & FLAG_CONST) return OR_EINVAL;
+    long bl = get_u32(s + 20);
+    if (HDR + bl > len || lw < 2 || lw > 6 || lh < 2 || lh > 6) return OR_ECORRUPT;
+    if (L != or_effective_levels(ny, nx, L)) return OR_ECORRUPT;
+    fctx F;
+    memset(&F, 0, sizeof(F));
+    setup_geometry(&F, ny, nx, L, 1 << lw, 1 << lh, P);
+    memset(out, 0, sizeof(double) * (long)ny * nx);
+    int st = decode_base(s, bl, &F, out);
+    free_ctx(&F);
+    return st;
+}
+
+int or_decompress(const uint8_t *s, long len, float *out, int ny, int nx) {
+    if (len < HDR || memcmp(s, "EBC1", 4) != 0 || s[4] != 1) return OR_ECORRUPT;
+    int flags = s[5], L = s[6], lw = s[7], lh = s[8], P = s[9];
+    int es = (int8_t)s[10], nmax = (int8_t)s[11];
+    if ((int)get_u32(s + 12) != ny || (int)get_u32(s + 16) != nx) return OR_EINVAL;
+    long bl = get_u32(s + 20), rl = get_u32(s + 24), ne = get_u32(s + 28);
+    double mn = get_f64(s + 32), mx = get_f64(s + 40);
+    long N = (long)ny * nx;
+    if (flags & FLAG_CONST) {
+        for (long i = 0; i < N; i++) out[i] = (float)mn;
+        return OR_OK;
+    }
+    if (HDR + bl + rl + 8 * ne != len || lw < 2 || lw > 6 || lh < 2 || lh > 6) return OR_ECORRUPT;
+    if (L != or_effective_levels(ny, nx, L)) return OR_ECORRUPT;
+    fctx F;
+    memset(&F, 0, sizeof(F));
+    fctx *f = &F;
+    setup_geometry(f, ny, nx, L, 1 << lw, 1 << lh, P);
+    double range = mx - mn;
+    double *W = (double *)calloc(N, sizeof(double));
+    int st = decode_base(s, bl, f, W);
     double *Ar = (double *)calloc(N, sizeof(double));
     if (st == OR_OK) {
-        or_dwt_inv(W, ny, nx, L);
         if ((flags & FLAG_RES) && rl > 0) {
             int32_t *dm = (int32_t *)malloc(sizeof(int32_t) * N);
             int8_t *dp = (int8_t *)malloc(N);
@@ -586,7 +612,7 @@ int or_decompress(const uint8_t *s, long len, float *out, int ny, int nx) {
             memcpy(&out[idx], e + 8 * k + 4, 4);
         }
     }
-    free(W); free(Ar); free(np); free(K); free(bl_k);
+    free(W); free(Ar);
     free_ctx(f);
     return st;
 }

@@ -166,6 +166,9 @@ int or_base_loop_trace(double (*qa)(double), double r0, double tol, double q, in
 int or_compress(const float *x, int ny, int nx, double bound, int kind, const or_params *p,
                 uint8_t **out, long *out_len, or_stats *st);
 int or_decompress(const uint8_t *s, long len, float *out, int ny, int nx);
+/* the base layer of a stream alone, reconstructed in normalised units (FP64,
+ * ny*nx values): the quantity the JPEG2000 codestream export carries */
+int or_base_decode(const uint8_t *s, long len, int ny, int nx, double *out);
 void or_free(void *p);
 
 #endif

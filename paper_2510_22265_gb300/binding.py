@@ -30,6 +30,7 @@ EXPORTS = [
     "ebcc_stream_info", "ebcc_compress_batch_dev", "ebcc_decompress_batch_dev", "ebcc_max_stream_bytes",
     "ebcc_compress_batch", "ebcc_decompress_batch", "ebcc_chunk_count", "ebcc_chunk_info",
     "ebcc_compress_chunks_dev", "ebcc_decompress_chunks_dev", "ebcc_error_stats_dev", "ebcc_intake_check",
+    "ebcc_j2k_codestream",
     "ebcc_autotune_cblk", "ebcc_autotune_lookup", "ebcc_autotune_reset", "ebcc_compress_batch_tuned_dev",
     "ebcc_server_create", "ebcc_server_submit", "ebcc_server_poll", "ebcc_server_cancel",
     "ebcc_server_destroy", "ebcc_dwt_fwd_dev", "ebcc_dwt_fwd_static_dev", "ebcc_dwt_inv_dev", "ebcc_effective_levels",
@@ -112,6 +113,7 @@ def lib():
         L.ebcc_stream_info.argtypes = [C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t),
                                        C.POINTER(C.c_double)]
         L.ebcc_free.argtypes = [C.c_void_p]
+        L.ebcc_j2k_codestream.argtypes = [C.c_void_p, C.c_size_t, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t)]
         L.ebcc_compress_batch_dev.argtypes = [C.POINTER(ebcc_field_desc), C.c_int, C.POINTER(ebcc_out_desc),
                                               C.POINTER(ebcc_params), C.c_void_p]
         L.ebcc_decompress_batch_dev.argtypes = [C.POINTER(ebcc_stream_desc), C.c_int, C.POINTER(C.c_void_p),
@@ -228,6 +230,17 @@ def ebcc_decompress(stream: bytes, ny: int, nx: int) -> np.ndarray:
     out = np.empty((ny, nx), np.float32)
     _check(lib().ebcc_decompress(buf.ctypes.data, len(stream), out.ctypes.data, ny, nx), "ebcc_decompress")
     return out
+
+
+def ebcc_j2k_codestream(stream: bytes) -> bytes:
+    """The base layer of an EBCC stream as a JPEG 2000 codestream (host only)."""
+    buf = np.frombuffer(stream, np.uint8)
+    out = C.c_void_p()
+    n = C.c_size_t()
+    _check(lib().ebcc_j2k_codestream(buf.ctypes.data, len(stream), C.byref(out), C.byref(n)), "ebcc_j2k_codestream")
+    data = C.string_at(out, n.value)
+    lib().ebcc_free(out)
+    return data
 
 
 def ebcc_stream_info(stream: bytes):

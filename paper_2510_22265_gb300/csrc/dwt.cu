@@ -206,9 +206,13 @@ constexpr int IT = 96;  // threads of an inverse-level CTA (72 stage the tile's 
 // template parameter so each instantiation carries only its own finish
 // per_pt > 0 (profiling): each tile processed adds its algorithmic bytes,
 // per_pt per point of the tile, to its field's sc->prof_bytes
-template <int MODE>
+// TB (counting at level 1, every field with tensor maps): the tile's bound
+// intervals come as one tensor-memory-access box into shared memory, issued at
+// the start and waited for (bounded) only by the counting threads; err is
+// set if that wait runs out
+template <int MODE, bool TB>
 __global__ void __launch_bounds__(IT, 12) inv_level(Live lv, const __grid_constant__ FieldRun one, int l, int src_plane,
-                                                InvFinal fin, float per_pt) {
+                                                InvFinal fin, float per_pt, int *err) {
     int f;
     const FieldRun *r = pick(lv, one, blockIdx.x, f);
     if (!r || l > r->L) return;
@@ -243,6 +247,16 @@ __global__ void __launch_bounds__(IT, 12) inv_level(Live lv, const __grid_consta
     if (!level_extents_ok(*r, l, hp, wp)) return;
     const int hl = (hp + 1) >> 1, wl = (wp + 1) >> 1;
     __shared__ float t[EY][EX + 1];
+    extern __shared__ __align__(16) uint8_t dyn_bnd[];
+    __shared__ __align__(8) uint64_t bnd_bar;
+    float *bnd_s = (float *)(((uintptr_t)dyn_bnd + 127) & ~(uintptr_t)127);  // TY rows of 2 TX floats
+    if (TB && tid == 0) {
+        mbar_init(&bnd_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_tx(&bnd_bar, TY * 2 * TX * 4);
+        tma_load_2d(bnd_s, (const CUtensorMap *)r->tm + TM_BND, 2 * tx0, ty0, &bnd_bar);
+    }
     // interior tile: the halo needs no reflection, every index is in range
     const bool interior = ty0 >= HALO && tx0 >= HALO && ty0 + TY + HALO <= hp && tx0 + TX + HALO <= wp;
     if (interior && tid < EX) {
@@ -320,6 +334,17 @@ __global__ void __launch_bounds__(IT, 12) inv_level(Live lv, const __grid_consta
                 for (int rr = 0; rr < TY; rr++) {
                     const int i = (ty0 + rr) * ds + gx;
                     if (rr < nr) dst[i] = w[HALO + rr];
+                }
+            } else if (TB) {  // base-loop count from the staged intervals
+                if (mbar_wait(&bnd_bar, 0)) {
+#pragma unroll
+                    for (int rr = 0; rr < TY; rr++) {
+                        const float2 bb = *reinterpret_cast<const float2 *>(bnd_s + rr * (2 * TX) + 2 * tid);
+                        const float v = w[HALO + rr];
+                        if (rr < nr) cnt += (v >= bb.x && v <= bb.y);
+                    }
+                } else {
+                    atomicExch(err, 1);
                 }
             } else if (mode == 1 && nr == TY) {  // base-loop count, full tile column
                 const float2 *__restrict__ bnd = r->bounds + (size_t)ty0 * nx + gx;
@@ -450,7 +475,8 @@ int dwt_inverse_b(const Live &lv, const FieldRun &one, int nslots, const BatchDi
         PROF("inv_identity", st, 0.0, inv_identity<<<dim3(pgrid(d.maxN, nslots), nslots), NT, 0, st>>>(lv, one, src, fin));
         CK(cudaGetLastError());
     }
-    if (d.tma && lv.tab && d.tma_err) return dwt_inverse_tma(lv, nslots, d, src, fin, d.tma_err, st);
+    if (d.tma == 2 && lv.tab && d.tma_err) return dwt_inverse_tma(lv, nslots, d, src, fin, d.tma_err, st);
+    const bool tb = d.tma >= 1 && lv.tab && d.tma_err;  // level-1 counts stage their intervals by TMA
     for (int l = d.maxL; l >= 1; l--) {
         const int hp = d.h[l - 1], wp = d.w[l - 1];
         // field slot fastest: the tiles of a field are spread over the launch,
@@ -472,12 +498,24 @@ int dwt_inverse_b(const Live &lv, const FieldRun &one, int nslots, const BatchDi
         const bool dev = prof_enabled() && lv.tab != nullptr;
         const double hb = dev ? 0.0 : per * hp * wp * nslots;
         const float pp = dev ? (float)per : 0.0f;
+        constexpr int TBS = TY * 2 * TX * 4 + 128;  // the staged intervals, 128-byte aligned
         switch (mode) {
-        case -1: PROF("inv_level", st, hb, inv_level<-1><<<grid, IT, 0, st>>>(lv, one, l, src, fin, pp)); break;
-        case 0: PROF("inv_level", st, hb, inv_level<0><<<grid, IT, 0, st>>>(lv, one, l, src, fin, pp)); break;
-        case 1: PROF("inv_level", st, hb, inv_level<1><<<grid, IT, 0, st>>>(lv, one, l, src, fin, pp)); break;
-        case 2: PROF("inv_level", st, hb, inv_level<2><<<grid, IT, 0, st>>>(lv, one, l, src, fin, pp)); break;
-        default: PROF("inv_level", st, hb, inv_level<3><<<grid, IT, 0, st>>>(lv, one, l, src, fin, pp)); break;
+        case -1: PROF("inv_level", st, hb, inv_level<-1, false><<<grid, IT, 0, st>>>(lv, one, l, src, fin, pp, d.tma_err)); break;
+        case 0: PROF("inv_level", st, hb, inv_level<0, false><<<grid, IT, 0, st>>>(lv, one, l, src, fin, pp, d.tma_err)); break;
+        case 1:
+            if (tb) {
+                static bool attr = false;
+                if (!attr) {
+                    CK(cudaFuncSetAttribute(inv_level<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TBS));
+                    attr = true;
+                }
+                PROF("inv_level", st, hb, inv_level<1, true><<<grid, IT, TBS, st>>>(lv, one, l, src, fin, pp, d.tma_err));
+            } else {
+                PROF("inv_level", st, hb, inv_level<1, false><<<grid, IT, 0, st>>>(lv, one, l, src, fin, pp, d.tma_err));
+            }
+            break;
+        case 2: PROF("inv_level", st, hb, inv_level<2, false><<<grid, IT, 0, st>>>(lv, one, l, src, fin, pp, d.tma_err)); break;
+        default: PROF("inv_level", st, hb, inv_level<3, false><<<grid, IT, 0, st>>>(lv, one, l, src, fin, pp, d.tma_err)); break;
         }
         CK(cudaGetLastError());
     }

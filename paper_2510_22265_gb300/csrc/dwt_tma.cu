@@ -45,7 +45,6 @@ constexpr int BH = 20, BW = 40;        // band box: rows, columns (x start round
 constexpr int BAND_BYTES = BH * BW * 4;
 constexpr int BND_W = 2 * TX;          // bound intervals: 2 floats per point
 constexpr int NCW = 4;                 // consumer warps
-constexpr unsigned long long WAIT_NS = 4000000000ull;  // 4 s
 
 __device__ __forceinline__ int reflect(int i, int n) {
     if ((unsigned)i < (unsigned)n) return i;
@@ -58,63 +57,11 @@ __device__ __forceinline__ int reflect(int i, int n) {
 
 __device__ __forceinline__ int ceil_sh(int n, int l) { return (int)(((long long)n + (1LL << l) - 1) >> l); }
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, unsigned parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long gtimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// wait for the phase of `parity` to complete, at most WAIT_NS; false when the
-// wait ran out
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
-    if (mbar_try(bar, parity)) return true;
-    const unsigned long long t0 = gtimer();
-    for (unsigned it = 0;; it++) {
-        if (mbar_try(bar, parity)) return true;
-        if ((it & 255) == 255 && gtimer() - t0 > WAIT_NS) return false;
-    }
-}
-
-// 2-D tiled copy global -> shared, completing on `bar`
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            smem_u32(dst)),
-        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-
 }  // namespace
 
 namespace {
 
 // slots of a field's tensor-map table
-enum { TM_W = 0, TM_R = 1, TM_BND = 2, TM_AB = 3, TM_S0 = 4, TM_PER_FIELD = 16 };
 
 template <int MODE>
 struct StageSize {
@@ -173,6 +120,14 @@ __global__ void __launch_bounds__(NCW * 32, 7) inv_tma(Live lv, int l, int src_p
         boff[b] = x - (x & ~3);  // the box starts at x rounded down to a 16-byte boundary
     }
     if (tid == 0) {
+        // fetch the tile's tensor maps while the count check below waits
+        const CUtensorMap *tm0 = (const CUtensorMap *)r.tm;
+        asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)(tm0 + (src_plane == PL_R ? TM_R : TM_W)))
+                     : "memory");
+        if (l < r.L)
+            asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)(tm0 + TM_S0 + (l - 1))) : "memory");
+        if (MODE == 1 || MODE == 2)
+            asm volatile("prefetch.tensormap [%0];" ::"l"((unsigned long long)(tm0 + TM_BND)) : "memory");
         int q = 0;
         if (MODE == 1) {  // the count is decided once enough points fail
             const unsigned long long thr = r.sc->fail_thr;

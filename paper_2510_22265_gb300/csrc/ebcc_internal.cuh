@@ -7,6 +7,9 @@
 #include <stdint.h>
 #include <vector>
 #include "../../include/ebcc.h"
+#ifdef __CUDACC__
+#include <cuda.h>
+#endif
 
 #define EBCC_MAX_LEVELS 12
 #define EBCC_MAX_BANDS (3 * EBCC_MAX_LEVELS + 1)
@@ -266,7 +269,8 @@ struct BatchDims {
     int maxnblk;
     int h[EBCC_MAX_LEVELS + 1], w[EBCC_MAX_LEVELS + 1];
     bool any_L0;
-    bool tma;       // every field of the batch has tensor maps: the inverse levels use the staged kernel
+    int tma;        // 0: no tensor maps; 1: every field has them (level-1 counts stage their
+                    // intervals by TMA); 2: the inverse levels use the fully staged kernel
     int *tma_err;   // device word the staged kernel sets when a wait runs out
 };
 void batch_dims_add(BatchDims &d, int ny, int nx, int L, int nblk);
@@ -490,6 +494,61 @@ __device__ __forceinline__ bool inb_rec(long long i, long long n, int *word, int
     return false;
 }
 #define INBS(i, n, word) inb_rec((long long)(i), (long long)(n), (word), 1)
+// ---- tensor-memory-access copies and mbarriers (inline PTX)
+// slots of a field's tensor-map table (FieldRun::tm)
+enum { TM_W = 0, TM_R = 1, TM_BND = 2, TM_AB = 3, TM_S0 = 4, TM_PER_FIELD = 16 };
+constexpr unsigned long long TMA_WAIT_NS = 4000000000ull;  // 4 s
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// wait for the phase of `parity` to complete, at most TMA_WAIT_NS; false when
+// the wait ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    for (unsigned it = 0;; it++) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255) == 255 && gtimer() - t0 > TMA_WAIT_NS) return false;
+    }
+}
+
+// 2-D tiled copy global -> shared, completing on `bar`
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // the quiet form that notes a miss in a per-thread flag (an OR, no branch,
 // so loads around it still batch); the kernel reports a noted miss once, at
 // its end, with guard_flush

@@ -801,22 +801,25 @@ const FieldRun kNone{};  // placeholder `one` argument of batched launches
 // tensor maps of the staged inverse DWT for the fields in L (pointers of the
 // table already laid out); the batch uses that path when every one has them
 int stage_maps(Engine &e, Batch &b, const std::vector<int> &L, cudaStream_t st) {
-    b.dims.tma = false;
+    b.dims.tma = 0;
     b.dims.tma_err = b.tma_err;
-    static const bool off = [] {
-        // the staged kernel is opt-in ("1") while it is slower than the
-        // register-staged one on the benchmarked batches
+    // EBCC_INV_TMA: unset or "0" the register-staged inverse kernels with
+    // plain loads (the fastest on the benchmarked batches); "1" the fully
+    // TMA-staged inverse kernel; "2" the register-staged kernel with the
+    // level-1 bound intervals staged by TMA.  Both TMA forms measured slower
+    // on batches of 721 x 1440 fields.
+    static const int want = [] {
         const char *v = getenv("EBCC_INV_TMA");
-        return !(v && v[0] == '1');
+        return v && v[0] == '1' ? 2 : (v && v[0] == '2' ? 1 : 0);
     }();
-    if (L.empty() || !b.tmaps || off) return EBCC_OK;
+    if (L.empty() || !b.tmaps || !want) return EBCC_OK;
     const size_t bytes = tma_table_bytes(b.F);
     uint8_t *ht = stage_take<uint8_t>(e, bytes + 128);
     if (!ht) return EBCC_OK;  // no staging room: the plain inverse kernels run
     ht = (uint8_t *)(((uintptr_t)ht + 127) & ~(uintptr_t)127);
     if (tma_build_maps(b.run, L, ht, b.tmaps)) {
         CK(cudaMemcpyAsync(b.tmaps, ht, bytes, cudaMemcpyHostToDevice, st));
-        b.dims.tma = true;
+        b.dims.tma = want;
     }
     CK(cudaMemsetAsync(b.tma_err, 0, sizeof(int), st));
     return EBCC_OK;
