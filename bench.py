@@ -53,8 +53,9 @@ from paper_2510_22265_gb300 import synth  # noqa: E402
 METRIC = "compress/decompress GB/s at 1% rel bound (batched vs plain); CR; p99 latency"
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) measured by ncu for the
 # dominant kernel as it stands, averaged over the launches of one compression step of the default
-# workload (profiles/); None until the current kernel has been captured
-NCU_TRAFFIC = {}
+# workload (profiles/launches_compress_era5_148x721x1440.md); None until the current kernel has
+# been captured
+NCU_TRAFFIC = {"inv_level": 247.6e6}
 DEFAULT_SHAPE = [4, 37, 721, 1440]
 BOUND = 1e-2
 FALLBACK_HBM_GBS = 6800.0

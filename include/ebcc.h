@@ -152,9 +152,10 @@ size_t ebcc_max_stream_bytes(size_t ny, size_t nx);
  * rate-distortion points the base layer can choose.  ebcc_autotune_cblk
  * compresses the n probe fields (device, all of one shape) with each of
  * 32x32, 64x64, 32x64 and 64x32 (after an untimed warm-up call each), timing
- * them with CUDA events on `stream`, and picks the fastest shape whose total
- * stream length is within 1% of the shortest; the choice is cached for that
- * (ny, nx) for the life of the process.  ms[4] and bytes[4] (either may be
+ * them with CUDA events on `stream`, and picks, among the shapes at most 1.25
+ * times slower than the fastest, the one with the shortest total stream
+ * length (ties: the faster); the choice is cached for that (ny, nx) for the
+ * life of the process.  ms[4] and bytes[4] (either may be
  * NULL) receive each candidate's time and total length (-1: the candidate
  * failed on these fields).  Synchronous.  Errors: EINVAL (no probe, mixed
  * shapes, bad params), ENOMEM, ECUDA.

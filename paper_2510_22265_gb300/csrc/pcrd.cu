@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(ST) seg_build_kernel(Live lv, const __grid_con
         if (b < nblk) {
             const size_t base = (size_t)(blk0 + b) * h.maxpt;
             for (int k = 1; k <= cnt; k++) {
-                if (!INBQ(off + k - 1, (long long)nblk * (h.maxpt - 1))) break;
+                if (!INBS(off + k - 1, (long long)nblk * (h.maxpt - 1), guard_word(*r))) break;
                 skey[off + k - 1] = h.key[base + k];
                 sdr[off + k - 1] = (uint32_t)(h.rate[base + k] - h.rate[base + k - 1]);
             }
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(ST) seg_sort_kernel(Live lv, const __grid_cons
             __syncthreads();
             if (valid) {
                 const unsigned int pos = base[d] + wcnt[wid][d] + rank;
-                if (INBQ(pos, m)) { kd[pos] = key; vd[pos] = val; }
+                if (INBS(pos, m, guard_word(*r))) { kd[pos] = key; vd[pos] = val; }
             }
             __syncthreads();
             if (tid < 256) base[tid] += tilecnt[tid];

@@ -33,8 +33,9 @@ def test_tune_picks_a_candidate_and_caches(B):
     assert (w, h) in [(32, 32), (64, 64), (32, 64), (64, 32)]
     assert all(m > 0 for m in ms) and all(b > 0 for b in by)
     k = [(32, 32), (64, 64), (32, 64), (64, 32)].index((w, h))
-    assert by[k] <= 1.01 * min(by)
-    assert all(ms[k] <= ms[j] for j in range(4) if by[j] <= 1.01 * min(by))
+    near = [j for j in range(4) if ms[j] <= 1.25 * min(ms)]  # at most 25% slower than the fastest
+    assert k in near
+    assert by[k] == min(by[j] for j in near)
     assert B.ebcc_autotune_lookup(181, 360) == (w, h)
 
 
