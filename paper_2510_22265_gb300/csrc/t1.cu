@@ -744,34 +744,15 @@ __global__ void __launch_bounds__(PW * 32, 8) t1_model_warp(int32_t *qt, const B
 // copy (the stream length the rate search needs, with its tail bytes).
 constexpr int MQT = 128;
 
-// one MQ symbol: the common MPS case without renormalisation returns early;
-// otherwise the interval update is a select (T.800 C.2: the conditional
-// exchange swaps which sub-interval is coded, the state transition depends
-// only on MPS / LPS) and one renormalisation
+// One MQ symbol: the common MPS case without renormalisation only moves A
+// and C; otherwise the interval update is a select (T.800 C.2: the
+// conditional exchange swaps which sub-interval is coded, the state
+// transition depends only on MPS / LPS) and one renormalisation.
 // One context's whole state in one word: Qe | NMPS << 16 | NLPS << 22 |
 // SWITCH << 28 of its current index, MPS in bit 31, so a symbol reads one
 // word; the fast MPS path (no renormalisation) leaves it unchanged
 __device__ __forceinline__ uint32_t mq_word(uint32_t tab) {
     return (tab & 0xFFFFu) | (((tab >> 16) & 63u) << 16) | ((tab >> 24) << 22);
-}
-
-__device__ __forceinline__ void mq_encode_w(MQEnc &e, uint32_t *ctx, const uint32_t *stab, int cx, int d) {
-    const uint32_t ent = ctx[cx];
-    const uint32_t qe = ent & 0xFFFFu;
-    const uint32_t A = e.A - qe;
-    const uint32_t mpsb = ent >> 31;
-    const bool mps = (uint32_t)d == mpsb;
-    if (mps && (A & 0x8000)) {
-        e.A = A;
-        e.C += qe;
-        return;
-    }
-    const bool small = A < qe;
-    if (mps != small) { e.A = A; e.C += qe; } else { e.A = qe; }
-    const uint32_t ni = mps ? (ent >> 16) & 63u : (ent >> 22) & 63u;
-    const uint32_t nm = mpsb ^ (uint32_t)(!mps && ((ent >> 28) & 1u));
-    ctx[cx] = stab[ni] | (nm << 31);
-    e.renorm();
 }
 
 // ---- order of the blocks for the MQ coders: counting sort by symbol count
@@ -841,7 +822,10 @@ __global__ void __launch_bounds__(MQT) t1_mq_kernel(int nblk, T1Out o) {
     // one loop over all the block's symbols; a pass end is recorded when the
     // symbol count reaches it, so lanes are not held together pass by pass.
     // Symbols are read 16 at a time, the next 16 already in flight (the
-    // buffer of a block starts on a 16-byte boundary, sym_cap % 16 == 0)
+    // buffer of a block starts on a 16-byte boundary, sym_cap % 16 == 0).
+    // The context word of symbol k + 1 is loaded before symbol k is coded
+    // (and replaced by symbol k's new state when both use one context), so
+    // the shared-memory load is off the coder's dependency chain.
     const uint4 *sym4 = (const uint4 *)(o.sym + (size_t)b * o.sym_cap);
     const size_t pb = (size_t)b * o.maxpass;
     const int npp = np < o.maxpass ? np : o.maxpass;
@@ -849,6 +833,8 @@ __global__ void __launch_bounds__(MQT) t1_mq_kernel(int nblk, T1Out o) {
     if (total > o.sym_cap) total = (int)o.sym_cap;
     uint4 cur = total > 0 ? sym4[0] : make_uint4(0, 0, 0, 0);
     uint4 nxt = total > 16 ? sym4[1] : make_uint4(0, 0, 0, 0);
+    uint32_t sy = cur.x & 0xFFu;
+    uint32_t ent = ctx[min(sy >> 1, 18u)];
     int pass = 0;
     int end = o.pass_sym[pb];
     for (int k = 0;; k++) {
@@ -862,14 +848,36 @@ __global__ void __launch_bounds__(MQT) t1_mq_kernel(int nblk, T1Out o) {
             if (pass < npp) end = o.pass_sym[pb + pass];
         }
         if (k >= total) break;
-        if ((k & 15) == 0 && k > 0) {
+        const int k1 = k + 1;
+        if ((k1 & 15) == 0) {
             cur = nxt;
-            if (k + 16 < total) nxt = sym4[(k >> 4) + 1];
+            if (k1 + 16 < total) nxt = sym4[(k1 >> 4) + 1];
         }
-        const int q = (k >> 2) & 3;
+        const int q = (k1 >> 2) & 3;
         const uint32_t wd = q == 0 ? cur.x : (q == 1 ? cur.y : (q == 2 ? cur.z : cur.w));
-        const int sy = (int)((wd >> ((k & 3) * 8)) & 0xFFu);
-        mq_encode_w(e, ctx, stab, sy >> 1, sy & 1);
+        const uint32_t sn = (wd >> ((k1 & 3) * 8)) & 0xFFu;  // zero padding past the last symbol
+        const uint32_t ent_n = ctx[min(sn >> 1, 18u)];
+        // code symbol k (T.800 C.2) on its context word
+        const int cx = (int)(sy >> 1), d = (int)(sy & 1u);
+        const uint32_t qe = ent & 0xFFFFu;
+        const uint32_t A = e.A - qe;
+        const uint32_t mpsb = ent >> 31;
+        const bool mps = (uint32_t)d == mpsb;
+        if (mps && (A & 0x8000)) {
+            e.A = A;
+            e.C += qe;
+            ent = ent_n;
+        } else {
+            const bool small = A < qe;
+            if (mps != small) { e.A = A; e.C += qe; } else { e.A = qe; }
+            const uint32_t ni = mps ? (ent >> 16) & 63u : (ent >> 22) & 63u;
+            const uint32_t nm = mpsb ^ (uint32_t)(!mps && ((ent >> 28) & 1u));
+            const uint32_t ne = stab[ni] | (nm << 31);
+            ctx[cx] = ne;
+            ent = (int)(sn >> 1) == cx ? ne : ent_n;
+            e.renorm();
+        }
+        sy = sn;
     }
     if (e.overflow) atomicOr(o.status, 1);
 }
