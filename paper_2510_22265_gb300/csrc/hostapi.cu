@@ -3,9 +3,13 @@
 // The library copies them through device buffers it keeps between calls
 // (grown on demand, never freed per call), so a call allocates nothing once
 // those have reached the size of the largest batch seen.  Host buffers that
-// are page-locked (cudaHostAlloc, cudaHostRegister, torch pin_memory) are
-// copied by DMA directly; pageable buffers go through two pinned chunks, the
-// CPU filling one while the DMA engine drains the other.  The computation is
+// are page-locked (cudaHostAlloc, cudaHostRegister, torch pin_memory) and
+// mapped into the device's address space are copied by one kernel per
+// direction for the whole batch (the SMs read or write the host memory over
+// the CPU-GPU link, every field's copy in flight at once); page-locked
+// buffers without a device mapping by DMA directly; pageable buffers go
+// through two pinned chunks, the CPU filling one while the DMA engine drains
+// the other.  The computation is
 // the device batch engine (Algorithm 1 on every field of the batch at once).
 #include <string.h>
 #include <algorithm>
@@ -41,6 +45,69 @@ bool host_pinned(const void *p) {
         return false;
     }
     return a.type == cudaMemoryTypeHost;
+}
+
+// the address under which the device reaches a page-locked host buffer
+// (null for pageable memory, or where the device cannot map it)
+void *host_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// Copies between page-locked host buffers and device buffers done by one
+// kernel for a whole batch: the SMs read (or write) the host memory through
+// its device mapping, every copy of the batch in flight at once, instead of
+// one copy-engine transfer per field.
+struct CopyJob {
+    const uint8_t *src;
+    uint8_t *dst;
+    unsigned long long n;
+};
+
+// grid.y = job; grid.x strides over the job in 16-byte pieces when both ends
+// are 16-byte aligned (bytes past the last whole piece, or every byte of an
+// unaligned job, one at a time)
+__global__ void __launch_bounds__(256) copy_jobs(const CopyJob *__restrict__ jobs, int njobs) {
+    const int j = blockIdx.y;
+    if (j >= njobs) return;
+    const CopyJob c = jobs[j];
+    const bool vec = (((uintptr_t)c.src | (uintptr_t)c.dst) & 15) == 0;
+    const unsigned long long nv = vec ? c.n / 16 : 0;
+    const unsigned long long t0 = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x;
+    const uint4 *s4 = (const uint4 *)c.src;
+    uint4 *d4 = (uint4 *)c.dst;
+    for (unsigned long long i = t0; i < nv; i += step) d4[i] = s4[i];
+    for (unsigned long long i = nv * 16 + t0; i < c.n; i += step) c.dst[i] = c.src[i];
+}
+
+struct JobTable {
+    Arena dev;
+    std::vector<CopyJob> host;
+};
+JobTable g_jobs;
+
+// run the queued jobs on st (one small upload of the table, one launch)
+int run_jobs(cudaStream_t st) {
+    const int n = (int)g_jobs.host.size();
+    if (!n) return EBCC_OK;
+    if (n > 65535) return EBCC_EINVAL;
+    unsigned long long most = 0;
+    for (const CopyJob &c : g_jobs.host) most = std::max(most, c.n);
+    RC(arena_reserve(g_jobs.dev, sizeof(CopyJob) * (size_t)n + 256));
+    CK(cudaMemcpyAsync(g_jobs.dev.base, g_jobs.host.data(), sizeof(CopyJob) * (size_t)n, cudaMemcpyHostToDevice, st));
+    // enough CTAs per job that the whole batch fills the GPU a few times over
+    unsigned long long gx = (most / 16 + 255) / 256;
+    const unsigned long long want = std::max(1ull, 152ull * 8 / (unsigned long long)n);
+    gx = std::min(std::max(gx, 1ull), std::max(want, 1ull) * 4);
+    copy_jobs<<<dim3((unsigned)std::min(gx, 65535ull), (unsigned)n), 256, 0, st>>>((const CopyJob *)g_jobs.dev.base, n);
+    CK(cudaGetLastError());
+    g_jobs.host.clear();
+    return EBCC_OK;
 }
 
 // host -> device, queued on st
@@ -119,18 +186,28 @@ int compress_host_locked(const ebcc_field_desc *fields, int n, ebcc_out_desc *ou
             continue;
         }
         float *d = (float *)(g_io.in.base + in_off[i]);
-        RC(h2d(d, fields[i].field, fields[i].ny * fields[i].nx * sizeof(float), st));
+        const size_t bytes = fields[i].ny * fields[i].nx * sizeof(float);
+        if (const void *m = host_device_ptr(fields[i].field))
+            g_jobs.host.push_back({(const uint8_t *)m, (uint8_t *)d, (unsigned long long)bytes});
+        else
+            RC(h2d(d, fields[i].field, bytes, st));
         dfd[i].field = d;
         dod[i].stream = g_io.out.base + out_off[i];
         dod[i].capacity = cap[i];
     }
+    RC(run_jobs(st));
     const int rc = engine_compress(ebcc_api_engine(), dfd.data(), n, dod.data(), p, st);
     for (int i = 0; i < n; i++) {
         outs[i].status = dod[i].status;
         outs[i].stats = dod[i].stats;
         outs[i].len = dod[i].status ? 0 : dod[i].len;
-        if (!dod[i].status) RC(d2h(outs[i].stream, dod[i].stream, dod[i].len, st));
+        if (dod[i].status) continue;
+        if (void *m = host_device_ptr(outs[i].stream))
+            g_jobs.host.push_back({dod[i].stream, (uint8_t *)m, (unsigned long long)dod[i].len});
+        else
+            RC(d2h(outs[i].stream, dod[i].stream, dod[i].len, st));
     }
+    RC(run_jobs(st));
     CK(cudaStreamSynchronize(st));
     return rc;
 }
@@ -159,16 +236,26 @@ int decompress_host_locked(const ebcc_stream_desc *streams, int n, float **outs,
     for (int i = 0; i < n; i++) {
         if (!ok[i]) { dsd[i].stream = nullptr; continue; }
         uint8_t *d = g_io.in.base + in_off[i];
-        RC(h2d(d, streams[i].stream, streams[i].len, st));
+        if (const void *m = host_device_ptr(streams[i].stream))
+            g_jobs.host.push_back({(const uint8_t *)m, d, (unsigned long long)streams[i].len});
+        else
+            RC(h2d(d, streams[i].stream, streams[i].len, st));
         dsd[i].stream = d;
         dout[i] = (float *)(g_io.out.base + out_off[i]);
     }
+    RC(run_jobs(st));
     const int rc = engine_decompress(ebcc_api_engine(), dsd.data(), n, dout.data(), dst.data(), st);
     for (int i = 0; i < n; i++) {
         if (!ok[i]) continue;
         status[i] = dst[i];
-        if (!dst[i]) RC(d2h(outs[i], dout[i], streams[i].ny * streams[i].nx * sizeof(float), st));
+        if (dst[i]) continue;
+        const size_t bytes = streams[i].ny * streams[i].nx * sizeof(float);
+        if (void *m = host_device_ptr(outs[i]))
+            g_jobs.host.push_back({(const uint8_t *)dout[i], (uint8_t *)m, (unsigned long long)bytes});
+        else
+            RC(d2h(outs[i], dout[i], bytes, st));
     }
+    RC(run_jobs(st));
     CK(cudaStreamSynchronize(st));
     return rc;
 }
