@@ -181,8 +181,11 @@ int ebcc_compress_batch_tuned_dev(const ebcc_field_desc *fields, int n, ebcc_out
  * buffers it keeps between calls (grown to the largest batch seen, so a call
  * allocates nothing once they have that size), runs the device batch, and
  * copies every stream back.  Page-locked host buffers (cudaHostAlloc,
- * cudaHostRegister) are copied by DMA directly; pageable ones go through the
- * library's pinned staging.  `stream` is a cudaStream_t as void* (NULL = the
+ * cudaHostRegister) that the device maps are copied by one kernel per
+ * direction for the whole batch, reading or writing the host memory through
+ * its device mapping; other page-locked buffers by DMA; pageable ones through
+ * the library's pinned staging.  A caller's host buffers must not be written
+ * (inputs) or read (outputs) by the host during the call.  `stream` is a cudaStream_t as void* (NULL = the
  * legacy default stream); the call is synchronous.  Return value as
  * ebcc_compress_batch_dev.  Errors: EINVAL, ENONFINITE, ENOMEM, ECAPACITY,
  * ECUDA (per field in outs[i].status). */
