@@ -260,7 +260,9 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
     long long *refine_start = r->sc->refine_start;
     int *status = &r->sc->spiht_status;
     const long long N = r->N;
-    uint2 *lip = r->sw.elip, *lsp = r->sw.elsp, *lis = r->sw.elis, *lis_new = r->sw.elis + N;
+    // the LSP keeps only |s| (the refinement pass reads nothing else)
+    uint2 *lip = r->sw.elip, *lis = r->sw.elis, *lis_new = r->sw.elis + N;
+    uint32_t *lsp = (uint32_t *)r->sw.elsp;
     uint2 *wave_a = r->sw.ewav, *wave_b = r->sw.ewav + N;
     const int tid = threadIdx.x;
     const long long NN = (long long)g.ny * g.nx;
@@ -345,7 +347,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                         if (INBN(ls, NN, miss)) {
                             sig_pos[x.x] = (uint32_t)(bp + 1);
                             lsp_idx[x.x] = (uint32_t)ls;
-                            lsp[ls] = make_uint2(x.x, x.y & 0x7FFFFFFFu);
+                            lsp[ls] = x.y & 0x7FFFFFFFu;
                         }
                         ls++;
                         bp += 2;
@@ -437,7 +439,7 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
                                     if (sv[q] < 0) win_set(sh, bp + 1, miss);
                                     sig_pos[c[q]] = (uint32_t)(bp + 1);
                                     lsp_idx[c[q]] = (uint32_t)ls;
-                                    if (INBN(ls, NN, miss)) lsp[ls] = make_uint2(c[q], absi(sv[q]));
+                                    if (INBN(ls, NN, miss)) lsp[ls] = absi(sv[q]);
                                     ls++;
                                     bp += 2;
                                 } else {
@@ -477,18 +479,36 @@ __global__ void __launch_bounds__(ET) encode_kernel(Live lv, const __grid_consta
             if (tid == 0) sh.nlis = sh.nstay;
             __syncthreads();
         }
-        // ---- refinement pass over the LSP entries of earlier planes
+        // ---- refinement pass over the LSP entries of earlier planes: entry k
+        // gives stream bit pos + k.  A warp reads 32 consecutive entries
+        // (coalesced) and its lane 0 ORs their bits, gathered by a ballot, into
+        // the window as one 32-bit run (two words when the run is unaligned).
         {
             if (tid == 0) refine_start[n] = (long long)sh.pos;
+            const int lane = tid & 31, wid = tid >> 5;
             for (long long base = 0; base < lsp_before; base += (long long)ET * EPL) {
                 if (tid == 0) sh.wbase = (sh.pos + base) >> 5;
                 win_clear(sh);
                 __syncthreads();
-                const long long k0 = base + (long long)tid * EPL;
 #pragma unroll
                 for (int j = 0; j < EPL; j++) {
-                    const long long k = k0 + j;
-                    if (k < lsp_before && INBN(k, NN, miss) && ((lsp[k].y >> n) & 1)) win_set(sh, sh.pos + k, miss);
+                    const long long k0 = base + (long long)j * ET + (long long)wid * 32;
+                    const long long k = k0 + lane;
+                    const bool bit = k < lsp_before && INBN(k, NN, miss) && ((lsp[k] >> n) & 1u);
+                    const uint32_t word = __ballot_sync(0xffffffffu, bit);
+                    if (lane == 0 && word) {
+                        // the run in stream order (its first bit in bit 31), then
+                        // split over the two window words it touches; a stored
+                        // word holds its stream bits byte by byte, each byte
+                        // most significant bit first (bitmask), i.e. byte-swapped
+                        const uint32_t x = __brev(word);
+                        const unsigned long long b0 = sh.pos + (unsigned long long)k0;
+                        const long long wi = (long long)(b0 >> 5) - (long long)sh.wbase;
+                        const unsigned sft = (unsigned)(b0 & 31);
+                        if (INBN(wi, WIN_WORDS, miss)) atomicOr(&sh.win[wi], __byte_perm(x >> sft, 0, 0x0123));
+                        if (sft && INBN(wi + 1, WIN_WORDS, miss))
+                            atomicOr(&sh.win[wi + 1], __byte_perm(x << (32 - sft), 0, 0x0123));
+                    }
                 }
                 __syncthreads();
                 const long long end = base + (long long)ET * EPL < lsp_before ? base + (long long)ET * EPL : lsp_before;
