@@ -593,7 +593,10 @@ def run_gpu(args):
                         "copies inside the call; host wall clock, median of the steps"},
         "bounds": other_bounds, "single_field": one, "uneven_batch": uneven, "high_res": hires,
         "ablation": ablation,
-        "gpu_launches": int(round(sum(p["launches"] for p in prof))) if prof else None,
+        # the library's launches inside the timed region: every timed step runs
+        # the same launches as a profiled step
+        "gpu_launches": int(round(sum(p["launches"] for p in prof))) * args.steps if prof else None,
+        "gpu_launches_per_step": int(round(sum(p["launches"] for p in prof))) if prof else None,
         "roofline": roof, "serving": serving, "kernels": prof,
         "kernels_unit": "per step (profiled pass after the timed region)",
         "kernels_decompress": prof_dec,
