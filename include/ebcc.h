@@ -360,7 +360,8 @@ int ebcc_dwt_fwd_dev(const float *in, float *out, size_t ny, size_t nx, int leve
  * EBCC_ECAPACITY, touching nothing, beyond that.  Nothing in the scratch has
  * to start at zero.  The first call on a device looks up the array's address
  * (cudaGetSymbolAddress, with that device current) and may load the module,
- * so make it before any latency-critical region; the address is kept for the
+ * so make it before any latency-critical region and before any stream
+ * capture; the address is kept for the
  * life of the process, so the call must not be used after a cudaDeviceReset
  * of that device.  All calls on one device share the scratch: calls that
  * can overlap in time (different streams, or threads without ordering) race
