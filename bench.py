@@ -483,7 +483,7 @@ def run_gpu(args):
         e2e_out = sum(r[1] for r in res_e)
     t_e2e = float(np.median(e2e_times))  # host wall clock: the median step, every step listed
     pool = mp.get_context("spawn").Pool(cores)
-    # the stack at the other two bounds of the survey's grid (0.1% and 10%)
+    # the stack at the other two bounds of the benchmark grid (0.1% and 10%)
     other_bounds = {}
     for bb in (1e-3, 1e-1):
         tb, rb = timed_batch(B, torch, dfields, [bb] * n, outs, max(1, min(args.steps, 3)), stream)
