@@ -276,10 +276,11 @@ int ebcc_decompress_chunks_dev(const ebcc_stream_desc *streams, const size_t sha
 
 /* ---------------------------------------------------------------- serving */
 /* A request loop with continuous batching: requests that arrive while others
- * are on the GPU are admitted as slots and memory free up (HBM budget); two
- * workers, each with its own stream and device buffers (kept between groups,
- * no allocation per request), run admitted groups as batches, so groups
- * overlap on the device.  A group's requests enter the device through a
+ * are on the GPU are admitted as slots and memory free up (HBM budget); four
+ * workers (EBCC_SERVER_WORKERS, 1..8), each with its own stream and device
+ * buffers (kept between groups, no allocation per request), run admitted
+ * groups as batches -- a group's decompressions first, their results
+ * published before its compressions run -- so groups overlap on the device.  A group's requests enter the device through a
  * request ring in page-locked host memory, read by an intake kernel that
  * waits on the ring's doorbell for at most 2 s (EBCC_ETIMEOUT for the group's
  * requests if it runs out).  Thread-safe per handle. */
