@@ -669,13 +669,24 @@ unsigned cgrid(long long n, int nslots, int per = 256) {
 }  // namespace
 
 // ------------------------------------------------------------ workspace
+// An arena that must grow is reallocated with half its old size again as
+// headroom (the exact size if that much is not free), so that a sequence of
+// slightly larger requests (a server's groups) reallocates rarely: cudaFree
+// synchronises the whole device, stalling every stream's work.
 int arena_reserve(Arena &a, size_t bytes) {
     int dev;
     CK(cudaGetDevice(&dev));
     if (a.base && a.cap >= bytes && a.dev == dev) { a.used = 0; return EBCC_OK; }
+    const size_t grown = a.base && a.dev == dev ? std::max(bytes, a.cap + a.cap / 2) : bytes;
     if (a.base) { cudaFree(a.base); a.base = nullptr; a.cap = 0; }
-    CK(cudaMalloc(&a.base, bytes));
-    a.cap = bytes;
+    size_t cap = grown;
+    if (cudaMalloc(&a.base, cap) != cudaSuccess) {
+        cudaGetLastError();
+        a.base = nullptr;
+        cap = bytes;
+        CK(cudaMalloc(&a.base, cap));
+    }
+    a.cap = cap;
     a.used = 0;
     a.dev = dev;
     return EBCC_OK;
