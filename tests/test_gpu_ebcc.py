@@ -220,6 +220,15 @@ def test_host_batch_api(B):
     for f, y, d, b in zip(fields, ys, douts, bounds):
         assert np.array_equal(y, d.cpu().numpy())
         assert _within(f, y, b * (float(f.max()) - float(f.min())))
+    # page-locked streams and outputs (copied by the batch's copy kernel, which
+    # takes the bytes past the last whole 16-byte piece one at a time; stream
+    # lengths are not multiples of 16)
+    pstreams = [torch.frombuffer(bytearray(s), dtype=torch.uint8).pin_memory() for s in want]
+    pys = [torch.full(f.shape, float("nan"), dtype=torch.float32).pin_memory() for f in fields]
+    rc, _ = B.ebcc_decompress_batch(pstreams, [f.shape for f in fields], outs=pys)
+    assert rc == 0
+    for y, py in zip(ys, pys):
+        assert np.array_equal(y, py.numpy())
     # a bad entry fails alone
     rc, host3 = B.ebcc_compress_batch([fields[0], fields[1]], [1e-2, -1.0])
     assert rc == B.EBCC_EINVAL and host3[0][2] == 0 and host3[1][2] == B.EBCC_EINVAL
