@@ -46,7 +46,7 @@ int ebcc_dwt_fwd_dev(const float *in, float *out, size_t ny, size_t nx, int leve
     if (levels < 0 || !in || !out) return EBCC_EINVAL;
     int L = effective_levels((int)ny, (int)nx, levels);
     Tmp t;
-    float *s1, *s2;
+    float *s1 = nullptr, *s2 = nullptr;
     RC(t.get(&s1, dwt_scratch_floats(ny, nx, 1)));
     RC(t.get(&s2, dwt_scratch_floats(ny, nx, 2)));
     double inv = norm_range > 0 ? 1.0 / norm_range : 0.0;
@@ -60,7 +60,7 @@ int ebcc_dwt_inv_dev(const float *in, float *out, size_t ny, size_t nx, int leve
     if (levels < 0 || !in || !out) return EBCC_EINVAL;
     int L = effective_levels((int)ny, (int)nx, levels);
     Tmp t;
-    float *s1, *s2;
+    float *s1 = nullptr, *s2 = nullptr;
     RC(t.get(&s1, dwt_scratch_floats(ny, nx, 1)));
     RC(t.get(&s2, dwt_scratch_floats(ny, nx, 2)));
     RC(dwt_inverse_plain(in, out, s1, s2, (int)ny, (int)nx, L, (cudaStream_t)stream));
@@ -75,7 +75,7 @@ int ebcc_quantise_dev(const float *coef, int32_t *q, size_t ny, size_t nx, int l
     FieldGeom g;
     make_geom(&g, (int)ny, (int)nx, levels, 32, 32, P);
     Tmp t;
-    FieldGeom *dg;
+    FieldGeom *dg = nullptr;
     RC(t.get(&dg, 1));
     CK(cudaMemcpy(dg, &g, sizeof(g), cudaMemcpyHostToDevice));
     FieldRun one = single((int)ny, (int)nx, g.L);
@@ -101,8 +101,8 @@ int ebcc_t1_encode_dev(const int32_t *q, const int32_t *orient, int nblk, int w,
         bd[k].delta = 1.0f;
     }
     Tmp t;
-    BlockDesc *dbd;
-    int32_t *status;
+    BlockDesc *dbd = nullptr;
+    int32_t *status = nullptr;
     RC(t.get(&dbd, nblk + 1));
     RC(t.get(&status, 4));
     if (nblk) CK(cudaMemcpy(dbd, bd.data(), nblk * sizeof(BlockDesc), cudaMemcpyHostToDevice));
@@ -135,7 +135,7 @@ int ebcc_t1_decode_dev(const uint8_t *bytes, const int64_t *off, const int32_t *
         bd[k].delta = 1.0f;
     }
     Tmp t;
-    BlockDesc *dbd;
+    BlockDesc *dbd = nullptr;
     RC(t.get(&dbd, nblk + 1));
     if (nblk) CK(cudaMemcpy(dbd, bd.data(), nblk * sizeof(BlockDesc), cudaMemcpyHostToDevice));
     RC(t1_decode_blocks(bytes, off, len, dbd, K, npass, nblk, w, h, nullptr, mag, plane, neg, (long long)nblk * w * h,
@@ -151,9 +151,9 @@ int ebcc_pcrd_dev(const int32_t *npass, const int32_t *pass_len, const int64_t *
     Tmp t;
     Hulls hl;
     hl.maxpt = T1_MAXPASS + 1;
-    double *db;
-    Sel *sel;
-    FieldScal *sc;
+    double *db = nullptr;
+    Sel *sel = nullptr;
+    FieldScal *sc = nullptr;
     RC(t.get(&hl.nh, nblk + 1));
     RC(t.get(&hl.pt, (size_t)(nblk + 1) * hl.maxpt));
     RC(t.get(&hl.rate, (size_t)(nblk + 1) * hl.maxpt));
@@ -189,8 +189,8 @@ int ebcc_spiht_encode_dev(const int32_t *s, size_t ny, size_t nx, int levels, ui
     const size_t n = ny * nx;
     int L = effective_levels((int)ny, (int)nx, levels);
     Tmp t;
-    uint8_t *w;
-    FieldScal *sc;
+    uint8_t *w = nullptr;
+    FieldScal *sc = nullptr;
     RC(t.get(&w, spiht_work_bytes(n)));
     RC(t.get(&sc, 1));
     CK(cudaMemsetAsync(sc, 0, sizeof(FieldScal), st));
@@ -223,8 +223,8 @@ int ebcc_spiht_decode_dev(const uint8_t *in, int64_t nbits, size_t ny, size_t nx
     const size_t n = ny * nx;
     int L = effective_levels((int)ny, (int)nx, levels);
     Tmp t;
-    uint8_t *w;
-    FieldScal *sc;
+    uint8_t *w = nullptr;
+    FieldScal *sc = nullptr;
     RC(t.get(&w, spiht_work_bytes(n)));
     RC(t.get(&sc, 1));
     FieldScal h;
@@ -251,7 +251,7 @@ int ebcc_spiht_prefix_recon_dev(const int32_t *s, const uint32_t *sig_pos, const
         return EBCC_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     Tmp t;
-    FieldScal *sc;
+    FieldScal *sc = nullptr;
     RC(t.get(&sc, 1));
     FieldScal h;
     memset(&h, 0, sizeof(h));
@@ -276,8 +276,8 @@ int ebcc_count_within_dev(const float *x, const float *an_hat, size_t n, double 
         return EBCC_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     Tmp t;
-    float2 *b;
-    FieldScal *sc;
+    float2 *b = nullptr;
+    FieldScal *sc = nullptr;
     RC(t.get(&b, n + 1));
     RC(t.get(&sc, 1));
     CK(cudaMemsetAsync(sc, 0, sizeof(FieldScal), st));
