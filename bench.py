@@ -61,6 +61,25 @@ BOUND = 1e-2
 FALLBACK_HBM_GBS = 6800.0
 
 
+def measured_hbm_gbs(path):
+    """The measured HBM copy bandwidth (GB/s) from the peaks file: its
+    `hbm_gbs` entry, a number or an object holding one; None when the file,
+    the entry or a positive number is missing."""
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    v = d.get("hbm_gbs") if isinstance(d, dict) else None
+    if isinstance(v, dict):
+        v = next((v[k] for k in ("value", "gbs", "burst", "mean", "median") if k in v), None)
+    try:
+        v = float(v)
+    except (TypeError, ValueError):
+        return None
+    return v if v > 0 else None
+
+
 def workload_fields(n_vars=4, n_levels=37, ny=721, nx=1440):
     out = []
     for v in range(n_vars):
@@ -562,11 +581,11 @@ def run_gpu(args):
             dist.destroy_process_group()
         return
     value = job_gbs(raw_bytes, world, t_ms)
-    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk_path):
-        peak, peak_src = float(json.load(open(pk_path))["hbm_gbs"]), "measured copy (MEASURED_PEAKS.json)"
+    peak = measured_hbm_gbs(os.path.join(ROOT, "MEASURED_PEAKS.json"))
+    if peak:
+        peak_src = "measured copy (MEASURED_PEAKS.json hbm_gbs)"
     else:
-        peak, peak_src = FALLBACK_HBM_GBS, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
+        peak, peak_src = FALLBACK_HBM_GBS, "fallback 6.8 TB/s (no usable hbm_gbs in MEASURED_PEAKS.json)"
     roof = None
     if prof:
         top = max(prof, key=lambda p: p["ms"])

@@ -97,3 +97,17 @@ def test_reference_arm_silent_on_other_ranks():
     r = _reference({"RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_measured_peak_file_shapes(tmp_path):
+    import json
+    import bench
+    p = tmp_path / "peaks.json"
+    assert bench.measured_hbm_gbs(str(p)) is None  # absent
+    for content, want in [({"hbm_gbs": 6775.6}, 6775.6), ({"hbm_gbs": {"value": 7000}}, 7000.0),
+                          ({"hbm_gbs": "x"}, None), ({"bf16_tflops": 1900}, None), ([1, 2], None),
+                          ({"hbm_gbs": -1}, None)]:
+        p.write_text(json.dumps(content))
+        assert bench.measured_hbm_gbs(str(p)) == want
+    p.write_text("{not json")
+    assert bench.measured_hbm_gbs(str(p)) is None
