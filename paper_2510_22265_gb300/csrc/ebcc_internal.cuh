@@ -339,9 +339,11 @@ constexpr int T1_GUARD = 4;
 #define SYM_PER_COEF 40
 int t1_encode_blocks(int32_t *qt, const BlockDesc *blk, int nblk, int maxw, int maxh, const T1Out &o,
                      int sign_magnitude_q, uint8_t *spp_out, long long nq, cudaStream_t st);
+// order (optional, nblk + 1024 entries): scratch for decoding the blocks longest first
 int t1_decode_blocks(const uint8_t *bytes, const int64_t *off, const int32_t *len, const BlockDesc *blk,
                      const int32_t *K, const int32_t *npass, int nblk, int maxw, int maxh, float *coef,
-                     int32_t *mag, int8_t *plane, uint8_t *neg, long long nq, int *guard, cudaStream_t st);
+                     int32_t *mag, int8_t *plane, uint8_t *neg, long long nq, int *guard, int32_t *order,
+                     cudaStream_t st);
 
 // ------------------------------------------------------------ PCRD
 // Batch-wide arrays, indexed by global code-block (hull points) or by

@@ -956,6 +956,7 @@ void layout_decompress(Arena &a, Batch &b, const std::vector<int> &ny, const std
     b.t1.K = carve<int32_t>(a, nb);
     b.t1.pass_len = carve<int32_t>(a, nb);  // payload length per block
     b.t1.status = carve<int32_t>(a, 4);     // T1_GUARD: a range check of the tier-1 decoder missed
+    b.t1.order = carve<int32_t>(a, nb + 1024);  // decoding order, longest first, and its histogram
     b.npass = carve<int32_t>(a, nb);
     b.addr = carve<int64_t>(a, nb);
     b.d_blk = carve<BlockDesc>(a, nb);
@@ -1631,7 +1632,7 @@ int decompress_batch(Engine &e, const ebcc_stream_desc *sd, int n, float *const 
             remove_from(E, bad);
             // tier-1 of every code-block of the batch (failed fields decode nothing)
             RC(t1_decode_blocks(nullptr, b.addr, b.t1.pass_len, b.d_blk, b.t1.K, b.npass, blk0, maxw, maxh,
-                                b.run[0].W, nullptr, nullptr, nullptr, b.Ntot, b.t1.status, st));
+                                b.run[0].W, nullptr, nullptr, nullptr, b.Ntot, b.t1.status, b.t1.order, st));
             STAGE(st, "tier-1 decode");
         }
         if (!B1.empty()) {  // base layer only: IDWT, denormalise

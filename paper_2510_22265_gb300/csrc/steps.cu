@@ -139,7 +139,7 @@ int ebcc_t1_decode_dev(const uint8_t *bytes, const int64_t *off, const int32_t *
     RC(t.get(&dbd, nblk + 1));
     if (nblk) CK(cudaMemcpy(dbd, bd.data(), nblk * sizeof(BlockDesc), cudaMemcpyHostToDevice));
     RC(t1_decode_blocks(bytes, off, len, dbd, K, npass, nblk, w, h, nullptr, mag, plane, neg, (long long)nblk * w * h,
-                         nullptr, st));
+                         nullptr, nullptr, st));
     CK(cudaStreamSynchronize(st));
     return EBCC_OK;
 }

@@ -889,7 +889,7 @@ __global__ void __launch_bounds__(WARPS * 32) t1_decode_kernel(const uint8_t *by
                                                                const int32_t *Kb, const int32_t *npb, int nblk,
                                                                float *coef, int32_t *omag, int8_t *oplane,
                                                                uint8_t *oneg, SmemLayout SL, int maxh, long long nq,
-                                                               int *guard) {
+                                                               int *guard, const int32_t *order) {
     bool miss = false;
     extern __shared__ __align__(16) uint8_t sm[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -902,7 +902,8 @@ __global__ void __launch_bounds__(WARPS * 32) t1_decode_kernel(const uint8_t *by
     S.neg = S.ref + maxh;
     uint8_t *I = base + SL.ctx_off, *M = I + 24;
     int8_t *pl = (int8_t *)(base + SL.pl_off);
-    for (int b = blockIdx.x * WARPS + wid; b < nblk; b += gridDim.x * WARPS) {
+    for (int i = blockIdx.x * WARPS + wid; i < nblk; i += gridDim.x * WARPS) {
+        const int b = order ? order[i] : i;  // longest first when ordered
         const BlockDesc d = blk[b];
         const int w = d.w, h = d.h, n = w * h;
         S.w = w; S.h = h;
@@ -1148,16 +1149,66 @@ int t1_encode_blocks(int32_t *qt, const BlockDesc *blk, int nblk, int maxw, int 
     return EBCC_OK;
 }
 
+// ---- decoder order: blocks by payload length, longest first (counting sort
+// in bins of 16 bytes), so that the warps, which take blocks in turn, start
+// on the long serial decodes and finish on the short ones
+constexpr int DEC_BINS = 1024;
+__device__ __forceinline__ int dec_bin(const int32_t *len, int b) {
+    const int t = len[b] > 0 ? len[b] >> 4 : 0;
+    return DEC_BINS - 1 - (t < DEC_BINS - 1 ? t : DEC_BINS - 1);  // longest first
+}
+__global__ void dec_order_count(const int32_t *len, int nblk, int *hist) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x)
+        atomicAdd(&hist[dec_bin(len, b)], 1);
+}
+__global__ void __launch_bounds__(DEC_BINS) dec_order_scan(int *hist) {
+    __shared__ int ws[DEC_BINS / 32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int v = hist[t];
+    int x = v;
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) ws[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int z = ws[lane];
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, z, d);
+            if (lane >= d) z += y;
+        }
+        ws[lane] = z;
+    }
+    __syncthreads();
+    hist[t] = x - v + (wid ? ws[wid - 1] : 0);  // exclusive offsets
+}
+__global__ void dec_order_place(const int32_t *len, int nblk, int *hist, int32_t *order) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x) {
+        const int at = atomicAdd(&hist[dec_bin(len, b)], 1);
+        if (at < nblk) order[at] = b;
+    }
+}
+
 int t1_decode_blocks(const uint8_t *bytes, const int64_t *off, const int32_t *len, const BlockDesc *blk,
                      const int32_t *K, const int32_t *npass, int nblk, int maxw, int maxh, float *coef, int32_t *mag,
-                     int8_t *plane, uint8_t *neg, long long nq, int *guard, cudaStream_t st) {
+                     int8_t *plane, uint8_t *neg, long long nq, int *guard, int32_t *order, cudaStream_t st) {
     int rc = upload_tables();
     if (rc) return rc;
     if (nblk <= 0) return EBCC_OK;
     if (maxw > 64 || maxh > 64) return EBCC_EINVAL;
     SmemLayout SL = smem_layout(maxw * maxh, maxh, true);
+    if (order) {  // scratch: nblk entries, then DEC_BINS for the histogram
+        int *hist = order + nblk;
+        CK(cudaMemsetAsync(hist, 0, sizeof(int) * DEC_BINS, st));
+        const unsigned g = (unsigned)((nblk + 255) / 256 < 1216 ? (nblk + 255) / 256 : 1216);
+        PROF("dec_order", st, 0.0, dec_order_count<<<g, 256, 0, st>>>(len, nblk, hist));
+        PROF("dec_order", st, 0.0, dec_order_scan<<<1, DEC_BINS, 0, st>>>(hist));
+        PROF("dec_order", st, 0.0, dec_order_place<<<g, 256, 0, st>>>(len, nblk, hist, order));
+        CK(cudaGetLastError());
+    }
     PROF("t1_decode_kernel", st, 0.0, t1_decode_kernel<<<grid_for(nblk), WARPS * 32, WARPS * SL.per_warp, st>>>(bytes, off, len, blk, K, npass, nblk,
-                                                                             coef, mag, plane, neg, SL, maxh, nq, guard););
+                                                                             coef, mag, plane, neg, SL, maxh, nq, guard, order););
     CK(cudaGetLastError());
     return EBCC_OK;
 }
