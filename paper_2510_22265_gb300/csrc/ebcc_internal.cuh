@@ -54,7 +54,6 @@ struct BlockDesc {
 
 int effective_levels(int ny, int nx, int levels);
 void make_geom(FieldGeom *g, int ny, int nx, int levels, int cw, int ch, int P);
-void make_blocks(const FieldGeom &g, std::vector<BlockDesc> &out);
 double band_step(int P, int level, int orient);
 int base_precision(double eps_n);
 

@@ -122,26 +122,6 @@ void make_geom(FieldGeom *g, int ny, int nx, int levels, int cw, int ch, int P) 
     g->nblocks = nb;
 }
 
-void make_blocks(const FieldGeom &g, std::vector<BlockDesc> &out) {
-    out.clear();
-    out.reserve(g.nblocks);
-    for (int b = 0; b < g.nbands; b++) {
-        const BandGeom &B = g.band[b];
-        for (int by = 0; by < B.nby; by++)
-            for (int bx = 0; bx < B.nbx; bx++) {
-                BlockDesc d;
-                int y = B.y0 + by * g.ch, x = B.x0 + bx * g.cw;
-                d.off = (long long)y * g.nx + x;
-                d.stride = g.nx;
-                d.w = (B.w - bx * g.cw) < g.cw ? (B.w - bx * g.cw) : g.cw;
-                d.h = (B.h - by * g.ch) < g.ch ? (B.h - by * g.ch) : g.ch;
-                d.orient = B.orient;
-                d.delta = B.delta;
-                out.push_back(d);
-            }
-    }
-}
-
 int ebcc_debug_sync_enabled() {
     static int v = -1;
     if (v < 0) {

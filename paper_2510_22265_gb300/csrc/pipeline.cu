@@ -597,6 +597,50 @@ __global__ void hdr_gather(const uint8_t *const *src, const long long *len, int 
         dst[(size_t)f * HDR_BYTES + k] = len[f] >= HDR_BYTES ? src[f][k] : 0;
 }
 
+// the code-block descriptors of fields f0 .. f0 + gridDim.y - 1 of the table,
+// built on the device from each field's geometry (its blocks band by band,
+// raster within a band, each band cut from its top-left corner, the last
+// block of a row or column clipped to the band): block j of field f goes to
+// out[blk0 + j], its offset counted from `base0` in the field's plane (qt
+// when which = 0, W when which = 1)
+__global__ void build_blocks(const FieldRun *tab, const FieldGeom *geom, int f0, int F, int which,
+                             const void *base0, BlockDesc *out) {
+    const int f = f0 + (int)blockIdx.y;
+    if (f >= F) return;
+    const FieldRun &r = tab[f];
+    const int nb = r.nblk;
+    if (nb <= 0) return;
+    const FieldGeom &g = geom[f];
+    const long long base = which ? (long long)(r.W - (const float *)base0) : (long long)(r.qt - (const int32_t *)base0);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nb; j += gridDim.x * blockDim.x) {
+        int q = 0;
+        while (q + 1 < g.nbands && g.band[q + 1].blk0 <= j) q++;
+        const BandGeom &B = g.band[q];
+        const int k = j - B.blk0, by = k / B.nbx, bx = k - by * B.nbx;
+        BlockDesc d;
+        d.off = (long long)(B.y0 + by * g.ch) * g.nx + (B.x0 + bx * g.cw) + base;
+        d.stride = g.nx;
+        d.w = B.w - bx * g.cw < g.cw ? B.w - bx * g.cw : g.cw;
+        d.h = B.h - by * g.ch < g.ch ? B.h - by * g.ch : g.ch;
+        d.orient = B.orient;
+        d.delta = B.delta;
+        out[r.blk0 + j] = d;
+    }
+}
+
+int build_blocks_b(const FieldRun *tab, const FieldGeom *geom, BlockDesc *out, int F, int maxnblk, int which,
+                   const void *base0, cudaStream_t st) {
+    if (F <= 0 || maxnblk <= 0) return EBCC_OK;
+    const int gx = (maxnblk + 255) / 256 < 64 ? (maxnblk + 255) / 256 : 64;
+    for (int f0 = 0; f0 < F; f0 += 65535) {
+        const int nf = F - f0 < 65535 ? F - f0 : 65535;
+        PROF("build_blocks", st, 0.0,
+             build_blocks<<<dim3(gx, nf), 256, 0, st>>>(tab, geom, f0, F, which, base0, out));
+        CK(cudaGetLastError());
+    }
+    return EBCC_OK;
+}
+
 // sequential parse of the base metadata of one stream: per-block pass count,
 // K, payload length and absolute payload address; sc->ok = 0 on inconsistency
 __global__ void base_parse(Live lv, int32_t *np_all, int32_t *K_all, int32_t *len_all, int64_t *addr_all) {
@@ -768,7 +812,6 @@ struct Batch {
     int F = 0;                      // table entries
     std::vector<FieldRun> run;      // host copy of the table
     std::vector<FieldGeom> geom;
-    std::vector<BlockDesc> blk;     // code-blocks of the fields taking part, in table order
     FieldRun *d_run = nullptr;
     FieldGeom *d_geom = nullptr;
     FieldScal *d_sc = nullptr;
@@ -1212,7 +1255,6 @@ int compress_batch(Engine &e, const ebcc_field_desc *fd, int n, ebcc_out_desc *o
     std::vector<double> mn(F), mx(F), eps(F), eps_n(F);
     std::vector<int> P(F, 0);
     b.geom.assign(F, FieldGeom{});
-    b.blk.clear();
     const int32_t *qt0 = b.run[0].qt;
     int blk0 = 0;
     batch_dims_init(b.dims);
@@ -1230,10 +1272,6 @@ int compress_batch(Engine &e, const ebcc_field_desc *fd, int n, ebcc_out_desc *o
         if (guard > 0.25 * eps[f]) guard = 0.25 * eps[f];
         P[f] = base_precision(eps_n[f]);
         make_geom(&b.geom[f], ny[f], nx[f], p.levels, cw, ch, P[f]);
-        std::vector<BlockDesc> bd;
-        make_blocks(b.geom[f], bd);
-        const long long base = (long long)(r.qt - qt0);
-        for (BlockDesc &x : bd) { x.off += base; b.blk.push_back(x); }
         r.inv_range = 1.0 / range;
         r.E = eps[f] - guard;
         r.blk0 = blk0;
@@ -1246,7 +1284,7 @@ int compress_batch(Engine &e, const ebcc_field_desc *fd, int n, ebcc_out_desc *o
     RC(stage_maps(e, b, A, st));
     RC(upload(e, b.d_run, b.run.data(), F * sizeof(FieldRun), st));
     RC(upload(e, b.d_geom, b.geom.data(), F * sizeof(FieldGeom), st));
-    RC(upload(e, b.d_blk, b.blk.data(), b.blk.size() * sizeof(BlockDesc), st));
+    RC(build_blocks_b(b.d_run, b.d_geom, b.d_blk, F, b.dims.maxnblk, 0, qt0, st));
     std::vector<BaseLoop> hb1(F), hb2(F);
     std::vector<TruncLoop> htl(F);
     std::vector<int> G(F, p.spiht_guard_bits), esv(F, 0), nmaxv(F, -1);
@@ -1579,7 +1617,6 @@ int decompress_batch(Engine &e, const ebcc_stream_desc *sd, int n, float *const 
         const float *W0 = b.run[0].W;
         int blk0 = 0, maxw = 4, maxh = 4;
         batch_dims_init(b.dims);
-        b.blk.clear();
         for (int f = 0; f < F; f++) {
             const ParsedHeader &h = H[vin[f]];
             FieldRun &r = b.run[f];
@@ -1595,10 +1632,6 @@ int decompress_batch(Engine &e, const ebcc_stream_desc *sd, int n, float *const 
             r.blk0 = blk0;
             r.nblk = nblk[f];
             blk0 += nblk[f];
-            std::vector<BlockDesc> bd;
-            make_blocks(b.geom[f], bd);
-            const long long base = (long long)(r.W - W0);
-            for (BlockDesc &x : bd) { x.off += base; b.blk.push_back(x); }
             maxw = std::max(maxw, h.cw);
             maxh = std::max(maxh, h.ch);
             sc[f].nbits = 8LL * h.rl;
@@ -1614,7 +1647,7 @@ int decompress_batch(Engine &e, const ebcc_stream_desc *sd, int n, float *const 
         RC(upload(e, b.d_run, b.run.data(), F * sizeof(FieldRun), st));
         RC(upload(e, b.d_geom, b.geom.data(), F * sizeof(FieldGeom), st));
         RC(upload(e, b.d_sc, sc.data(), F * sizeof(FieldScal), st));
-        RC(upload(e, b.d_blk, b.blk.data(), b.blk.size() * sizeof(BlockDesc), st));
+        RC(build_blocks_b(b.d_run, b.d_geom, b.d_blk, F, b.dims.maxnblk, 1, W0, st));
         CK(cudaMemsetAsync(b.t1.status, 0, sizeof(int32_t), st));
         const Live lv = live_of(b);
         std::vector<char> bad(F, 0);
