@@ -1655,6 +1655,13 @@ int decompress_batch(Engine &e, const ebcc_stream_desc *sd, int n, float *const 
             RC(set_list(e, b, D, st));
             PROF("base_parse", st, 0.0, base_parse<<<(int)D.size(), 32, 0, st>>>(lv, b.npass, b.t1.K, b.t1.pass_len, b.addr));
             CK(cudaGetLastError());
+            // tier-1 of every code-block of the batch: base_parse gives the
+            // blocks of a stream that does not parse no passes and no payload,
+            // so they decode nothing, and the host reads the parse outcomes
+            // while the decoder runs
+            RC(t1_decode_blocks(nullptr, b.addr, b.t1.pass_len, b.d_blk, b.t1.K, b.npass, blk0, maxw, maxh,
+                                b.run[0].W, nullptr, nullptr, nullptr, b.Ntot, b.t1.status, b.t1.order, st));
+            STAGE(st, "tier-1 decode");
             FieldScal *hs = nullptr;
             RC(download(e, b.d_sc, F, &hs, st));
             for (int f : D)
@@ -1663,10 +1670,6 @@ int decompress_batch(Engine &e, const ebcc_stream_desc *sd, int n, float *const 
             remove_from(B1, bad);
             remove_from(B2, bad);
             remove_from(E, bad);
-            // tier-1 of every code-block of the batch (failed fields decode nothing)
-            RC(t1_decode_blocks(nullptr, b.addr, b.t1.pass_len, b.d_blk, b.t1.K, b.npass, blk0, maxw, maxh,
-                                b.run[0].W, nullptr, nullptr, nullptr, b.Ntot, b.t1.status, b.t1.order, st));
-            STAGE(st, "tier-1 decode");
         }
         if (!B1.empty()) {  // base layer only: IDWT, denormalise
             RC(set_list(e, b, B1, st));
