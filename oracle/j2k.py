@@ -24,6 +24,10 @@ trees' leaves for blocks the layer leaves out); the packet header of a
 resolution with no included block is the single bit 0; a code-block length is
 written with the fewest Lblock increments.
 
+Parity unpinned for conformance: no third-party JPEG 2000 decoder is at hand,
+so a misreading of the syntax shared by this writer and this reader (a tag-tree
+bit order, say) would pass; the tables it uses are pinned to T.800's.
+
 Only ``tests/`` may import this module.  It shares no code with the library.
 """
 from __future__ import annotations

@@ -5,6 +5,12 @@
  * DECODE / RENORMD / BYTEIN) and its 47-state probability table (Table C.2).
  * EBCC's base layer uses JPEG2000 (Materials and Methods), whose tier-1 coder
  * drives this arithmetic coder.
+ *
+ * Parity unpinned: the Qe / NMPS / NLPS / SWITCH values of Table C.2 are as
+ * read from the standard, with no published coded-byte sequence to hold them
+ * to; the tests pin the coder's procedures (round trips, long runs, code
+ * length against the empirical entropy, the table's structure) but a wrong
+ * Qe value shared by encoder and decoder would pass them.
  */
 #include <string.h>
 #include "oracle.h"
