@@ -185,8 +185,8 @@ extern "C" int ebcc_j2k_codestream(const uint8_t *stream, size_t len, uint8_t **
     }
     for (int k = 0; k < g.nblocks; k++) {
         blk[k].data = b;
+        if (blk[k].len > end - b) return EBCC_ECORRUPT;
         b += blk[k].len;
-        if (b > end) return EBCC_ECORRUPT;
     }
     // quantisation: epsilon_b, mu_b per band, and the guard bits
     std::vector<int> eps_b(g.nbands), mu_b(g.nbands);

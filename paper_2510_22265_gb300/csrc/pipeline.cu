@@ -666,7 +666,12 @@ __global__ void base_parse(Live lv, int32_t *np_all, int32_t *K_all, int32_t *le
                 sh += 7;
                 if (!(c & 0x80)) { done = 1; break; }
             }
-            if (!done || k < 1 || k > 30 || n > 3 * k - 2) { good = 0; break; }
+            // a length must fit the section: lengths that wrap int32 could
+            // otherwise sum to base_len with a payload outside it
+            if (!done || k < 1 || k > 30 || n > 3 * k - 2 || v > 0x7FFFFFFFu || (long long)v > base_len) {
+                good = 0;
+                break;
+            }
             K_all[b0 + b] = k; len_all[b0 + b] = (int32_t)v;
         }
     }
