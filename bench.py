@@ -508,7 +508,6 @@ def run_gpu(args):
         e2e_out = sum(r[1] for r in res_e)
     t_e2e = float(np.median(e2e_times))  # host wall clock: the median step, every step listed
     t_e2e_job = max_over_ranks(t_e2e * 1e3, dist, "cuda")  # ms, the slowest rank
-    pool = mp.get_context("spawn").Pool(cores)
     # the stack at the other two bounds of the benchmark grid (0.1% and 10%)
     other_bounds = {}
     for bb in (1e-3, 1e-1):
@@ -525,6 +524,9 @@ def run_gpu(args):
         t1, r1 = timed_batch(B, torch, [d1], [BOUND], [o1], max(3, args.steps), stream)
         one = {"ms_per_field": t1, "compress_gbs": x1.nbytes / (t1 / 1e3) / 1e9, "cr": x1.nbytes / r1[0][1],
                "what": "one 181x360 field (seed 0), one call"}
+    # a new process pool for the legs' input generation, started only now: its
+    # processes' start-up would otherwise share the host with timed calls
+    pool = mp.get_context("spawn").Pool(cores)
     # the uneven batch: grids 91x180 .. 1441x2880, bounds log-uniform in 0.1-10%
     uneven = None
     if args.uneven and legs:
