@@ -410,6 +410,31 @@ __global__ void __launch_bounds__(NT) fwd_identity(Live lv, const __grid_constan
     }
 }
 
+// the exact normalisation fl32((x - mn) * inv) of plane src into plane dst,
+// for fields with DWT levels (a level-0 field takes fwd_identity)
+__global__ void __launch_bounds__(NT) norm_plane(Live lv, const __grid_constant__ FieldRun one, int src_plane,
+                                                 int dst_plane) {
+    int f;
+    const FieldRun *r = pick(lv, one, blockIdx.y, f);
+    if (!r || r->L == 0) return;
+    const float *__restrict__ src = plane_ptr(*r, src_plane);
+    float *__restrict__ dst = plane_ptr(*r, dst_plane);
+    const double mn = r->mn, inv = r->inv_range;
+    const NormK k = make_norm_k(mn, inv);
+    const long long n = r->N;
+    // the next three points' loads stay in flight while a point is worked on
+    const long long st = (long long)gridDim.x * NT, i0 = blockIdx.x * (long long)NT + threadIdx.x;
+    float q0 = i0 < n ? src[i0] : 0.0f, q1 = i0 + st < n ? src[i0 + st] : 0.0f;
+    float q2 = i0 + 2 * st < n ? src[i0 + 2 * st] : 0.0f;
+    for (long long i = i0; i < n; i += st) {
+        const float v = q0;
+        q0 = q1;
+        q1 = q2;
+        q2 = i + 3 * st < n ? src[i + 3 * st] : 0.0f;
+        dst[i] = norm_value(v, k, mn, inv);
+    }
+}
+
 __global__ void __launch_bounds__(NT) inv_identity(Live lv, const __grid_constant__ FieldRun one, int src_plane,
                                                    InvFinal fin) {
     int f;
@@ -449,7 +474,7 @@ void batch_dims_add(BatchDims &d, int ny, int nx, int L, int nblk) {
 }
 
 int dwt_forward_b(const Live &lv, const FieldRun &one, int nslots, const BatchDims &d, int src, int norm,
-                  cudaStream_t st) {
+                  cudaStream_t st, int norm_into) {
     if (nslots <= 0) return EBCC_OK;
     if (d.any_L0) {
         PROF("fwd_identity", st, 0.0, fwd_identity<<<dim3(pgrid(d.maxN, nslots), nslots), NT, 0, st>>>(lv, one, src, norm));
@@ -459,7 +484,14 @@ int dwt_forward_b(const Live &lv, const FieldRun &one, int nslots, const BatchDi
         const int hp = d.h[l - 1], wp = d.w[l - 1];
         dim3 grid((wp + TX - 1) / TX, (hp + TY - 1) / TY, nslots);
         const double bytes = 8.0 * hp * wp * nslots;
-        if (l == 1 && norm)
+        if (l == 1 && norm && norm_into >= 0) {
+            // the normalisation once per point at full occupancy, instead of
+            // on every tile's halo inside the load phase of the tile kernel
+            PROF("norm_plane", st, 8.0 * (double)d.maxN * nslots,
+                 norm_plane<<<dim3(pgrid(d.maxN, nslots), nslots), NT, 0, st>>>(lv, one, src, norm_into));
+            CK(cudaGetLastError());
+            PROF("fwd_level", st, bytes, fwd_level<false><<<grid, 96, 0, st>>>(lv, one, l, norm_into));
+        } else if (l == 1 && norm)
             PROF("fwd_level", st, bytes, fwd_level<true><<<grid, 96, 0, st>>>(lv, one, l, src));
         else
             PROF("fwd_level", st, bytes, fwd_level<false><<<grid, 96, 0, st>>>(lv, one, l, src));

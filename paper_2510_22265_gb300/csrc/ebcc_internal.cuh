@@ -285,9 +285,11 @@ struct InvFinal {
     // (original units) into `dst`.  Counts add to sc->cnt[counter].
     int mode, add_base, dst, counter;
 };
-// forward: plane `src` (PL_X with normalisation when norm, or PL_R) -> W
+// forward: plane `src` (PL_X with normalisation when norm, or PL_R) -> W.
+// norm_into >= 0: the normalised field is first written to that plane by an
+// elementwise pass and level 1 reads it there (same values as the fused form)
 int dwt_forward_b(const Live &lv, const FieldRun &one, int nslots, const BatchDims &d, int src, int norm,
-                  cudaStream_t st);
+                  cudaStream_t st, int norm_into = -1);
 // inverse: plane `src` (W or R), finished per fin
 int dwt_inverse_b(const Live &lv, const FieldRun &one, int nslots, const BatchDims &d, int src, InvFinal fin,
                   cudaStream_t st);

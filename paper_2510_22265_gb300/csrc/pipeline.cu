@@ -1304,7 +1304,7 @@ int compress_batch(Engine &e, const ebcc_field_desc *fd, int n, ebcc_out_desc *o
         // ---- per-point acceptance intervals of the bound test (FP64, once)
         RC(make_bounds_b(lv, kNone, na, b.dims.maxN, st));
         // ---- base layer: DWT of the normalised field, quantise, tier-1, hulls
-        RC(dwt_forward_b(lv, kNone, na, b.dims, PL_X, 1, st));
+        RC(dwt_forward_b(lv, kNone, na, b.dims, PL_X, 1, st, PL_R));  // R is free until the residue
         RC(quantise_b(lv, kNone, na, b.dims.maxN, 1, st));
         STAGE(st, "quantise");
         CK(cudaMemsetAsync(b.t1.status, 0, 4, st));

@@ -315,8 +315,15 @@ __global__ void __launch_bounds__(NT) bounds_kernel(Live lv, const __grid_consta
     }
     __syncthreads();
     const BoundsK k = sk;
-    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) {
-        const float xf = xs[i];
+    // the next three points' loads stay in flight while a point is worked on
+    const long long st = (long long)gridDim.x * NT, i0 = blockIdx.x * (long long)NT + threadIdx.x;
+    float q0 = i0 < n ? xs[i0] : 0.0f, q1 = i0 + st < n ? xs[i0 + st] : 0.0f;
+    float q2 = i0 + 2 * st < n ? xs[i0 + 2 * st] : 0.0f;
+    for (long long i = i0; i < n; i += st) {
+        const float xf = q0;
+        q0 = q1;
+        q1 = q2;
+        q2 = i + 3 * st < n ? xs[i + 3 * st] : 0.0f;
         float2 fb;
         if (k.ok && bounds_fast(xf, k, fb)) {
             bounds[i] = fb;
@@ -366,8 +373,19 @@ __global__ void __launch_bounds__(NT) residue_kernel(Live lv, const __grid_const
     const double mn = r->mn, inv = r->inv_range;
     const NormK k = make_norm_k(mn, inv);
     const long long n = r->N;
-    for (long long i = blockIdx.x * (long long)NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT)
-        res[i] = residue_value(x[i], ab[i], k, mn, inv);
+    // the next three points' loads stay in flight while a point is worked on
+    const long long st = (long long)gridDim.x * NT, i0 = blockIdx.x * (long long)NT + threadIdx.x;
+    float x0 = 0.0f, x1 = 0.0f, x2 = 0.0f, a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+    if (i0 < n) { x0 = x[i0]; a0 = ab[i0]; }
+    if (i0 + st < n) { x1 = x[i0 + st]; a1 = ab[i0 + st]; }
+    if (i0 + 2 * st < n) { x2 = x[i0 + 2 * st]; a2 = ab[i0 + 2 * st]; }
+    for (long long i = i0; i < n; i += st) {
+        const float xv = x0, av = a0;
+        x0 = x1; a0 = a1;
+        x1 = x2; a1 = a2;
+        if (i + 3 * st < n) { x2 = x[i + 3 * st]; a2 = ab[i + 3 * st]; }
+        res[i] = residue_value(xv, av, k, mn, inv);
+    }
 }
 
 __global__ void __launch_bounds__(NT) squant_kernel(Live lv, const __grid_constant__ FieldRun one) {
