@@ -6,13 +6,12 @@
 * compression ratio within 1% of the oracle's on the same field;
 * error codes, degenerate fields, batched == plain.
 """
-import struct
-
 import numpy as np
 import pytest
 
 import oracle as O
 from paper_2510_22265_gb300 import synth
+from streamutil import wrap_first_length
 
 pytestmark = pytest.mark.gpu
 
@@ -236,55 +235,12 @@ def test_host_batch_api(B):
     assert rc == B.EBCC_EINVAL and host3[0][2] == 0 and host3[1][2] == B.EBCC_EINVAL
 
 
-def _leb128(v):
-    out = bytearray()
-    while v >= 0x80:
-        out.append(0x80 | (v & 0x7F))
-        v >>= 7
-    out.append(v)
-    return bytes(out)
-
-
-def _wrap_first_length(s: bytes) -> bytes:
-    """The stream with the first two coded blocks' payload lengths rewritten
-    as (len_a - d) mod 2^32 and len_b + d, d = len_a + 1: the lengths still
-    sum to the base section, but the first reads as -1 in 32 bits.  Base
-    metadata (after the 64-byte header): per block its pass count, then, when
-    nonzero, K and the payload length as a 7-bit little-endian varint; the
-    base section's length is the uint32 at header byte 20."""
-    hdr, bl = 64, struct.unpack_from("<I", s, 20)[0]
-    pos, recs = hdr, []
-    while len(recs) < 2:
-        n = s[pos]
-        pos += 1
-        if n == 0:
-            continue
-        k0 = pos + 1  # after K
-        v, sh, q = 0, 0, k0
-        while True:
-            c = s[q]
-            q += 1
-            v |= (c & 0x7F) << sh
-            sh += 7
-            if not c & 0x80:
-                break
-        recs.append((k0, q, v))
-        pos = q
-    (a0, a1, la), (b0, b1, lb) = recs
-    d = la + 1
-    out = (s[:a0] + _leb128((la - d) % (1 << 32)) + s[a1:b0] + _leb128(lb + d) + s[b1:])
-    grow = len(out) - len(s)
-    out = bytearray(out)
-    struct.pack_into("<I", out, 20, bl + grow)
-    return bytes(out)
-
-
 def test_wrapped_block_length_is_corrupt(B):
     """A base section whose payload lengths sum correctly but one of which
     wraps a 32-bit integer is rejected (ECORRUPT), alone in its batch."""
     x = synth.smooth_field(91, 180, seed=4)
     s, _ = B.ebcc_compress(x, 1e-2)
-    bad = _wrap_first_length(s)
+    bad = wrap_first_length(s)
     with pytest.raises(B.EbccError) as e:
         B.ebcc_decompress(bad, *x.shape)
     assert e.value.code == -3

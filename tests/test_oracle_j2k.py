@@ -15,6 +15,7 @@ import pytest
 
 import oracle as O
 from oracle import j2k
+from streamutil import wrap_first_length
 
 GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "t800_table_b4.txt")
 
@@ -224,3 +225,7 @@ def test_library_export_errors(B, streams):
     with pytest.raises(B.EbccError) as e:
         B.ebcc_j2k_codestream(c)
     assert e.value.code == B.EBCC_EINVAL
+    # payload lengths that sum to the section but one of which is 2^32 - 1
+    with pytest.raises(B.EbccError) as e:
+        B.ebcc_j2k_codestream(wrap_first_length(s))
+    assert e.value.code == B.EBCC_ECORRUPT
