@@ -207,6 +207,8 @@ __device__ __forceinline__ NormK make_norm_k(double mn, double inv) {
     return k;
 }
 
+// Knuth's TwoSum (exact error of a float32 sum, any magnitudes); ff_norm's
+// product error comes from one FMA (the FMA-based TwoProduct)
 __device__ __forceinline__ void ff_sum(float a, float b, float &s, float &e) {
     s = __fadd_rn(a, b);
     const float bb = __fsub_rn(s, a);

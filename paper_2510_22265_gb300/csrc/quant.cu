@@ -228,6 +228,10 @@ struct BoundsK {
     int ok;    // the field's constants lie in the covered range
 };
 
+// Knuth's TwoSum: s = fl(a + b) and the exact error e = (a + b) - s, with no
+// assumption on the magnitudes (Knuth, TAOCP vol. 2, 4.2.2); the products
+// below take their exact error from one FMA (fma(a, b, -fl(a b)), the
+// FMA-based TwoProduct)
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     s = __fadd_rn(a, b);
     const float bb = __fsub_rn(s, a);
