@@ -6,6 +6,8 @@
 * determinism, degenerate inputs and error codes;
 * the escape path of the residual layer, forced by a coarse SPIHT step.
 """
+import struct
+
 import numpy as np
 import pytest
 
@@ -113,3 +115,53 @@ def test_cblk_and_levels_parameters():
         _check(x, 1e-2, p=O.params(cblk=cb))
     for L in (0, 1, 3):
         _check(x, 1e-2, p=O.params(levels=L))
+
+
+def test_full_rate_base_layer_is_the_annex_e_quantiser():
+    """A bound far below the base layer's step leaves no ratio feasible, so the
+    base loop halves r down to 1, whose budget keeps every coding pass on a
+    block's rate-distortion hull.  The base layer's coefficients are then those
+    of the dead-zone quantiser of T.800 E.1.1 (q = sign(c) floor(|c| /
+    delta_b), delta_b from the band's step) with midpoint reconstruction
+    (E.1.1.2, r = 1/2), restated here from those definitions.  A block's last
+    pass (the cleanup of plane 0) may fall off its hull when it codes no new
+    significance, which changes no coefficient.  A wrong sign, rounding,
+    band-to-step mapping or reconstruction offset in the oracle's quantiser,
+    tier-1 or base container fails it."""
+    from streamutil import HDR
+    x = synth.smooth_field(48, 64, seed=11)
+    s, _ = O.compress(x, 1e-6)
+    ny, nx = x.shape
+    L = O.effective_levels(ny, nx, 5)
+    mn, mx = float(x.min()), float(x.max())
+    P = O.base_precision(1e-6)
+    # every block keeps all its passes, or all but the last
+    bl = struct.unpack_from("<I", s, 20)[0]
+    pos = HDR
+    for b in O.bands(ny, nx, L):
+        for _ in range(-(-b["h"] // 32) * -(-b["w"] // 32)):
+            n = s[pos]
+            pos += 1
+            if n == 0:
+                continue
+            K = s[pos]
+            pos += 1
+            while s[pos] & 0x80:
+                pos += 1
+            pos += 1
+            assert n in (3 * K - 2, 3 * K - 3)
+    assert pos <= HDR + bl
+    an = (x.astype(np.float64) - mn) / (mx - mn)
+    w = O.dwt_fwd(an, L)
+    rec = np.zeros_like(w)
+    q = np.zeros_like(w)
+    for b in O.bands(ny, nx, L):
+        d = O.step_for_band(P, b["level"], b["orient"])[2]
+        ys, xs = slice(b["y0"], b["y0"] + b["h"]), slice(b["x0"], b["x0"] + b["w"])
+        c = w[ys, xs]
+        qb = np.sign(c) * np.floor(np.abs(c) / d)
+        q[ys, xs] = qb
+        rec[ys, xs] = np.where(qb != 0, np.sign(qb) * (np.abs(qb) + 0.5) * d, 0.0)
+    got = O.dwt_fwd(O.base_decode(s, ny, nx), L)  # the decoded coefficients (perfect reconstruction)
+    assert np.abs(got - rec).max() <= 1e-12 * max(1.0, float(np.abs(rec).max()))
+    assert np.count_nonzero(q) > 0.9 * q.size  # the pin covers nearly every coefficient
